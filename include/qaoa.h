@@ -1,0 +1,227 @@
+/*
+ * qaoa.h - C ABI of the B300 (sm_103a) QAOA statevector library.
+ *
+ * The library evolves the depth-p QAOA state of a QUBO over all 2^n basis
+ * states on one GPU and returns the expectation, its exact gradient, and the
+ * most probable bitstrings.  Problem statement and notation follow the paper
+ * (arXiv 2606.26297):
+ *   - input QUBO (H, f, c0), F(z) = c0 + f^T z + z^T H z      Sec. 2.1, Eq. qubo_input_form
+ *   - canonical form l_i = f_i + H_ii, b_ij = H_ij + H_ji      Eqs. canonical_linear, canonical_quadratic
+ *   - cost Hamiltonian, eigenvalue F(z) on |z>                 Sec. 2.2, Eq. cost_hamiltonian_raw
+ *   - state U_M(b_p)U_C(g_p)...U_M(b_1)U_C(g_1)|+>^n           Sec. 2.3, Eq. qaoa_state
+ *   - U_C(g) = exp(-i g H_C), U_M(b) = exp(-i b sum_j X_j)     Eqs. qaoa_cost_unitary, qaoa_mixer_unitary
+ *   - objective sum_z P(z) F(z)                                Eqs. qaoa_expectation_expanded, training_objective_mean_cost
+ *   - QPU allocation and local/cross couplings                 Sec. 3.1, Sec. 3.2, Eq. local_cross_rule
+ *
+ * Conventions shared by every call:
+ *   - Variable z_{i+1} of the paper is bit i of the basis index x
+ *     (x = sum_i z_{i+1} 2^i).  The logical bitstring z_1..z_n of Sec. 3.6 is
+ *     bit 0 first.
+ *   - Angles are double; gamma[l-1] = gamma_l and beta[l-1] = beta_l.  The
+ *     paper's interleaved vector x = [gamma_1, beta_1, ...] (Sec. 3.4) is split
+ *     into these two arrays by the caller.
+ *   - Amplitudes are complex64 (float re, float im interleaved), 2^n of them,
+ *     in index order.  The phase of U_C is exactly exp(-i g F(x)), c0 included.
+ *   - Every call returns a qaoa_status.  No call aborts the process; on error
+ *     the thread-local message of qaoa_last_error() says what failed, and
+ *     output arguments are left unspecified.
+ *   - Host pointers are read or written before the call returns.  Device work
+ *     is ordered on the context's CUDA stream; calls that return host values
+ *     synchronise that stream.
+ *   - Handles are owned by the library and released with qaoa_*_destroy;
+ *     every other buffer belongs to the caller.
+ *   - Sizes: 1 <= n <= 33 (the state of n=33 is 64 GiB).  Functions that
+ *     keep a second state (gradients) need 2 states + the 4-byte cost table
+ *     in device memory.
+ */
+#ifndef QAOA_H
+#define QAOA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    QAOA_OK = 0,
+    QAOA_ERR_INVALID_ARG = 1,   /* null pointer, bad size, n out of range, k out of range */
+    QAOA_ERR_OUT_OF_MEMORY = 2, /* device allocation failed or exceeds the memory budget */
+    QAOA_ERR_RANGE = 3,         /* integer objective does not fit the 32-bit table */
+    QAOA_ERR_CUDA = 4,          /* a CUDA runtime call or kernel launch failed */
+    QAOA_ERR_TIMEOUT = 5,       /* a bounded device-side wait expired (status word set by a kernel) */
+    QAOA_ERR_ALLOCATION = 6     /* QPU allocation rejected (Sec. 3.1, validate_allocation) */
+} qaoa_status;
+
+/* Coefficient type of the caller's H and f arrays. */
+typedef enum {
+    QAOA_I32 = 0, /* int32_t; the objective table is exact */
+    QAOA_F32 = 1, /* float */
+    QAOA_F64 = 2  /* double */
+} qaoa_dtype;
+
+/* A QUBO in the input form of Sec. 2.1 (Eq. qubo_input_form).
+ * H: n*n coefficients, row-major, host memory, any (non-symmetric) matrix.
+ * f: n coefficients, host memory, or NULL for f = 0.
+ * c0: the constant term. */
+typedef struct {
+    int32_t n;
+    qaoa_dtype dtype;
+    const void *H;
+    const void *f;
+    double c0;
+} qaoa_qubo;
+
+/* Adjoint (gradient) strategy. */
+typedef enum {
+    QAOA_ADJ_AUTO = 0,      /* uncompute unless the memory budget forbids it */
+    QAOA_ADJ_UNCOMPUTE = 1  /* reverse sweep recomputes earlier states by U^dagger */
+} qaoa_adjoint_mode;
+
+/* Options of a context.  Zero-initialised means "defaults". */
+typedef struct {
+    int32_t adjoint_mode;   /* qaoa_adjoint_mode */
+    int32_t profile;        /* 1: time every pass kernel with CUDA events (see qaoa_profile_read) */
+    int64_t memory_budget;  /* bytes of device memory the context may hold; 0 = free memory */
+    int32_t max_fused_qubits; /* qubits per mixer pass: 0 = default (10), else 3..10 */
+    int32_t state_fp64;     /* 1: complex128 states and arithmetic (n <= 12 only) */
+    int32_t reserved[6];
+} qaoa_options;
+
+typedef struct qaoa_ctx_s *qaoa_ctx;     /* device, stream, options, scratch, plan cache */
+typedef struct qaoa_cost_s *qaoa_cost;   /* device objective table + canonical QUBO */
+typedef struct qaoa_state_s *qaoa_state; /* device statevector, complex64 */
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * (NULL = the legacy default stream) on which every launch of this context is
+ * ordered; the caller keeps ownership of the stream.  `opt` may be NULL. */
+qaoa_status qaoa_ctx_create(int device, void *cuda_stream, const qaoa_options *opt, qaoa_ctx *out);
+void qaoa_ctx_destroy(qaoa_ctx ctx);
+
+/* Thread-local description of the last error (never NULL). */
+const char *qaoa_last_error(void);
+
+/* ---- objective table ---------------------------------------------------- */
+
+/* Canonicalise `q` (Sec. 2.1, Eqs. canonical_linear, canonical_quadratic) and
+ * build on the device the table of F(x) for all 2^n basis indices (the
+ * diagonal of H_C, Sec. 2.2, Eq. cost_hamiltonian_raw).
+ * Storage: int32 fixed point, F(x) = (T[x] + k_c) * 2^-s.  Integer QUBOs use
+ * s = 0 and are exact (QAOA_ERR_RANGE if the range of F exceeds 2^31).  Real
+ * QUBOs round each canonical coefficient to a multiple of 2^-s, with s the
+ * largest value that keeps T in int32; the per-entry error is at most
+ * (1 + n + n(n-1)/2) * 2^-(s+1).  The inputs are copied; `q` may be freed
+ * after the call.  Also records the brute-force minimum (Sec. 3.7). */
+qaoa_status qaoa_build_cost(qaoa_ctx ctx, const qaoa_qubo *q, qaoa_cost *out);
+void qaoa_cost_destroy(qaoa_cost cost);
+
+/* Table metadata: n, fractional bits s, offset k_c (F = (T + k_c) 2^-s), the
+ * brute-force minimiser (smallest index among ties) and its value. */
+qaoa_status qaoa_cost_info(qaoa_cost cost, int32_t *n, int32_t *shift_bits, int64_t *k_c,
+                           uint64_t *argmin_idx, double *min_cost);
+
+/* Copy the int32 table T (2^n entries) into host memory `table`. */
+qaoa_status qaoa_cost_copy_to_host(qaoa_ctx ctx, qaoa_cost cost, int32_t *table);
+
+/* ---- forward evolution -------------------------------------------------- */
+
+/* Evolve |+>^n through p layers (Eq. qaoa_state).  gamma, beta: host arrays
+ * of p doubles, p >= 0.  *inout: a state handle for the same n, or NULL, in
+ * which case a new state is allocated and returned. */
+qaoa_status qaoa_forward(qaoa_ctx ctx, qaoa_cost cost, int p, const double *gamma,
+                         const double *beta, qaoa_state *inout);
+void qaoa_state_destroy(qaoa_state state);
+
+/* Copy the 2^n amplitudes into host memory `amps`: 2 * 2^n floats for a
+ * complex64 state, or 2 * 2^n doubles (passed through this float pointer) for
+ * a complex128 state (options.state_fp64). */
+qaoa_status qaoa_state_copy_to_host(qaoa_ctx ctx, qaoa_state state, float *amps);
+
+/* Device address of the amplitudes (complex64, 2^n) and their count; the
+ * pointer stays owned by the state. */
+qaoa_status qaoa_state_device_ptr(qaoa_state state, void **amps, int64_t *count);
+
+/* <H_C> = sum_x |psi_x|^2 F(x) (Eq. qaoa_expectation_expanded), reduced
+ * deterministically in FP64 (same inputs give the same bits). */
+qaoa_status qaoa_expect(qaoa_ctx ctx, qaoa_cost cost, qaoa_state state, double *out_expect);
+
+/* The k most probable bitstrings (1 <= k <= 64), ordered by probability
+ * descending then index ascending (the elite set of Sec. 3.6, ranked by exact
+ * probability).  idx, prob, cost_out: host arrays of k.  argmin_idx and
+ * min_cost (either may be NULL) receive the brute-force minimiser of F
+ * (Sec. 3.7); prob_argmin (may be NULL) its probability in this state. */
+qaoa_status qaoa_topk(qaoa_ctx ctx, qaoa_cost cost, qaoa_state state, int k, uint64_t *idx,
+                      float *prob, double *cost_out, uint64_t *argmin_idx, double *min_cost,
+                      float *prob_argmin);
+
+/* ---- gradient ----------------------------------------------------------- */
+
+/* E(gamma, beta) and its exact gradient dE/dgamma_l, dE/dbeta_l by a reverse
+ * (adjoint) sweep over the layers (the exact counterpart of the objective of
+ * Sec. 3.4, Eq. training_objective_mean_cost, whose gradient Sec. 4.2
+ * estimates by SPSA).  gamma, beta: host, p doubles each; out_expect: host
+ * double; dgamma, dbeta: host, p doubles each.  Optional top-K of the final
+ * state: k_top = 0 disables it; otherwise top_idx/top_prob are host arrays of
+ * k_top (<= 64), same ordering as qaoa_topk.  Device memory: one state plus
+ * the context's adjoint buffer (allocated on first use and kept). */
+qaoa_status qaoa_grad(qaoa_ctx ctx, qaoa_cost cost, int p, const double *gamma,
+                      const double *beta, double *out_expect, double *dgamma, double *dbeta,
+                      int k_top, uint64_t *top_idx, float *top_prob);
+
+/* ---- batched evaluation (Sec. 4.3: many parameter vectors per request) -- */
+
+/* B parameter sets evaluated in one request: item b uses cost handle
+ * costs[item_cost[b]] (item_cost may be NULL: all items use costs[0]), angles
+ * gamma[b*p .. b*p+p-1], beta[b*p ..].  Outputs expect[b], dgamma[b*p + l],
+ * dbeta[b*p + l]; dgamma/dbeta may be NULL for forward-only evaluation.
+ * All pointers are host memory.  Cost handles may differ in n (ragged batch). */
+qaoa_status qaoa_grad_batch(qaoa_ctx ctx, int nq, const qaoa_cost *costs, const int32_t *item_cost,
+                            int B, int p, const double *gamma, const double *beta,
+                            double *expect, double *dgamma, double *dbeta);
+
+/* ---- DQAOA bookkeeping (host) and the GPU factorisation invariant ------- */
+
+/* QPU allocation of Sec. 3.1.  caps: M capacities, or NULL for balanced
+ * capacities (floor(n/M) + [m < n mod M], make_balanced_capacities).
+ * manual: n QPU indices in [0, M), or NULL for the contiguous allocation
+ * (QPU 0 takes the first caps[0] variables, then QPU 1, ...).  The result
+ * is validated (every variable once, no capacity exceeded, every QPU used);
+ * QAOA_ERR_ALLOCATION if not.  qpu_of: host output, n entries. */
+qaoa_status qaoa_partition(int n, int M, const int32_t *caps, const int32_t *manual, int32_t *qpu_of);
+
+/* Classify the couplings b_ij != 0 (i<j) of `cost` as local (q(i) = q(j)) or
+ * cross-QPU (Eq. local_cross_rule), and estimate the remote CNOTs as
+ * 2 * cross * p (Sec. 3.1).  n_pairs_all (may be NULL) receives the cross
+ * count over all pairs, zero coefficients included.  Host only. */
+qaoa_status qaoa_classify(qaoa_cost cost, const int32_t *qpu_of, int p, int64_t *n_local,
+                          int64_t *n_cross, int64_t *remote_cx_est, int64_t *n_cross_all_pairs);
+
+/* GPU check that, for every x, the table splits as
+ *   T[x] + k_c == c0 + sum_m L_m[field_m(x)] + X(x)
+ * with L_m the objective of QPU m's own variables and local couplings and X
+ * the sum of the cross-QPU couplings (Sec. 3.2), i.e. that the cost phase
+ * factorises into local and cross-QPU parts.  All in exact integer arithmetic
+ * on the fixed-point coefficients.  *mismatches = number of x that differ;
+ * *max_phase_err = max over x of |e^{-i g F} - e^{-i g F_local} e^{-i g F_cross}|
+ * at g = gamma_probe, evaluated with the library's own phase routine. */
+qaoa_status qaoa_check_factorisation(qaoa_ctx ctx, qaoa_cost cost, const int32_t *qpu_of,
+                                     double gamma_probe, int64_t *mismatches, double *max_phase_err);
+
+/* ---- profiling ---------------------------------------------------------- */
+
+/* With options.profile = 1, every kernel launch of the given kind is timed
+ * with CUDA events on the context stream.  kind: 0 = forward mixer pass,
+ * 1 = reverse (adjoint) pass, 2 = objective table build, 3 = small-n resident
+ * kernel, 4 = factorisation check.  Returns launches, summed milliseconds and
+ * summed algorithmic bytes (bytes the method must move) since the last reset;
+ * reset = 1 clears the counters after reading. */
+qaoa_status qaoa_profile_read(qaoa_ctx ctx, int kind, int64_t *launches, double *ms,
+                              double *bytes, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QAOA_H */

@@ -1,0 +1,532 @@
+// Objective-table build (Sec. 2.1-2.2), expectation and top-K over a stored
+// state, the shared-memory-resident small-n evaluator, and the DQAOA
+// factorisation check (Sec. 3.2).
+#include "kernels_misc.h"
+#include "pass_common.cuh"
+
+namespace qaoa {
+
+// ---------------------------------------------------------------------------
+// objective table: T[x] = c_off + sum l_i z_i + sum_{i<j} b_ij z_i z_j (exact
+// int64, stored as int32).  x = x_lo | mid << nlo | top << (nlo+t); each
+// thread owns one (x_lo, top) and walks its 2^t mid values in Gray-code
+// order: flipping bit j changes F by +/-D_j with D_j = l_j + sum_{i!=j} b_ij z_i.
+// ---------------------------------------------------------------------------
+constexpr int MAXT = 8;
+
+__global__ void cost_build_kernel(CostBuildArgs a) {
+    extern __shared__ long long shc[];  // ell[n], bs[n*n] symmetric
+    const int n = a.n;
+    long long *ell = shc;
+    long long *bs = shc + n;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) ell[k] = a.ell[k];
+    for (int k = threadIdx.x; k < n * n; k += blockDim.x) {
+        const int i = k / n, j = k % n;
+        bs[k] = i < j ? a.b[k] : (j < i ? a.b[j * n + i] : 0);
+    }
+    __syncthreads();
+    const unsigned long long gt = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int nlo = a.nlo, t = a.t;
+    const unsigned long long xlo = gt & ((1ull << nlo) - 1ull), top = gt >> nlo;
+    unsigned long long x = xlo | (top << (nlo + t));
+    long long F = a.c_off;
+    for (int i = 0; i < n; ++i) {
+        if (!((x >> i) & 1ull)) continue;
+        F += ell[i];
+        for (int j = i + 1; j < n; ++j)
+            if ((x >> j) & 1ull) F += bs[i * n + j];
+    }
+    long long D[MAXT];
+#pragma unroll
+    for (int k = 0; k < MAXT; ++k) {
+        D[k] = 0;
+        if (k < t) {
+            const int j = nlo + k;
+            long long d = ell[j];
+            for (int i = 0; i < n; ++i)
+                if (i != j && ((x >> i) & 1ull)) d += bs[i * n + j];
+            D[k] = d;
+        }
+    }
+    long long best = F;
+    unsigned long long bestx = x;
+    a.T[x] = (int32_t)F;
+    const unsigned cnt = 1u << t;
+    for (unsigned u = 1; u < cnt; ++u) {
+        const int k = __ffs(u) - 1;
+        const int j = nlo + k;
+        const bool was = (x >> j) & 1ull;
+        long long dk = 0;
+#pragma unroll
+        for (int kk = 0; kk < MAXT; ++kk)
+            if (kk == k) dk = D[kk];
+        F += was ? -dk : dk;
+        const long long sgn = was ? -1 : 1;
+#pragma unroll
+        for (int kk = 0; kk < MAXT; ++kk)
+            if (kk < t && kk != k) D[kk] += sgn * bs[j * n + nlo + kk];
+        x ^= 1ull << j;
+        a.T[x] = (int32_t)F;
+        if (F < best || (F == best && x < bestx)) {
+            best = F;
+            bestx = x;
+        }
+    }
+    // block argmin (value, then index)
+    __shared__ long long sv[256];
+    __shared__ unsigned long long sx[256];
+    sv[threadIdx.x] = best;
+    sx[threadIdx.x] = bestx;
+    __syncthreads();
+    for (int s = blockDim.x >> 1; s; s >>= 1) {
+        if ((int)threadIdx.x < s) {
+            const long long ov = sv[threadIdx.x + s];
+            const unsigned long long ox = sx[threadIdx.x + s];
+            if (ov < sv[threadIdx.x] || (ov == sv[threadIdx.x] && ox < sx[threadIdx.x])) {
+                sv[threadIdx.x] = ov;
+                sx[threadIdx.x] = ox;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        a.blk_val[blockIdx.x] = sv[0];
+        a.blk_idx[blockIdx.x] = sx[0];
+    }
+}
+
+__global__ void argmin_reduce_kernel(const long long *val, const unsigned long long *idx, int m,
+                                     long long *oval, unsigned long long *oidx) {
+    __shared__ long long sv[256];
+    __shared__ unsigned long long sx[256];
+    long long bv = LLONG_MAX;
+    unsigned long long bx = ~0ull;
+    for (int k = threadIdx.x; k < m; k += 256)
+        if (val[k] < bv || (val[k] == bv && idx[k] < bx)) {
+            bv = val[k];
+            bx = idx[k];
+        }
+    sv[threadIdx.x] = bv;
+    sx[threadIdx.x] = bx;
+    __syncthreads();
+    for (int s = 128; s; s >>= 1) {
+        if ((int)threadIdx.x < s) {
+            const long long ov = sv[threadIdx.x + s];
+            const unsigned long long ox = sx[threadIdx.x + s];
+            if (ov < sv[threadIdx.x] || (ov == sv[threadIdx.x] && ox < sx[threadIdx.x])) {
+                sv[threadIdx.x] = ov;
+                sx[threadIdx.x] = ox;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        *oval = sv[0];
+        *oidx = sx[0];
+    }
+}
+
+cudaError_t launch_cost_build(CostBuildArgs a, int *nblocks_out, cudaStream_t st) {
+    const int n = a.n;
+    a.nlo = n < 12 ? n : 12;
+    a.t = (n - a.nlo) < MAXT ? (n - a.nlo) : MAXT;
+    const unsigned long long threads = 1ull << (n - a.t);
+    const int bs = threads < 256 ? (int)threads : 256;
+    const unsigned long long grid = threads / bs;
+    const int smem = (n + n * n) * (int)sizeof(long long);
+    cost_build_kernel<<<(unsigned)grid, bs, smem, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e) return e;
+    argmin_reduce_kernel<<<1, 256, 0, st>>>(a.blk_val, a.blk_idx, (int)grid, a.min_val, a.min_idx);
+    *nblocks_out = (int)grid;
+    return cudaGetLastError();
+}
+
+int cost_build_blocks(int n) {
+    const int nlo = n < 12 ? n : 12;
+    const int t = (n - nlo) < MAXT ? (n - nlo) : MAXT;
+    const unsigned long long threads = 1ull << (n - t);
+    const int bs = threads < 256 ? (int)threads : 256;
+    return (int)(threads / bs);
+}
+
+// ---------------------------------------------------------------------------
+// <H_C> and top-K over a stored complex64 state (chunks of 8192 amplitudes)
+// ---------------------------------------------------------------------------
+__global__ void expect_kernel(const float2 *__restrict__ psi, const int32_t *__restrict__ T, long long N,
+                              double *partials) {
+    __shared__ double red[8][NSLOT];
+    const long long b0 = (long long)blockIdx.x * 8192;
+    float e0 = 0.f, e1 = 0.f;
+#pragma unroll 8
+    for (int m = 0; m < 32; ++m) {
+        const long long x = b0 + threadIdx.x + 256 * m;
+        if (x < N) {
+            const float2 a = psi[x];
+            const float P = fmaf(a.x, a.x, a.y * a.y);
+            e0 = fmaf(P, (float)T[x], e0);
+            e1 += P;
+        }
+    }
+    double vals[NSLOT] = {(double)e0, (double)e1, 0.0, 0.0, 0.0};
+    block_sum_write(vals, red, partials, blockIdx.x);
+}
+
+// Per-chunk top-K (K <= 64) by key (P desc, index asc).
+__global__ void topk_chunk_kernel(const float2 *__restrict__ psi, long long N, int K,
+                                  unsigned long long *out) {
+    __shared__ unsigned long long smk[8 * 64];
+    const uint32_t l = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long long b0 = (long long)blockIdx.x * 8192;
+    float P[32];
+#pragma unroll
+    for (int m = 0; m < 32; ++m) {
+        const long long x = b0 + threadIdx.x + 256 * m;
+        if (x < N) {
+            const float2 a = psi[x];
+            P[m] = fmaf(a.x, a.x, a.y * a.y);
+        } else {
+            P[m] = -1.f;
+        }
+    }
+    uint32_t taken = 0;
+    unsigned long long bk = 0;
+    int bm = -1;
+    auto scan = [&]() {
+        bk = 0;
+        bm = -1;
+#pragma unroll
+        for (int m = 0; m < 32; ++m) {
+            if (((taken >> m) & 1u) || P[m] < 0.f) continue;
+            const unsigned long long x = (unsigned long long)(b0 + threadIdx.x + 256 * m);
+            const unsigned long long key = ((unsigned long long)__float_as_uint(P[m]) << 33) | (0x1FFFFFFFFull - x);
+            if (key > bk) {
+                bk = key;
+                bm = m;
+            }
+        }
+    };
+    scan();
+    for (int r = 0; r < K; ++r) {
+        unsigned long long wb = bk;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            const unsigned long long t = __shfl_xor_sync(0xffffffffu, wb, o);
+            wb = t > wb ? t : wb;
+        }
+        if (l == 0) smk[w * 64 + r] = wb;
+        if (bk == wb && bm >= 0) {
+            taken |= 1u << bm;
+            scan();
+        }
+    }
+    __syncthreads();
+    if (w == 0) {
+        int head = 0;
+        for (int r = 0; r < K; ++r) {
+            const unsigned long long mine = (l < 8 && head < K) ? smk[l * 64 + head] : 0ull;
+            unsigned long long wb = mine;
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                const unsigned long long t = __shfl_xor_sync(0xffffffffu, wb, o);
+                wb = t > wb ? t : wb;
+            }
+            if (l < 8 && mine == wb && wb != 0ull) ++head;
+            if (l == 0) out[(size_t)blockIdx.x * K + r] = wb;
+        }
+    }
+}
+
+cudaError_t launch_expect(const float2 *psi, const int32_t *T, int n, double *partials, cudaStream_t st) {
+    const long long N = 1ll << n;
+    const unsigned grid = (unsigned)((N + 8191) / 8192);
+    expect_kernel<<<grid, 256, 0, st>>>(psi, T, N, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_topk_chunks(const float2 *psi, int n, int K, unsigned long long *out, cudaStream_t st) {
+    const long long N = 1ll << n;
+    const unsigned grid = (unsigned)((N + 8191) / 8192);
+    topk_chunk_kernel<<<grid, 256, 0, st>>>(psi, N, K, out);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// small-n evaluator: one CTA per item, the whole state in shared memory,
+// all p layers forward (Eq. qaoa_state), <H_C>, optional top-K, and the
+// adjoint sweep.  R = float (complex64) or double (complex128).
+// ---------------------------------------------------------------------------
+template <typename R>
+struct Cx;
+template <>
+struct Cx<float> {
+    using T = float2;
+    __device__ static T mk(float a, float b) { return make_float2(a, b); }
+};
+template <>
+struct Cx<double> {
+    using T = double2;
+    __device__ static T mk(double a, double b) { return make_double2(a, b); }
+};
+
+template <typename R>
+__device__ __forceinline__ typename Cx<R>::T small_phase(int32_t tq, unsigned long long phi,
+                                                          unsigned long long off, int precise);
+template <>
+__device__ __forceinline__ float2 small_phase<float>(int32_t tq, unsigned long long phi,
+                                                      unsigned long long off, int precise) {
+    return cost_phase(tq, phi, off, 1.0f, precise);
+}
+template <>
+__device__ __forceinline__ double2 small_phase<double>(int32_t tq, unsigned long long phi,
+                                                        unsigned long long off, int) {
+    const unsigned long long t = (unsigned long long)(long long)tq * phi + off;
+    const double a = (double)(long long)t * 1.0842021724855044e-19;  // turns*2 in [-1,1): 2^-63
+    double s, c;
+    sincospi(a, &s, &c);
+    return make_double2(c, -s);
+}
+
+template <typename C2>
+__device__ __forceinline__ C2 cm(C2 a, C2 b) {
+    C2 r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+
+// deterministic block sum for 512 threads (16 warps); result valid in all threads
+__device__ __forceinline__ double bsum512(double x, double *sh) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = x;
+    __syncthreads();
+    double t = 0.0;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) t += sh[k];
+    return t;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(512, 1) small_kernel(const SmallItem *__restrict__ items) {
+    using C2 = typename Cx<R>::T;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ double red[16];
+    __shared__ unsigned long long bestk[16];
+    const SmallItem &it = items[blockIdx.x];
+    const int n = it.n, p = it.p;
+    const int N = 1 << n, H = N >> 1;
+    C2 *psi = reinterpret_cast<C2 *>(smraw);
+    C2 *lam = psi + N;
+    int32_t *T = reinterpret_cast<int32_t *>(lam + (it.grad ? N : 0));
+    const int tid = threadIdx.x;
+    for (int x = tid; x < N; x += 512) {
+        T[x] = it.T[x];
+        psi[x] = Cx<R>::mk((R)it.amp0, (R)0);
+    }
+    for (int l = 0; l < p; ++l) {
+        __syncthreads();
+        for (int x = tid; x < N; x += 512) psi[x] = cm(psi[x], small_phase<R>(T[x], it.phi[l], it.off[l], it.precise));
+        const R c = (R)it.cb[l], s = (R)it.sb[l];
+        for (int j = 0; j < n; ++j) {
+            __syncthreads();
+            for (int k = tid; k < H; k += 512) {
+                const int lowm = (1 << j) - 1;
+                const int x = ((k & ~lowm) << 1) | (k & lowm), y = x | (1 << j);
+                const C2 a = psi[x], b = psi[y];
+                psi[x] = Cx<R>::mk(c * a.x + s * b.y, c * a.y - s * b.x);  // c a - i s b
+                psi[y] = Cx<R>::mk(c * b.x + s * a.y, c * b.y - s * a.x);  // c b - i s a
+            }
+        }
+    }
+    __syncthreads();
+    // <H_C>
+    double e0 = 0.0, e1 = 0.0;
+    for (int x = tid; x < N; x += 512) {
+        const double P = (double)psi[x].x * psi[x].x + (double)psi[x].y * psi[x].y;
+        e0 += P * (double)T[x];
+        e1 += P;
+    }
+    e0 = bsum512(e0, red);
+    e1 = bsum512(e1, red);
+    if (tid == 0) it.out[0] = (e0 + (double)it.k_c * e1) * it.cscale;
+    if (it.psi_out) {
+        for (int x = tid; x < N; x += 512) {
+            if (sizeof(R) == 4) reinterpret_cast<float2 *>(it.psi_out)[x] = make_float2((float)psi[x].x, (float)psi[x].y);
+            else reinterpret_cast<double2 *>(it.psi_out)[x] = make_double2((double)psi[x].x, (double)psi[x].y);
+        }
+    }
+    // top-K by (P desc, x asc): K rounds of block argmax
+    if (it.ktop > 0) {
+        unsigned long long taken_last = ~0ull;  // key taken in the previous round
+        for (int r = 0; r < it.ktop; ++r) {
+            unsigned long long bk = 0;
+            for (int x = tid; x < N; x += 512) {
+                const float P = (float)((double)psi[x].x * psi[x].x + (double)psi[x].y * psi[x].y);
+                const unsigned long long key = ((unsigned long long)__float_as_uint(P) << 33) | (0x1FFFFFFFFull - x);
+                if (key < taken_last && key > bk) bk = key;
+            }
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                const unsigned long long t = __shfl_xor_sync(0xffffffffu, bk, o);
+                bk = t > bk ? t : bk;
+            }
+            __syncthreads();
+            if ((tid & 31) == 0) bestk[tid >> 5] = bk;
+            __syncthreads();
+            unsigned long long b = 0;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) b = bestk[k] > b ? bestk[k] : b;
+            if (tid == 0) it.topk[r] = b;
+            taken_last = b;
+        }
+    }
+    if (!it.grad) return;
+    // adjoint sweep: lambda = H_C psi (shifted by k_c 2^-s)
+    for (int x = tid; x < N; x += 512) {
+        const R f = (R)((double)T[x] * it.cscale);
+        lam[x] = Cx<R>::mk(f * psi[x].x, f * psi[x].y);
+    }
+    for (int l = p - 1; l >= 0; --l) {
+        const R c = (R)it.cb[l], s = (R)it.sb[l];
+        double xt = 0.0;
+        for (int j = 0; j < n; ++j) {
+            __syncthreads();
+            for (int k = tid; k < H; k += 512) {
+                const int lowm = (1 << j) - 1;
+                const int x = ((k & ~lowm) << 1) | (k & lowm), y = x | (1 << j);
+                const C2 a = psi[x], b = psi[y], la = lam[x], lb = lam[y];
+                // Im(conj(la) b) + Im(conj(lb) a)
+                xt += (double)(la.x * b.y - la.y * b.x) + (double)(lb.x * a.y - lb.y * a.x);
+                // undo: RX(-2 beta): (a, b) <- (c a + i s b, c b + i s a)
+                psi[x] = Cx<R>::mk(c * a.x - s * b.y, c * a.y + s * b.x);
+                psi[y] = Cx<R>::mk(c * b.x - s * a.y, c * b.y + s * a.x);
+                lam[x] = Cx<R>::mk(c * la.x - s * lb.y, c * la.y + s * lb.x);
+                lam[y] = Cx<R>::mk(c * lb.x - s * la.y, c * lb.y + s * la.x);
+            }
+        }
+        xt = bsum512(xt, red);
+        if (tid == 0) it.out[1 + p + l] = 2.0 * xt;
+        __syncthreads();
+        double g = 0.0;
+        for (int x = tid; x < N; x += 512) {
+            const C2 a = psi[x], la = lam[x];
+            g += (double)T[x] * (double)(la.x * a.y - la.y * a.x);
+            C2 ph = small_phase<R>(T[x], it.phi[l], it.off[l], it.precise);
+            ph.y = -ph.y;  // inverse phase
+            psi[x] = cm(a, ph);
+            lam[x] = cm(la, ph);
+        }
+        g = bsum512(g, red);
+        if (tid == 0) it.out[1 + l] = 2.0 * it.cscale * g;
+    }
+}
+
+int small_smem_bytes(int n, bool fp64, bool grad) {
+    const int N = 1 << n;
+    const int c2 = fp64 ? 16 : 8;
+    return N * c2 * (grad ? 2 : 1) + N * 4;
+}
+
+cudaError_t launch_small(const SmallItem *items_dev, int count, int max_n, bool fp64, bool grad,
+                         cudaStream_t st) {
+    const int smem = small_smem_bytes(max_n, fp64, grad);
+    cudaError_t e;
+    if (fp64) {
+        if ((e = cudaFuncSetAttribute(small_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)))
+            return e;
+        small_kernel<double><<<count, 512, smem, st>>>(items_dev);
+    } else {
+        if ((e = cudaFuncSetAttribute(small_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)))
+            return e;
+        small_kernel<float><<<count, 512, smem, st>>>(items_dev);
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// DQAOA factorisation check (Sec. 3.2): for every x,
+//   T[x] == c_off + sum_m L_m[u_m(x)] + sum_{m<m'} sum_{a in m} z_a V_{m,m'}[u_m'(x)][a]
+// with u_m(x) the bits of QPU m's variables.  Also the phase-product error.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 phase_ll(long long v, unsigned long long phi, unsigned long long off) {
+    const unsigned long long t = (unsigned long long)v * phi + off;
+    const int32_t hi = (int32_t)((t + 0x80000000ull) >> 32);
+    float s, c;
+    __sincosf((float)hi * 1.4629180792671596e-09f, &s, &c);
+    return make_float2(c, -s);
+}
+
+__global__ void fact_check_kernel(FactArgs a) {
+    __shared__ int qof[64], pos[64], qstart[17], qsize[16];
+    __shared__ unsigned long long cnt_sh;
+    __shared__ unsigned int err_sh;
+    if (threadIdx.x < (unsigned)a.n) {
+        qof[threadIdx.x] = a.qpu_of[threadIdx.x];
+        pos[threadIdx.x] = a.pos_in_q[threadIdx.x];
+    }
+    if (threadIdx.x <= (unsigned)a.M) qstart[threadIdx.x] = a.q_start[threadIdx.x];
+    if (threadIdx.x == 0) {
+        cnt_sh = 0;
+        err_sh = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x < (unsigned)a.M) qsize[threadIdx.x] = qstart[threadIdx.x + 1] - qstart[threadIdx.x];
+    __syncthreads();
+    const long long N = 1ll << a.n;
+    unsigned long long bad = 0;
+    float maxerr = 0.f;
+    for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < N;
+         x += (long long)gridDim.x * blockDim.x) {
+        unsigned int u[16];
+#pragma unroll
+        for (int m = 0; m < 16; ++m) u[m] = 0;
+        for (int i = 0; i < a.n; ++i)
+            if ((x >> i) & 1ll) {
+                const int m = qof[i];
+#pragma unroll
+                for (int mm = 0; mm < 16; ++mm)
+                    if (mm == m) u[mm] |= 1u << pos[i];
+            }
+        long long loc = a.c_off, cross = 0;
+        for (int m = 0; m < a.M; ++m) {
+            unsigned int um = 0;
+#pragma unroll
+            for (int mm = 0; mm < 16; ++mm)
+                if (mm == m) um = u[mm];
+            loc += a.Ltab[a.L_off[m] + um];
+            for (int m2 = m + 1; m2 < a.M; ++m2) {
+                unsigned int u2 = 0;
+#pragma unroll
+                for (int mm = 0; mm < 16; ++mm)
+                    if (mm == m2) u2 = u[mm];
+                const long long *Vrow = a.V + a.V_off[m * 16 + m2] + (size_t)u2 * qsize[m];
+                for (int q = 0; q < qsize[m]; ++q)
+                    if ((um >> q) & 1u) cross += Vrow[q];
+            }
+        }
+        const int32_t tx = a.T[x];
+        if ((long long)tx != loc + cross) ++bad;
+        const float2 pf = phase_ll((long long)tx + a.k_c, a.phi, 0ull);
+        const float2 pl = phase_ll(loc + a.k_c, a.phi, 0ull);
+        const float2 pc = phase_ll(cross, a.phi, 0ull);
+        const float2 pp = cmul(pl, pc);
+        const float err = fmaxf(fabsf(pf.x - pp.x), fabsf(pf.y - pp.y));
+        maxerr = fmaxf(maxerr, err);
+    }
+    atomicAdd(&cnt_sh, bad);
+    atomicMax(&err_sh, __float_as_uint(maxerr));
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        atomicAdd(a.mismatches, cnt_sh);
+        atomicMax(a.max_err_bits, err_sh);
+    }
+}
+
+cudaError_t launch_fact_check(const FactArgs &a, cudaStream_t st) {
+    fact_check_kernel<<<148 * 8, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace qaoa

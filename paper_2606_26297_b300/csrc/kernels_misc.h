@@ -1,0 +1,65 @@
+// Argument blocks and launchers of kernels_misc.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "qaoa_internal.h"
+
+namespace qaoa {
+
+struct CostBuildArgs {
+    int n, nlo, t;
+    const long long *ell;      // [n]    fixed-point linear coefficients (device)
+    const long long *b;        // [n*n]  fixed-point couplings, upper triangle (device)
+    long long c_off;           // c0_q - k_c
+    int32_t *T;                // [2^n]  table out
+    long long *blk_val;        // [blocks] per-CTA minimum
+    unsigned long long *blk_idx;
+    long long *min_val;        // final minimum (device scalar)
+    unsigned long long *min_idx;
+};
+cudaError_t launch_cost_build(CostBuildArgs a, int *nblocks_out, cudaStream_t st);
+int cost_build_blocks(int n);
+
+cudaError_t launch_expect(const float2 *psi, const int32_t *T, int n, double *partials, cudaStream_t st);
+cudaError_t launch_topk_chunks(const float2 *psi, int n, int K, unsigned long long *out, cudaStream_t st);
+
+constexpr int SMALL_MAXP = 64;
+constexpr int SMALL_MAXN = 12;
+
+// One small-n evaluation (n <= 12): the whole state lives in shared memory.
+struct SmallItem {
+    const int32_t *T;          // table (device)
+    void *psi_out;             // optional final state (complex64 or complex128), device
+    double *out;               // [1 + 2p]: E, dE/dgamma[p], dE/dbeta[p] (device)
+    unsigned long long *topk;  // [ktop] keys (device)
+    int n, p, grad, ktop, precise;
+    float amp0;
+    double cscale;             // 2^-s
+    long long k_c;
+    unsigned long long phi[SMALL_MAXP], off[SMALL_MAXP];
+    double cb[SMALL_MAXP], sb[SMALL_MAXP];  // cos, sin of beta_l
+};
+int small_smem_bytes(int n, bool fp64, bool grad);
+cudaError_t launch_small(const SmallItem *items_dev, int count, int max_n, bool fp64, bool grad,
+                         cudaStream_t st);
+
+struct FactArgs {
+    const int32_t *T;
+    int n, M;
+    const int *qpu_of;        // [n]
+    const int *pos_in_q;      // [n] position of variable i inside its QPU
+    const int *q_start;       // [M+1] prefix sums of QPU sizes
+    const long long *Ltab;    // concatenated per-QPU local tables
+    const long long *L_off;   // [M]
+    const long long *V;       // concatenated pair tables V_{m,m'}[u'][a]
+    const long long *V_off;   // [16*16]
+    long long c_off;          // c0_q - k_c
+    long long k_c;
+    unsigned long long phi;   // probe phase multiplier
+    unsigned long long *mismatches;
+    unsigned int *max_err_bits;
+};
+cudaError_t launch_fact_check(const FactArgs &a, cudaStream_t st);
+
+}  // namespace qaoa

@@ -1,0 +1,174 @@
+// Device helpers shared by the layer-pass kernels: block layouts, register
+// butterflies for RX(2 beta), the exact fixed-point cost phase, and
+// deterministic block reductions.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "qaoa_internal.h"
+
+namespace qaoa {
+
+// ---------------------------------------------------------------------------
+// Block layout.  A CTA owns 2^13 amplitudes ("block").  Its 13 local bits map
+// to global index bits in one of two ways:
+//   type 0 (low group):  local bit i  = global bit i, i < 13;
+//   type 1 (high group): local bits 0..2 = global bits 0..2 (carried for
+//                        coalescing), local bits 3..12 = global bits lo..lo+9.
+// 256 threads hold 32 amplitudes each, in one of two arrangements: a thread's
+// lane (5 bits), register slot m (5 bits) and warp (3 bits) select the local
+// index.  Butterflies act on the 5 register bits; a transpose through shared
+// memory swaps which local bits are register bits.
+//   type 0  X: lanes {0,1,2,8,9}  regs {3..7}        warps {10,11,12}
+//           Y: lanes {3..7}       regs {0,1,2,8,9}   warps {10,11,12}
+//   type 1  X: lanes {0..4}       regs {5..9}        warps {10,11,12}
+//           Y: lanes {0,1,2,5,6}  regs {3,4,10,11,12} warps {7,8,9}
+// Every arrangement keeps global bits 0..2 (or 0..4) in lanes or in a
+// thread-contiguous run, so global accesses stay in >= 64-byte segments.
+// ---------------------------------------------------------------------------
+
+template <int T, int A>
+__device__ __forceinline__ constexpr int regbit(int i) {
+    return T == 0 ? (A == 0 ? 3 + i : (i < 3 ? i : 5 + i))
+                  : (A == 0 ? 5 + i : (i < 2 ? 3 + i : 8 + i));
+}
+
+template <int T, int A>
+__device__ __forceinline__ constexpr uint32_t local_idx(uint32_t l, uint32_t m, uint32_t w) {
+    return T == 0 ? (A == 0 ? ((l & 7u) | ((l >> 3) << 8) | (m << 3) | (w << 10))
+                            : ((l << 3) | (m & 7u) | ((m >> 3) << 8) | (w << 10)))
+                  : (A == 0 ? (l | (m << 5) | (w << 10))
+                            : ((l & 7u) | ((l >> 3) << 5) | ((m & 3u) << 3) | ((m >> 2) << 10) | (w << 7)));
+}
+
+// XOR swizzle of the shared-memory slot; linear over GF(2), and conflict free
+// for 8-byte accesses in both arrangements (16 lanes of a half-warp hit 16
+// distinct slots mod 16).
+template <int T>
+__device__ __forceinline__ constexpr uint32_t swz(uint32_t e) {
+    return T == 0 ? (e ^ ((e >> 4) & 7u) ^ (((e >> 8) & 1u) << 3)) : (e ^ (((e >> 5) & 1u) << 3));
+}
+
+// Global element offset of local index e, relative to the block base.
+template <int T>
+__device__ __forceinline__ size_t goff(uint32_t e, int lo) {
+    return T == 0 ? (size_t)e : ((size_t)(e & 7u) | ((size_t)(e >> 3) << lo));
+}
+
+template <int T>
+__device__ __forceinline__ size_t block_base(uint32_t b, int lo) {
+    if (T == 0) return (size_t)b << 13;
+    const int nlow = lo - 3;  // global bits 3 .. lo-1 come from the low block-index bits
+    return ((size_t)(b & ((1u << nlow) - 1u)) << 3) | ((size_t)(b >> nlow) << (lo + 10));
+}
+
+// ---------------------------------------------------------------------------
+// complex helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+
+// RX(2 beta) pair update without its common factor.  Tangent form (mode 1):
+// (a, b) <- (a - i t b, b - i t a); the true result is cos(beta) times this.
+__device__ __forceinline__ void bfly_tan(float2 &a, float2 &b, float t) {
+    const float2 na = make_float2(fmaf(t, b.y, a.x), fmaf(-t, b.x, a.y));
+    const float2 nb = make_float2(fmaf(t, a.y, b.x), fmaf(-t, a.x, b.y));
+    a = na;
+    b = nb;
+}
+// Cotangent form (mode 2): (a, b) <- (b + i u a, a + i u b); the true result
+// is -i sin(beta) times this.
+__device__ __forceinline__ void bfly_cot(float2 &a, float2 &b, float u) {
+    const float2 na = make_float2(fmaf(-u, a.y, b.x), fmaf(u, a.x, b.y));
+    const float2 nb = make_float2(fmaf(-u, b.y, a.x), fmaf(u, b.x, a.y));
+    a = na;
+    b = nb;
+}
+
+// One register round: the butterflies of every mixed register bit.
+template <int T, int A>
+__device__ __forceinline__ void round_mix(float2 (&v)[32], MixOp op, uint32_t mask) {
+    if (op.mode == 1) {
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            if (!((mask >> regbit<T, A>(i)) & 1u)) continue;
+#pragma unroll
+            for (int m = 0; m < 32; ++m)
+                if (!(m & (1 << i))) bfly_tan(v[m], v[m | (1 << i)], op.t);
+        }
+    } else if (op.mode == 2) {
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            if (!((mask >> regbit<T, A>(i)) & 1u)) continue;
+#pragma unroll
+            for (int m = 0; m < 32; ++m)
+                if (!(m & (1 << i))) bfly_cot(v[m], v[m | (1 << i)], op.t);
+        }
+    }
+}
+
+// sum over the mixed register bits j of sum_m Im(conj(u_m) v_{m^j}): the part
+// of Im <lambda| sum_j X_j |psi> held by this thread in this arrangement.
+template <int T, int A>
+__device__ __forceinline__ float xterm(const float2 (&u)[32], const float2 (&v)[32], uint32_t mask) {
+    float acc = 0.f;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        if (!((mask >> regbit<T, A>(i)) & 1u)) continue;
+        float s = 0.f;
+#pragma unroll
+        for (int m = 0; m < 32; ++m) {
+            if (m & (1 << i)) continue;
+            const int q = m | (1 << i);
+            // Im(conj(u_m) v_q) + Im(conj(u_q) v_m)
+            s = fmaf(u[m].x, v[q].y, s);
+            s = fmaf(-u[m].y, v[q].x, s);
+            s = fmaf(u[q].x, v[m].y, s);
+            s = fmaf(-u[q].y, v[m].x, s);
+        }
+        acc += s;
+    }
+    return acc;
+}
+
+// exp(-2 pi i t / 2^64) * kmag for t = T * phi + off (mod 2^64).  The turn
+// count is exact modular integer arithmetic; it is rounded to 32 bits
+// (2^-33 turn) and then to an FP32 angle in [-pi, pi).
+__device__ __forceinline__ float2 cost_phase(int32_t tq, unsigned long long phi, unsigned long long off,
+                                             float kmag, int precise) {
+    const unsigned long long t = (unsigned long long)(long long)tq * phi + off;
+    const int32_t hi = (int32_t)((t + 0x80000000ull) >> 32);
+    float s, c;
+    if (precise) {
+        sincospif((float)hi * 4.656612873077393e-10f, &s, &c);  // angle/pi = hi 2^-31
+    } else {
+        __sincosf((float)hi * 1.4629180792671596e-09f, &s, &c);  // angle = hi 2 pi 2^-32
+    }
+    return make_float2(c * kmag, -s * kmag);
+}
+
+// Deterministic block sum of NSLOT FP64 values (fixed shuffle tree, then warps
+// in index order).  red: shared [8][NSLOT].  Writes out[blockIdx.x*NSLOT+s].
+__device__ __forceinline__ void block_sum_write(double (&val)[NSLOT], double (*red)[NSLOT], double *out,
+                                                uint32_t blk) {
+    const int l = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int s = 0; s < NSLOT; ++s) {
+        double x = val[s];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (l == 0) red[w][s] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < NSLOT) {
+        double t = 0.0;
+#pragma unroll
+        for (int k = 0; k < PASS_THREADS / 32; ++k) t += red[k][threadIdx.x];
+        out[(size_t)blk * NSLOT + threadIdx.x] = t;
+    }
+}
+
+}  // namespace qaoa

@@ -1,0 +1,281 @@
+"""Thin Python binding of the C ABI in include/qaoa.h.
+
+Argument marshalling only: every function has the name of its C entry point,
+converts numpy / torch arguments to plain pointers, calls the library, and
+raises QaoaError on a non-zero status.  All computation happens in
+libqaoa.so (CUDA, sm_103a); if the library is missing, importing this module
+fails loudly.  There is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libqaoa.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2606_26297_b300.build_lib`")
+_lib = ctypes.CDLL(LIB_PATH)
+
+QAOA_OK, QAOA_ERR_INVALID_ARG, QAOA_ERR_OUT_OF_MEMORY, QAOA_ERR_RANGE, QAOA_ERR_CUDA, \
+    QAOA_ERR_TIMEOUT, QAOA_ERR_ALLOCATION = range(7)
+QAOA_I32, QAOA_F32, QAOA_F64 = 0, 1, 2
+_DTYPES = {"i32": (QAOA_I32, np.int32), "f32": (QAOA_F32, np.float32), "f64": (QAOA_F64, np.float64)}
+
+
+class QaoaError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"status {status}: {msg}")
+        self.status = status
+
+
+class qaoa_qubo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("dtype", ctypes.c_int), ("H", ctypes.c_void_p),
+                ("f", ctypes.c_void_p), ("c0", ctypes.c_double)]
+
+
+class qaoa_options(ctypes.Structure):
+    _fields_ = [("adjoint_mode", ctypes.c_int32), ("profile", ctypes.c_int32),
+                ("memory_budget", ctypes.c_int64), ("max_fused_qubits", ctypes.c_int32),
+                ("state_fp64", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_PD = ctypes.POINTER(ctypes.c_double)
+_PF = ctypes.POINTER(ctypes.c_float)
+_PU64 = ctypes.POINTER(ctypes.c_uint64)
+_PI64 = ctypes.POINTER(ctypes.c_int64)
+_PI32 = ctypes.POINTER(ctypes.c_int32)
+
+_SIGS = {
+    "qaoa_ctx_create": ([_I, _P, ctypes.POINTER(qaoa_options), ctypes.POINTER(_P)], _I),
+    "qaoa_ctx_destroy": ([_P], None),
+    "qaoa_last_error": ([], ctypes.c_char_p),
+    "qaoa_build_cost": ([_P, ctypes.POINTER(qaoa_qubo), ctypes.POINTER(_P)], _I),
+    "qaoa_cost_destroy": ([_P], None),
+    "qaoa_cost_info": ([_P, _PI32, _PI32, _PI64, _PU64, _PD], _I),
+    "qaoa_cost_copy_to_host": ([_P, _P, _P], _I),
+    "qaoa_forward": ([_P, _P, _I, _PD, _PD, ctypes.POINTER(_P)], _I),
+    "qaoa_state_destroy": ([_P], None),
+    "qaoa_state_copy_to_host": ([_P, _P, _P], _I),
+    "qaoa_state_device_ptr": ([_P, ctypes.POINTER(_P), _PI64], _I),
+    "qaoa_expect": ([_P, _P, _P, _PD], _I),
+    "qaoa_topk": ([_P, _P, _P, _I, _PU64, _PF, _PD, _PU64, _PD, _PF], _I),
+    "qaoa_grad": ([_P, _P, _I, _PD, _PD, _PD, _PD, _PD, _I, _PU64, _PF], _I),
+    "qaoa_grad_batch": ([_P, _I, ctypes.POINTER(_P), _PI32, _I, _I, _PD, _PD, _PD, _PD, _PD], _I),
+    "qaoa_partition": ([_I, _I, _PI32, _PI32, _PI32], _I),
+    "qaoa_classify": ([_P, _PI32, _I, _PI64, _PI64, _PI64, _PI64], _I),
+    "qaoa_check_factorisation": ([_P, _P, _PI32, _D, _PI64, _PD], _I),
+    "qaoa_profile_read": ([_P, _I, _PI64, _PD, _PD, _I], _I),
+}
+for _name, (_args, _res) in _SIGS.items():
+    _fn = getattr(_lib, _name)
+    _fn.argtypes = _args
+    _fn.restype = _res
+
+
+def _check(status: int) -> None:
+    if status != QAOA_OK:
+        raise QaoaError(status, _lib.qaoa_last_error().decode())
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(_PD)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(-1))
+
+
+def qaoa_last_error() -> str:
+    return _lib.qaoa_last_error().decode()
+
+
+# ---- context ---------------------------------------------------------------------
+
+def qaoa_ctx_create(device: int = 0, stream: int | None = None, profile: bool = False,
+                    memory_budget: int = 0, max_fused_qubits: int = 0, state_fp64: bool = False):
+    """Create a context; `stream` is a raw cudaStream_t (e.g. torch's
+    `torch.cuda.current_stream().cuda_stream`), None for the default stream."""
+    opt = qaoa_options()
+    opt.profile = int(profile)
+    opt.memory_budget = int(memory_budget)
+    opt.max_fused_qubits = int(max_fused_qubits)
+    opt.state_fp64 = int(state_fp64)
+    out = _P()
+    _check(_lib.qaoa_ctx_create(int(device), _P(stream or 0), ctypes.byref(opt), ctypes.byref(out)))
+    return out
+
+
+def qaoa_ctx_destroy(ctx) -> None:
+    _lib.qaoa_ctx_destroy(ctx)
+
+
+# ---- objective table ---------------------------------------------------------------
+
+def make_qubo(H, f=None, c0: float = 0.0, dtype: str = "f64"):
+    """Build a qaoa_qubo struct (Sec. 2.1 input form) plus the arrays it points
+    to (keep the returned tuple alive for the duration of the call)."""
+    code, npt = _DTYPES[dtype]
+    Hc = np.ascontiguousarray(np.asarray(H).astype(npt))
+    n = Hc.shape[0]
+    fc = None if f is None else np.ascontiguousarray(np.asarray(f).astype(npt))
+    q = qaoa_qubo(n, code, Hc.ctypes.data, 0 if fc is None else fc.ctypes.data, float(c0))
+    return q, (Hc, fc)
+
+
+def qaoa_build_cost(ctx, H, f=None, c0: float = 0.0, dtype: str = "f64"):
+    q, keep = make_qubo(H, f, c0, dtype)
+    out = _P()
+    _check(_lib.qaoa_build_cost(ctx, ctypes.byref(q), ctypes.byref(out)))
+    del keep
+    return out
+
+
+def qaoa_cost_destroy(cost) -> None:
+    _lib.qaoa_cost_destroy(cost)
+
+
+def qaoa_cost_info(cost) -> dict:
+    n, s = ctypes.c_int32(), ctypes.c_int32()
+    kc = ctypes.c_int64()
+    am = ctypes.c_uint64()
+    mc = ctypes.c_double()
+    _check(_lib.qaoa_cost_info(cost, ctypes.byref(n), ctypes.byref(s), ctypes.byref(kc), ctypes.byref(am),
+                               ctypes.byref(mc)))
+    return {"n": n.value, "shift_bits": s.value, "k_c": kc.value, "argmin": am.value, "min_cost": mc.value}
+
+
+def qaoa_cost_copy_to_host(ctx, cost, n: int) -> np.ndarray:
+    out = np.empty(1 << n, dtype=np.int32)
+    _check(_lib.qaoa_cost_copy_to_host(ctx, cost, out.ctypes.data))
+    return out
+
+
+# ---- forward --------------------------------------------------------------------------
+
+def qaoa_forward(ctx, cost, gamma, beta, state=None):
+    g, b = _f64(gamma), _f64(beta)
+    assert g.shape == b.shape
+    st = _P(state.value if isinstance(state, _P) else (state or 0))
+    _check(_lib.qaoa_forward(ctx, cost, g.shape[0], _dptr(g), _dptr(b), ctypes.byref(st)))
+    return st
+
+
+def qaoa_state_destroy(state) -> None:
+    _lib.qaoa_state_destroy(state)
+
+
+def qaoa_state_copy_to_host(ctx, state, n: int, fp64: bool = False) -> np.ndarray:
+    out = np.empty(1 << n, dtype=np.complex128 if fp64 else np.complex64)
+    _check(_lib.qaoa_state_copy_to_host(ctx, state, out.ctypes.data))
+    return out
+
+
+def qaoa_state_device_ptr(state):
+    p = _P()
+    cnt = ctypes.c_int64()
+    _check(_lib.qaoa_state_device_ptr(state, ctypes.byref(p), ctypes.byref(cnt)))
+    return p.value, cnt.value
+
+
+def qaoa_expect(ctx, cost, state) -> float:
+    e = ctypes.c_double()
+    _check(_lib.qaoa_expect(ctx, cost, state, ctypes.byref(e)))
+    return e.value
+
+
+def qaoa_topk(ctx, cost, state, k: int):
+    idx = np.zeros(k, dtype=np.uint64)
+    prob = np.zeros(k, dtype=np.float32)
+    cst = np.zeros(k, dtype=np.float64)
+    am = ctypes.c_uint64()
+    mc = ctypes.c_double()
+    pam = ctypes.c_float()
+    _check(_lib.qaoa_topk(ctx, cost, state, int(k), idx.ctypes.data_as(_PU64), prob.ctypes.data_as(_PF),
+                          _dptr(cst), ctypes.byref(am), ctypes.byref(mc), ctypes.byref(pam)))
+    return {"idx": idx, "prob": prob, "cost": cst, "argmin": am.value, "min_cost": mc.value,
+            "prob_argmin": pam.value}
+
+
+# ---- gradient ---------------------------------------------------------------------------
+
+def qaoa_grad(ctx, cost, gamma, beta, k_top: int = 0):
+    """(E, dE/dgamma, dE/dbeta[, top-K indices, probabilities])."""
+    g, b = _f64(gamma), _f64(beta)
+    p = g.shape[0]
+    dg = np.zeros(p)
+    db = np.zeros(p)
+    e = ctypes.c_double()
+    ti = np.zeros(max(k_top, 1), dtype=np.uint64)
+    tp = np.zeros(max(k_top, 1), dtype=np.float32)
+    _check(_lib.qaoa_grad(ctx, cost, p, _dptr(g), _dptr(b), ctypes.byref(e), _dptr(dg), _dptr(db), int(k_top),
+                          ti.ctypes.data_as(_PU64), tp.ctypes.data_as(_PF)))
+    if k_top:
+        return e.value, dg, db, ti[:k_top], tp[:k_top]
+    return e.value, dg, db
+
+
+def qaoa_grad_batch(ctx, costs, gamma, beta, item_cost=None, grad: bool = True):
+    """Batched evaluation: gamma, beta of shape (B, p)."""
+    g = np.ascontiguousarray(np.asarray(gamma, dtype=np.float64))
+    b = np.ascontiguousarray(np.asarray(beta, dtype=np.float64))
+    B, p = g.shape
+    arr = (_P * len(costs))(*[c.value if isinstance(c, _P) else c for c in costs])
+    ic = None if item_cost is None else np.ascontiguousarray(np.asarray(item_cost, dtype=np.int32))
+    E = np.zeros(B)
+    dg = np.zeros((B, p)) if grad else None
+    db = np.zeros((B, p)) if grad else None
+    _check(_lib.qaoa_grad_batch(ctx, len(costs), arr, None if ic is None else ic.ctypes.data_as(_PI32), B, p,
+                                _dptr(g), _dptr(b), _dptr(E), None if dg is None else _dptr(dg),
+                                None if db is None else _dptr(db)))
+    return (E, dg, db) if grad else E
+
+
+# ---- DQAOA ----------------------------------------------------------------------------------
+
+def qaoa_partition(n: int, M: int, caps=None, manual=None) -> np.ndarray:
+    out = np.zeros(n, dtype=np.int32)
+    c = None if caps is None else np.ascontiguousarray(np.asarray(caps, dtype=np.int32))
+    m = None if manual is None else np.ascontiguousarray(np.asarray(manual, dtype=np.int32))
+    _check(_lib.qaoa_partition(int(n), int(M), None if c is None else c.ctypes.data_as(_PI32),
+                               None if m is None else m.ctypes.data_as(_PI32), out.ctypes.data_as(_PI32)))
+    return out
+
+
+def qaoa_classify(cost, qpu_of, p: int):
+    q = np.ascontiguousarray(np.asarray(qpu_of, dtype=np.int32))
+    a, b, c, d = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(_lib.qaoa_classify(cost, q.ctypes.data_as(_PI32), int(p), ctypes.byref(a), ctypes.byref(b),
+                              ctypes.byref(c), ctypes.byref(d)))
+    return {"local": a.value, "cross": b.value, "remote_cx": c.value, "cross_all_pairs": d.value}
+
+
+def qaoa_check_factorisation(ctx, cost, qpu_of, gamma_probe: float = 0.7):
+    q = np.ascontiguousarray(np.asarray(qpu_of, dtype=np.int32))
+    mm = ctypes.c_int64()
+    pe = ctypes.c_double()
+    _check(_lib.qaoa_check_factorisation(ctx, cost, q.ctypes.data_as(_PI32), float(gamma_probe), ctypes.byref(mm),
+                                         ctypes.byref(pe)))
+    return mm.value, pe.value
+
+
+def qaoa_profile_read(ctx, kind: int, reset: bool = False):
+    n = ctypes.c_int64()
+    ms, by = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.qaoa_profile_read(ctx, int(kind), ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by), int(reset)))
+    return {"launches": n.value, "ms": ms.value, "bytes": by.value}
+
+
+PROFILE_KINDS = {"fwd_pass": 0, "rev_pass": 1, "cost_build": 2, "small_resident": 3, "factorisation": 4}
+
+
+def bitstring(x: int, n: int) -> str:
+    """Logical QUBO bitstring z_1..z_n of basis index x (Sec. 3.6): bit i of x
+    is z_{i+1}, printed first to last."""
+    return "".join("1" if (int(x) >> i) & 1 else "0" for i in range(n))

@@ -1,0 +1,329 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+the same seeded inputs.
+
+Tolerances: integer work (objective tables, argmin, top-K indices, counts)
+bit-exact; complex64 amplitudes: L2 error <= 1e-5; expectation:
+|dE| / max|F| <= 1e-5; gradient: max_l |dg_l| / max(|g|_inf, 1e-12) <= 1e-4.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2606_26297_b300 import instances as inst
+
+pytestmark = pytest.mark.gpu
+
+AMP_TOL = 1e-5
+E_TOL = 1e-5
+G_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def q():
+    from paper_2606_26297_b300 import build_lib
+    build_lib.build()
+    from paper_2606_26297_b300 import qaoa
+    return qaoa
+
+
+@pytest.fixture(scope="module")
+def ctx(q):
+    c = q.qaoa_ctx_create(0)
+    yield c
+    q.qaoa_ctx_destroy(c)
+
+
+def _cost(q, ctx, Q):
+    return q.qaoa_build_cost(ctx, Q.H, Q.f, Q.c0, "i32" if Q.dtype == "i32" else "f32")
+
+
+def _table_error_bound(n, s):
+    return (1 + n + n * (n - 1) / 2) * 2.0 ** (-(s + 1))
+
+
+# ---- objective table ---------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [1, 2, 5, 12, 13, 14, 17, 20])
+def test_cost_table_integer_bitexact(q, ctx, n):
+    Q = inst.upper_int_qubo(n, 500 + n)
+    cost = _cost(q, ctx, Q)
+    info = q.qaoa_cost_info(cost)
+    T = q.qaoa_cost_copy_to_host(ctx, cost, n).astype(np.int64)
+    F = oracle.cost_table(oracle.canonical_of(Q))
+    assert info["shift_bits"] == 0
+    assert np.array_equal(T + info["k_c"], F.astype(np.int64))
+    assert info["argmin"] == oracle.argmin(F)
+    assert info["min_cost"] == F.min()
+    q.qaoa_cost_destroy(cost)
+
+
+def test_cost_table_nonsymmetric_input(q, ctx):
+    """H with both triangles and f and c0: canonicalisation (Sec. 2.1)."""
+    rng = inst.SplitMix64(4)
+    n = 13
+    H = np.array([[rng.randint(-7, 7) for _ in range(n)] for _ in range(n)], dtype=float)
+    f = np.array([rng.randint(-7, 7) for _ in range(n)], dtype=float)
+    cost = q.qaoa_build_cost(ctx, H, f, 5.0, "i32")
+    info = q.qaoa_cost_info(cost)
+    T = q.qaoa_cost_copy_to_host(ctx, cost, n).astype(np.int64)
+    F = oracle.cost_table(oracle.canonicalize(H, f, 5.0))
+    assert np.array_equal(T + info["k_c"], F.astype(np.int64))
+    q.qaoa_cost_destroy(cost)
+
+
+@pytest.mark.parametrize("maker,n", [(inst.normal_qubo, 14), (inst.unit_commitment_qubo, 16)])
+def test_cost_table_real_within_bound(q, ctx, maker, n):
+    Q = maker(n, 600 + n)
+    cost = _cost(q, ctx, Q)
+    info = q.qaoa_cost_info(cost)
+    T = q.qaoa_cost_copy_to_host(ctx, cost, n).astype(np.float64)
+    Fg = (T + info["k_c"]) * 2.0 ** (-info["shift_bits"])
+    F = oracle.cost_table(oracle.canonical_of(Q))
+    assert np.max(np.abs(Fg - F)) <= _table_error_bound(n, info["shift_bits"])
+    assert abs(F[info["argmin"]] - F.min()) <= 2 * _table_error_bound(n, info["shift_bits"])
+    q.qaoa_cost_destroy(cost)
+
+
+# ---- forward state -------------------------------------------------------------------
+
+FWD_CASES = [
+    (4, 1, "int"), (9, 2, "normal"), (12, 2, "int"),             # shared-memory resident path
+    (13, 1, "int"), (13, 3, "normal"), (14, 2, "int"), (16, 3, "normal"),
+    (18, 2, "maxcut"), (20, 3, "int"), (21, 2, "normal"), (23, 4, "int"),   # layer-pass path
+]
+
+
+def _instance(kind, n, seed):
+    if kind == "int":
+        return inst.upper_int_qubo(n, seed)
+    if kind == "normal":
+        return inst.normal_qubo(n, seed)
+    return inst.regular_maxcut_qubo(n, seed)
+
+
+def _angles(Q, p, kind):
+    scale = 1.0 if kind != "normal" else math.sqrt(Q.n) / inst.coefficient_norm(Q)
+    if kind == "int":
+        scale = 0.15
+    return inst.ramp_angles(p, gamma_scale=scale)
+
+
+@pytest.mark.parametrize("n,p,kind", FWD_CASES)
+def test_forward_amplitudes_and_expectation(q, ctx, n, p, kind):
+    Q = _instance(kind, n, 700 + n + p)
+    g, b = _angles(Q, p, kind)
+    cost = _cost(q, ctx, Q)
+    st = q.qaoa_forward(ctx, cost, g, b)
+    psi = q.qaoa_state_copy_to_host(ctx, st, n).astype(np.complex128)
+    F = oracle.cost_table(oracle.canonical_of(Q))
+    ref = oracle.evolve(F, g, b)
+    assert np.linalg.norm(psi - ref) <= AMP_TOL
+    E = q.qaoa_expect(ctx, cost, st)
+    assert abs(E - oracle.expectation(F, ref)) / np.max(np.abs(F)) <= E_TOL
+    q.qaoa_state_destroy(st)
+    q.qaoa_cost_destroy(cost)
+
+
+def test_forward_fp64_state_small(q):
+    """n=12, p=2 with a complex128 state (the dense integer n=12 workload)."""
+    c = q.qaoa_ctx_create(0, state_fp64=True)
+    Q, g, b = inst.workload_small_int()
+    cost = _cost(q, c, Q)
+    st = q.qaoa_forward(c, cost, g, b)
+    psi = q.qaoa_state_copy_to_host(c, st, 12, fp64=True)
+    F = oracle.cost_table(oracle.canonical_of(Q))
+    ref = oracle.evolve(F, g, b)
+    assert np.linalg.norm(psi - ref) <= 1e-12
+    E, dg, db = q.qaoa_grad(c, cost, g, b)
+    Eo, dgo, dbo = oracle.grad_adjoint(F, g, b)
+    assert abs(E - Eo) <= 1e-10 * np.max(np.abs(F))
+    sc = max(np.max(np.abs(dgo)), np.max(np.abs(dbo)))
+    assert max(np.max(np.abs(dg - dgo)), np.max(np.abs(db - dbo))) <= 1e-9 * sc
+    q.qaoa_state_destroy(st)
+    q.qaoa_cost_destroy(cost)
+    q.qaoa_ctx_destroy(c)
+
+
+def test_p0_is_uniform(q, ctx):
+    for n in (5, 15):
+        Q = inst.upper_int_qubo(n, 3)
+        cost = _cost(q, ctx, Q)
+        st = q.qaoa_forward(ctx, cost, [], [])
+        psi = q.qaoa_state_copy_to_host(ctx, st, n)
+        assert np.max(np.abs(psi - 2.0 ** (-n / 2))) < 1e-7
+        F = oracle.cost_table(oracle.canonical_of(Q))
+        assert abs(q.qaoa_expect(ctx, cost, st) - F.mean()) <= E_TOL * np.max(np.abs(F))
+        q.qaoa_state_destroy(st)
+        q.qaoa_cost_destroy(cost)
+
+
+def test_gamma_zero_global_phase(q, ctx):
+    n = 16
+    Q = inst.normal_qubo(n, 9)
+    cost = _cost(q, ctx, Q)
+    beta = [0.3, 1.1, -0.7]
+    st = q.qaoa_forward(ctx, cost, [0.0, 0.0, 0.0], beta)
+    psi = q.qaoa_state_copy_to_host(ctx, st, n).astype(np.complex128)
+    ref = np.exp(-1j * n * sum(beta)) * 2.0 ** (-n / 2)
+    assert np.linalg.norm(psi - ref) <= AMP_TOL
+    q.qaoa_state_destroy(st)
+    q.qaoa_cost_destroy(cost)
+
+
+# ---- gradient ----------------------------------------------------------------------------
+
+GRAD_CASES = [(8, 2, "int"), (12, 3, "normal"), (13, 1, "int"), (13, 2, "normal"), (14, 3, "maxcut"),
+              (16, 4, "int"), (18, 2, "normal"), (21, 3, "int"), (22, 2, "normal")]
+
+
+@pytest.mark.parametrize("n,p,kind", GRAD_CASES)
+def test_gradient_vs_oracle(q, ctx, n, p, kind):
+    Q = _instance(kind, n, 800 + n + p)
+    g, b = _angles(Q, p, kind)
+    cost = _cost(q, ctx, Q)
+    E, dg, db = q.qaoa_grad(ctx, cost, g, b)
+    F = oracle.cost_table(oracle.canonical_of(Q))
+    Eo, dgo, dbo = oracle.grad_adjoint(F, g, b)
+    assert abs(E - Eo) / np.max(np.abs(F)) <= E_TOL
+    sc = max(np.max(np.abs(dgo)), np.max(np.abs(dbo)), 1e-12)
+    err = max(np.max(np.abs(dg - dgo)), np.max(np.abs(db - dbo))) / sc
+    assert err <= G_TOL, (err, dg, dgo, db, dbo)
+    q.qaoa_cost_destroy(cost)
+
+
+def test_gradient_special_cases(q, ctx):
+    Q = inst.upper_int_qubo(15, 41)
+    cost = _cost(q, ctx, Q)
+    _, dg, db = q.qaoa_grad(ctx, cost, [0.0, 0.0], [0.4, 1.2])
+    assert np.max(np.abs(db)) < 1e-4
+    _, dg, db = q.qaoa_grad(ctx, cost, [0.05, 0.09], [0.0, 0.0])
+    assert np.max(np.abs(dg)) < 1e-4 * max(1.0, np.max(np.abs(q.qaoa_grad(ctx, cost, [0.05, 0.09], [0.3, 0.2])[1])))
+    q.qaoa_cost_destroy(cost)
+
+
+def test_grad_deterministic(q, ctx):
+    Q = inst.normal_qubo(19, 5)
+    g, b = _angles(Q, 3, "normal")
+    cost = _cost(q, ctx, Q)
+    r1 = q.qaoa_grad(ctx, cost, g, b, k_top=8)
+    r2 = q.qaoa_grad(ctx, cost, g, b, k_top=8)
+    assert r1[0] == r2[0]
+    assert np.array_equal(r1[1], r2[1]) and np.array_equal(r1[2], r2[2])
+    assert np.array_equal(r1[3], r2[3]) and np.array_equal(r1[4], r2[4])
+    q.qaoa_cost_destroy(cost)
+
+
+# ---- top-K -------------------------------------------------------------------------------
+
+def _cpu_topk(P, k):
+    return np.lexsort((np.arange(P.shape[0]), -P))[:k]
+
+
+@pytest.mark.parametrize("n,k", [(10, 8), (14, 10), (17, 16), (20, 64)])
+def test_topk_bitexact_on_gpu_probabilities(q, ctx, n, k):
+    Q = inst.upper_int_qubo(n, 900 + n)
+    g, b = _angles(Q, 2, "int")
+    cost = _cost(q, ctx, Q)
+    st = q.qaoa_forward(ctx, cost, g, b)
+    psi = q.qaoa_state_copy_to_host(ctx, st, n)
+    res = q.qaoa_topk(ctx, cost, st, k)
+    # bit-exact against a CPU selection on the GPU's own probabilities (same FP32 key)
+    ref = _cpu_topk(res_prob_array(psi), k)
+    assert list(res["idx"]) == list(ref)
+    # against the oracle: equal as tie groups (probabilities within 1e-6 max P)
+    F = oracle.cost_table(oracle.canonical_of(Q))
+    Po = oracle.probabilities(oracle.evolve(F, g, b))
+    thr = 1e-6 * Po.max()
+    kth = np.sort(Po)[::-1][k - 1]
+    for x in res["idx"]:
+        assert Po[x] >= kth - thr
+    assert res["argmin"] == oracle.argmin(F)
+    assert np.allclose(res["cost"], F[res["idx"].astype(np.int64)])
+    q.qaoa_state_destroy(st)
+    q.qaoa_cost_destroy(cost)
+
+
+def res_prob_array(psi):
+    """|psi|^2 as the kernels form it: fmaf(re, re, im*im) in FP32 (the
+    product re*re is exact in extended precision, then one rounding)."""
+    re = psi.real.astype(np.float32)
+    im = psi.imag.astype(np.float32)
+    im2 = (im * im).astype(np.float32)
+    return (re.astype(np.longdouble) * re.astype(np.longdouble) + im2.astype(np.longdouble)).astype(np.float32)
+
+
+def test_fused_topk_matches_state_topk(q, ctx):
+    n = 18
+    Q = inst.regular_maxcut_qubo(n, 12)
+    g, b = inst.ramp_angles(3)
+    cost = _cost(q, ctx, Q)
+    _, _, _, ti, tp = q.qaoa_grad(ctx, cost, g, b, k_top=10)
+    st = q.qaoa_forward(ctx, cost, g, b)
+    res = q.qaoa_topk(ctx, cost, st, 10)
+    F = oracle.cost_table(oracle.canonical_of(Q))
+    Po = oracle.probabilities(oracle.evolve(F, g, b))
+    kth = np.sort(Po)[::-1][9]
+    for x in ti:
+        assert Po[x] >= kth - 1e-6 * Po.max()
+    assert np.allclose(tp, res["prob"], rtol=1e-4, atol=1e-9)
+    q.qaoa_state_destroy(st)
+    q.qaoa_cost_destroy(cost)
+
+
+# ---- DQAOA ---------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("maker,n,M", [(inst.upper_int_qubo, 16, 3), (inst.normal_qubo, 15, 4),
+                                      (inst.unit_commitment_qubo, 14, 2)])
+def test_factorisation_check(q, ctx, maker, n, M):
+    Q = maker(n, 1100 + n)
+    cost = _cost(q, ctx, Q)
+    qpu_of = q.qaoa_partition(n, M)
+    mism, perr = q.qaoa_check_factorisation(ctx, cost, qpu_of, 0.8)
+    assert mism == 0
+    assert perr < 1e-5
+    loc = q.qaoa_classify(cost, qpu_of, 5)
+    assert (loc["local"], loc["cross"], loc["remote_cx"]) == oracle.classify(oracle.canonical_of(Q), list(qpu_of), 5)
+    q.qaoa_cost_destroy(cost)
+
+
+def test_dense30_partition_counts_through_abi(q, ctx):
+    """Dense n=30 (N(0,1) couplings), caps [10,10,10] contiguous: 135 local,
+    300 cross, 4800 remote CX at p=8 (Sec. 3.1).  Uses a small n=30 handle."""
+    Q = inst.normal_qubo(30, 1003)
+    cost = _cost(q, ctx, Q)
+    qpu_of = q.qaoa_partition(30, 3, caps=[10, 10, 10])
+    r = q.qaoa_classify(cost, qpu_of, 8)
+    assert (r["local"], r["cross"], r["remote_cx"]) == (135, 300, 4800)
+    q.qaoa_cost_destroy(cost)
+
+
+# ---- boundary error paths ---------------------------------------------------------------------
+
+def test_error_paths(q, ctx):
+    Q = inst.upper_int_qubo(14, 1)
+    cost = _cost(q, ctx, Q)
+    with pytest.raises(q.QaoaError) as e:
+        q.qaoa_grad(ctx, cost, [], [])
+    assert e.value.status == q.QAOA_ERR_INVALID_ARG
+    with pytest.raises(q.QaoaError):
+        q.qaoa_grad(ctx, cost, [0.1], [float("nan")])
+    st = q.qaoa_forward(ctx, cost, [0.1], [0.2])
+    with pytest.raises(q.QaoaError):
+        q.qaoa_topk(ctx, cost, st, 0)
+    with pytest.raises(q.QaoaError):
+        q.qaoa_topk(ctx, cost, st, 65)
+    Q2 = inst.upper_int_qubo(15, 1)
+    cost2 = _cost(q, ctx, Q2)
+    with pytest.raises(q.QaoaError):
+        q.qaoa_expect(ctx, cost2, st)
+    with pytest.raises(q.QaoaError) as e:
+        q.qaoa_build_cost(ctx, np.zeros((34, 34)), None, 0.0, "f64")
+    assert e.value.status == q.QAOA_ERR_INVALID_ARG
+    with pytest.raises(q.QaoaError) as e:
+        q.qaoa_build_cost(ctx, np.full((3, 3), 2 ** 30), None, 0.0, "i32")
+    assert e.value.status == q.QAOA_ERR_RANGE
+    q.qaoa_state_destroy(st)
+    q.qaoa_cost_destroy(cost)
+    q.qaoa_cost_destroy(cost2)
