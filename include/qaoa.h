@@ -85,7 +85,9 @@ typedef struct {
     int64_t memory_budget;  /* bytes of device memory the context may hold; 0 = free memory */
     int32_t max_fused_qubits; /* qubits per mixer pass: 0 = default (10), else 3..10 */
     int32_t state_fp64;     /* 1: complex128 states and arithmetic (n <= 12 only) */
-    int32_t reserved[6];
+    int32_t pass_variant;   /* layer-pass kernels: 0 = default (TMA-pipelined persistent),
+                               1 = direct global loads, 2 = TMA-pipelined persistent */
+    int32_t reserved[5];
 } qaoa_options;
 
 typedef struct qaoa_ctx_s *qaoa_ctx;     /* device, stream, options, scratch, plan cache */
@@ -214,9 +216,10 @@ qaoa_status qaoa_check_factorisation(qaoa_ctx ctx, qaoa_cost cost, const int32_t
 /* With options.profile = 1, every kernel launch of the given kind is timed
  * with CUDA events on the context stream.  kind: 0 = forward mixer pass,
  * 1 = reverse (adjoint) pass, 2 = objective table build, 3 = small-n resident
- * kernel, 4 = factorisation check.  Returns launches, summed milliseconds and
- * summed algorithmic bytes (bytes the method must move) since the last reset;
- * reset = 1 clears the counters after reading. */
+ * kernel, 4 = factorisation check; kind 5 counts every kernel the context
+ * launched (timed or not; ms and bytes are 0).  Returns launches, summed
+ * milliseconds and summed algorithmic bytes (bytes the method must move) since
+ * the last reset; reset = 1 clears the counters after reading. */
 qaoa_status qaoa_profile_read(qaoa_ctx ctx, int kind, int64_t *launches, double *ms,
                               double *bytes, int reset);
 

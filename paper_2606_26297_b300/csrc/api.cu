@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "kernels_misc.h"
+#include "kernels_tma.h"
 #include "qaoa_internal.h"
 
 using namespace qaoa;
@@ -83,6 +84,9 @@ struct qaoa_ctx_s {
     int64_t prof_launches[5] = {0, 0, 0, 0, 0};
     double prof_ms[5] = {0, 0, 0, 0, 0};
     double prof_bytes[5] = {0, 0, 0, 0, 0};
+    int64_t launches_total = 0;  // every kernel launched by this context
+    int num_sms = 148;
+    DevBuf status;               // device status word of the bounded waits
 };
 
 struct qaoa_cost_s {
@@ -177,8 +181,8 @@ struct PassDesc {
     int la = -1, lc = -1, lb = -1;  // layers (0-based) of pre mixer, cost, post mixer
 };
 
-constexpr uint32_t REGS_X[2] = {0x0F8u, 0x3E0u};   // type 0: bits 3..7; type 1: bits 5..9
-constexpr uint32_t REGS_Y[2] = {0x307u, 0x1C18u};  // type 0: {0,1,2,8,9}; type 1: {3,4,10,11,12}
+constexpr uint32_t REGS_X[2] = {0x0F8u, 0x1C18u};  // type 0: bits 3..7; type 1: {3,4,10,11,12}
+constexpr uint32_t REGS_Y[2] = {0x307u, 0x3E0u};   // type 0: {0,1,2,8,9}; type 1: bits 5..9
 
 std::vector<Group> make_groups(int n, int maxq) {
     const int G = (n + maxq - 1) / maxq;
@@ -260,13 +264,14 @@ struct Mix {
 Mix mix_of(double beta) {
     Mix m{};
     const double c = std::cos(beta), s = std::sin(beta);
-    if (std::fabs(c) >= std::fabs(s)) {
-        m.op.mode = 1;
+    m.op.mode = 1;
+    if (std::fabs(c) >= std::fabs(s)) {  // RX(2 beta) = cos(beta) (1 - i tan(beta) X)
+        m.op.flip = 0;
         m.op.t = (float)(s / c);
         m.f = cd(c, 0.0);
-    } else {
-        m.op.mode = 2;
-        m.op.t = (float)(c / s);
+    } else {  // RX(2 beta) = -i X RX(2 beta - pi) = -i sin(beta) X (1 - i tan(beta - pi/2) X)
+        m.op.flip = 1;
+        m.op.t = (float)(-c / s);
         m.f = cd(0.0, -s);
     }
     return m;
@@ -489,6 +494,11 @@ qaoa_status run_passes(qaoa_ctx c, const qaoa_cost_s *cost, int p, const double 
     if (grad)
         for (int i = (int)sched.size() - 2; i >= 0; --i)
             runs.push_back(rev_args(groups[sched[i].group], sched[i], cost, gamma, beta, psi, lam, partials, p));
+    const bool use_tma = c->opt.pass_variant != 1;
+    if (use_tma) {
+        QAOA_TRY(c->status.ensure(16, &c->held, c->opt.memory_budget));
+        CUDA_TRY(cudaMemsetAsync(c->status.p, 0, 16, c->stream));
+    }
     int ns = 0;
     std::vector<int> sum_index(runs.size(), -1);
     for (size_t i = 0; i < runs.size(); ++i) {
@@ -496,27 +506,45 @@ qaoa_status run_passes(qaoa_ctx c, const qaoa_cost_s *cost, int p, const double 
         const bool rev = grad && i >= sched.size();
         {
             ProfScope ps(c, rev ? 1 : 0, r.bytes);
-            cudaError_t e = rev ? launch_rev_pass(r.type, r.args, c->stream)
-                                : launch_fwd_pass(r.type, r.epi, r.args, c->stream);
+            cudaError_t e;
+            if (use_tma)
+                e = rev ? launch_rev_tma(r.type, r.args, c->num_sms, c->status.as<unsigned int>(), c->stream)
+                        : launch_fwd_tma(r.type, r.epi, r.args, c->num_sms, c->status.as<unsigned int>(), c->stream);
+            else
+                e = rev ? launch_rev_pass(r.type, r.args, c->stream)
+                        : launch_fwd_pass(r.type, r.epi, r.args, c->stream);
+            c->launches_total += 1;
             if (e) return fail(QAOA_ERR_CUDA, "pass launch failed: %s", cudaGetErrorString(e));
         }
         if (r.has_partials) {
             CUDA_TRY(launch_reduce_partials(partials, nb, NSLOT, sums + (size_t)ns * NSLOT, c->stream));
+            c->launches_total += 1;
             sum_index[i] = ns++;
         }
     }
-    if (!grad) return QAOA_OK;
+    unsigned int hstatus = 0;
+    if (use_tma) CUDA_TRY(cudaMemcpyAsync(&hstatus, c->status.p, 4, cudaMemcpyDeviceToHost, c->stream));
+    if (!grad) {
+        if (use_tma) {
+            CUDA_TRY(cudaStreamSynchronize(c->stream));
+            if (hstatus) return fail(QAOA_ERR_TIMEOUT, "a bounded wait of a layer-pass kernel expired");
+        }
+        return QAOA_OK;
+    }
     std::vector<double> h((size_t)ns * NSLOT);
     std::vector<unsigned long long> keys(std::max(ktop, 1));
     if (ktop > 0) {
         int which = 0;
+        int nl = 0;
         CUDA_TRY(launch_topk_merge(c->topk_a.as<unsigned long long>(), nb, ktop,
-                                   c->topk_b.as<unsigned long long>(), &which, c->stream));
+                                   c->topk_b.as<unsigned long long>(), &which, &nl, c->stream));
+        c->launches_total += nl;
         const unsigned long long *src = which ? c->topk_b.as<unsigned long long>() : c->topk_a.as<unsigned long long>();
         CUDA_TRY(cudaMemcpyAsync(keys.data(), src, (size_t)ktop * 8, cudaMemcpyDeviceToHost, c->stream));
     }
     CUDA_TRY(cudaMemcpyAsync(h.data(), sums, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (hstatus) return fail(QAOA_ERR_TIMEOUT, "a bounded wait of a layer-pass kernel expired");
     const double cs = std::ldexp(1.0, -cost->fp.s);
     for (int l = 0; l < p; ++l) dg[l] = db[l] = 0.0;
     double S0 = 0, S1 = 0;
@@ -566,6 +594,7 @@ qaoa_status run_small(qaoa_ctx c, const std::vector<SmallItem> &items, bool fp64
     for (auto &it : items) bytes += std::ldexp(4.0, it.n);
     ProfScope ps(c, 3, bytes);
     CUDA_TRY(launch_small(c->items.as<SmallItem>(), (int)items.size(), max_n, fp64, grad, c->stream));
+    c->launches_total += 1;
     return QAOA_OK;
 }
 
@@ -598,6 +627,11 @@ qaoa_status qaoa_ctx_create(int device, void *cuda_stream, const qaoa_options *o
     c->device = device;
     c->stream = (cudaStream_t)cuda_stream;
     if (opt) c->opt = *opt;
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (c->opt.pass_variant < 0 || c->opt.pass_variant > 2) {
+        delete c;
+        return fail(QAOA_ERR_INVALID_ARG, "pass_variant must be 0, 1 or 2");
+    }
     if (c->opt.max_fused_qubits != 0 && (c->opt.max_fused_qubits < 3 || c->opt.max_fused_qubits > 10)) {
         delete c;
         return fail(QAOA_ERR_INVALID_ARG, "max_fused_qubits must be 0 or in [3, 10]");
@@ -659,6 +693,7 @@ qaoa_status qaoa_build_cost(qaoa_ctx c, const qaoa_qubo *q, qaoa_cost *out) {
     {
         ProfScope ps(c, 2, (double)N * 4.0);
         CUDA_TRY(launch_cost_build(a, &nb, c->stream));
+        c->launches_total += 2;
     }
     long long mv = 0;
     unsigned long long mi = 0;
@@ -772,6 +807,7 @@ qaoa_status qaoa_expect(qaoa_ctx c, qaoa_cost cost, qaoa_state s, double *out) {
     QAOA_TRY(c->partials.ensure((size_t)nb * NSLOT * 8, &c->held, c->opt.memory_budget));
     QAOA_TRY(c->pass_sums.ensure(NSLOT * 8 * 2, &c->held, c->opt.memory_budget));
     CUDA_TRY(launch_expect((const float2 *)s->amps, cost->T, n, c->partials.as<double>(), c->stream));
+    c->launches_total += 2;
     CUDA_TRY(launch_reduce_partials(c->partials.as<double>(), nb, NSLOT, c->pass_sums.as<double>(), c->stream));
     double h[NSLOT];
     CUDA_TRY(cudaMemcpyAsync(h, c->pass_sums.p, sizeof h, cudaMemcpyDeviceToHost, c->stream));
@@ -794,8 +830,10 @@ qaoa_status qaoa_topk(qaoa_ctx c, qaoa_cost cost, qaoa_state s, int k, uint64_t 
     QAOA_TRY(c->topk_b.ensure((size_t)((nb + 255) / 256 + 1) * k * 8 + 64, &c->held, c->opt.memory_budget));
     CUDA_TRY(launch_topk_chunks((const float2 *)s->amps, n, k, c->topk_a.as<unsigned long long>(), c->stream));
     int which = 0;
+    int nl = 0;
     CUDA_TRY(launch_topk_merge(c->topk_a.as<unsigned long long>(), nb, k, c->topk_b.as<unsigned long long>(), &which,
-                               c->stream));
+                               &nl, c->stream));
+    c->launches_total += 1 + nl;
     std::vector<unsigned long long> keys(k);
     const void *src = which ? c->topk_b.p : c->topk_a.p;
     CUDA_TRY(cudaMemcpyAsync(keys.data(), src, (size_t)k * 8, cudaMemcpyDeviceToHost, c->stream));
@@ -1027,10 +1065,17 @@ qaoa_status qaoa_check_factorisation(qaoa_ctx c, qaoa_cost cost, const int32_t *
     a.c_off = fp.c0_q - fp.k_c;
     a.k_c = fp.k_c;
     a.phi = phase_multiplier(gamma_probe, fp.s);
+    // contiguous: QPU indices start at 0 and never decrease, stepping by 0 or 1
+    a.contiguous = qpu_of[0] == 0 ? 1 : 0;
+    for (int i = 1; i < n; ++i)
+        if (qpu_of[i] != qpu_of[i - 1] && qpu_of[i] != qpu_of[i - 1] + 1) a.contiguous = 0;
+    a.c0 = (int)vars[0].size();
+    if (a.c0 > 12 || n - a.c0 > 31) a.contiguous = 0;
     CUDA_TRY(cudaGetLastError());
     {
         ProfScope ps(c, 4, std::ldexp(4.0, n));
         CUDA_TRY(launch_fact_check(a, c->stream));
+        c->launches_total += 1;
     }
     unsigned long long hres[2];
     CUDA_TRY(cudaMemcpyAsync(hres, res, 16, cudaMemcpyDeviceToHost, c->stream));
@@ -1046,8 +1091,15 @@ qaoa_status qaoa_check_factorisation(qaoa_ctx c, qaoa_cost cost, const int32_t *
 }
 
 qaoa_status qaoa_profile_read(qaoa_ctx c, int kind, int64_t *launches, double *ms, double *bytes, int reset) {
-    if (!c || kind < 0 || kind > 4) return fail(QAOA_ERR_INVALID_ARG, "bad context or kind");
+    if (!c || kind < 0 || kind > 5) return fail(QAOA_ERR_INVALID_ARG, "bad context or kind");
     QAOA_TRY(set_device(c->device));
+    if (kind == 5) {
+        if (launches) *launches = c->launches_total;
+        if (ms) *ms = 0.0;
+        if (bytes) *bytes = 0.0;
+        if (reset) c->launches_total = 0;
+        return QAOA_OK;
+    }
     drain_profile(c);
     if (launches) *launches = c->prof_launches[kind];
     if (ms) *ms = c->prof_ms[kind];

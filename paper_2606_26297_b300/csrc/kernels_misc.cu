@@ -8,64 +8,74 @@ namespace qaoa {
 
 // ---------------------------------------------------------------------------
 // objective table: T[x] = c_off + sum l_i z_i + sum_{i<j} b_ij z_i z_j (exact
-// int64, stored as int32).  x = x_lo | mid << nlo | top << (nlo+t); each
-// thread owns one (x_lo, top) and walks its 2^t mid values in Gray-code
-// order: flipping bit j changes F by +/-D_j with D_j = l_j + sum_{i!=j} b_ij z_i.
+// int64, stored as int32)
 // ---------------------------------------------------------------------------
 constexpr int MAXT = 8;
 
+// x = x_lo | x_mid << nlo | x_top << (nlo + t).  A thread owns one (x_lo,
+// x_top) and walks the 2^t values of x_mid in Gray-code order.  With the
+// objective split as
+//   F(x) = K(x_lo, x_top) + F_mid(x_mid) + sum_{j in mid} z_j W_j(x_lo, x_top),
+//   W_j = sum_{i not in mid} b_ij z_i,
+// flipping mid bit j changes the last sum by +/-W_j, F_mid (the objective of
+// the mid bits alone, shared by the CTA) is a table lookup, and K is fixed.
 __global__ void cost_build_kernel(CostBuildArgs a) {
-    extern __shared__ long long shc[];  // ell[n], bs[n*n] symmetric
-    const int n = a.n;
+    extern __shared__ long long shc[];  // ell[n], bs[n*n] (symmetric), fmid[2^t], wsh[t][blockDim]
+    const int n = a.n, nlo = a.nlo, t = a.t;
     long long *ell = shc;
     long long *bs = shc + n;
+    long long *fmid = bs + n * n;
+    long long *wsh = fmid + (1 << t);
     for (int k = threadIdx.x; k < n; k += blockDim.x) ell[k] = a.ell[k];
     for (int k = threadIdx.x; k < n * n; k += blockDim.x) {
         const int i = k / n, j = k % n;
         bs[k] = i < j ? a.b[k] : (j < i ? a.b[j * n + i] : 0);
     }
     __syncthreads();
-    const unsigned long long gt = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int nlo = a.nlo, t = a.t;
-    const unsigned long long xlo = gt & ((1ull << nlo) - 1ull), top = gt >> nlo;
-    unsigned long long x = xlo | (top << (nlo + t));
-    long long F = a.c_off;
-    for (int i = 0; i < n; ++i) {
-        if (!((x >> i) & 1ull)) continue;
-        F += ell[i];
-        for (int j = i + 1; j < n; ++j)
-            if ((x >> j) & 1ull) F += bs[i * n + j];
-    }
-    long long D[MAXT];
-#pragma unroll
-    for (int k = 0; k < MAXT; ++k) {
-        D[k] = 0;
-        if (k < t) {
-            const int j = nlo + k;
-            long long d = ell[j];
-            for (int i = 0; i < n; ++i)
-                if (i != j && ((x >> i) & 1ull)) d += bs[i * n + j];
-            D[k] = d;
+    // F_mid over the mid bits alone (linear + mid-mid couplings)
+    for (int u = threadIdx.x; u < (1 << t); u += blockDim.x) {
+        long long f = 0;
+        for (int k = 0; k < t; ++k) {
+            if (!((u >> k) & 1)) continue;
+            f += ell[nlo + k];
+            for (int k2 = k + 1; k2 < t; ++k2)
+                if ((u >> k2) & 1) f += bs[(nlo + k) * n + nlo + k2];
         }
+        fmid[u] = f;
     }
-    long long best = F;
-    unsigned long long bestx = x;
-    a.T[x] = (int32_t)F;
+    const unsigned long long gt = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned long long xlo = gt & ((1ull << nlo) - 1ull), top = gt >> nlo;
+    const unsigned long long x0 = xlo | (top << (nlo + t));
+    // K(x0): the objective of the fixed bits
+    long long K = a.c_off;
+    for (int i = 0; i < n; ++i) {
+        if (!((x0 >> i) & 1ull)) continue;
+        K += ell[i];
+        for (int j = i + 1; j < n; ++j)
+            if ((x0 >> j) & 1ull) K += bs[i * n + j];
+    }
+    for (int k = 0; k < t; ++k) {
+        const int j = nlo + k;
+        long long wj = 0;
+        for (int i = 0; i < n; ++i)
+            if (((x0 >> i) & 1ull)) wj += bs[i * n + j];
+        wsh[k * blockDim.x + threadIdx.x] = wj;
+    }
+    __syncthreads();
+    long long cross = 0;
+    unsigned mid = 0;
+    long long best = K + fmid[0];
+    unsigned long long bestx = x0;
+    a.T[x0] = (int32_t)best;
     const unsigned cnt = 1u << t;
     for (unsigned u = 1; u < cnt; ++u) {
         const int k = __ffs(u) - 1;
-        const int j = nlo + k;
-        const bool was = (x >> j) & 1ull;
-        long long dk = 0;
-#pragma unroll
-        for (int kk = 0; kk < MAXT; ++kk)
-            if (kk == k) dk = D[kk];
-        F += was ? -dk : dk;
-        const long long sgn = was ? -1 : 1;
-#pragma unroll
-        for (int kk = 0; kk < MAXT; ++kk)
-            if (kk < t && kk != k) D[kk] += sgn * bs[j * n + nlo + kk];
-        x ^= 1ull << j;
+        const long long wk = wsh[k * blockDim.x + threadIdx.x];
+        const bool was = (mid >> k) & 1u;
+        cross += was ? -wk : wk;
+        mid ^= 1u << k;
+        const long long F = K + fmid[mid] + cross;
+        const unsigned long long x = x0 | ((unsigned long long)mid << nlo);
         a.T[x] = (int32_t)F;
         if (F < best || (F == best && x < bestx)) {
             best = F;
@@ -133,7 +143,7 @@ cudaError_t launch_cost_build(CostBuildArgs a, int *nblocks_out, cudaStream_t st
     const unsigned long long threads = 1ull << (n - a.t);
     const int bs = threads < 256 ? (int)threads : 256;
     const unsigned long long grid = threads / bs;
-    const int smem = (n + n * n) * (int)sizeof(long long);
+    const int smem = (n + n * n + (1 << a.t) + a.t * bs) * (int)sizeof(long long);
     cost_build_kernel<<<(unsigned)grid, bs, smem, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e) return e;
@@ -524,8 +534,84 @@ __global__ void fact_check_kernel(FactArgs a) {
     }
 }
 
+// Contiguous allocation (QPU m owns bits [s_m, s_m + c_m)): a CTA fixes the
+// fields of QPUs 1..M-1 (its index), its threads walk QPU 0's field.  The
+// CTA-uniform part of the split (their local tables and their mutual cross
+// terms) is formed once; per x only QPU 0's table and its cross sum remain.
+__global__ void fact_check_contig_kernel(FactArgs a) {
+    __shared__ long long wrow[16];
+    __shared__ long long hi_part;
+    __shared__ unsigned long long cnt_sh;
+    __shared__ unsigned int err_sh;
+    __shared__ int qs[17];
+    if (threadIdx.x <= (unsigned)a.M) qs[threadIdx.x] = a.q_start[threadIdx.x];
+    if (threadIdx.x == 0) {
+        cnt_sh = 0;
+        err_sh = 0;
+    }
+    __syncthreads();
+    const int c0 = qs[1];
+    const unsigned long long hi = blockIdx.x;  // bits c0..n-1 of x
+    if (threadIdx.x < 32) {
+        // W[a] = sum over QPUs m' >= 1 of V_{0,m'}[u_m'][a]
+        for (int q = threadIdx.x; q < c0; q += 32) {
+            long long w = 0;
+            for (int m2 = 1; m2 < a.M; ++m2) {
+                const unsigned u2 = (unsigned)((hi >> (qs[m2] - c0)) & ((1u << (qs[m2 + 1] - qs[m2])) - 1u));
+                w += a.V[a.V_off[m2] + (size_t)u2 * c0 + q];
+            }
+            wrow[q] = w;
+        }
+        if (threadIdx.x == 0) {
+            long long h = a.c_off;
+            for (int m = 1; m < a.M; ++m) {
+                const int cm = qs[m + 1] - qs[m];
+                const unsigned um = (unsigned)((hi >> (qs[m] - c0)) & ((1u << cm) - 1u));
+                h += a.Ltab[a.L_off[m] + um];
+                for (int m2 = m + 1; m2 < a.M; ++m2) {
+                    const unsigned u2 = (unsigned)((hi >> (qs[m2] - c0)) & ((1u << (qs[m2 + 1] - qs[m2])) - 1u));
+                    const long long *Vrow = a.V + a.V_off[m * 16 + m2] + (size_t)u2 * cm;
+                    for (int q = 0; q < cm; ++q)
+                        if ((um >> q) & 1u) h += Vrow[q];
+                }
+            }
+            hi_part = h;
+        }
+    }
+    __syncthreads();
+    const long long H = hi_part;
+    unsigned long long bad = 0;
+    float maxerr = 0.f;
+    for (unsigned u0 = threadIdx.x; u0 < (1u << c0); u0 += blockDim.x) {
+        const unsigned long long x = (hi << c0) | u0;
+        long long cross = 0;
+        for (int q = 0; q < c0; ++q)
+            if ((u0 >> q) & 1u) cross += wrow[q];
+        const long long loc = H + a.Ltab[u0];
+        const int32_t tx = a.T[x];
+        if ((long long)tx != loc + cross) ++bad;
+        const float2 pf = phase_ll((long long)tx + a.k_c, a.phi, 0ull);
+        const float2 pl = phase_ll(loc + a.k_c, a.phi, 0ull);
+        const float2 pc = phase_ll(cross, a.phi, 0ull);
+        const float2 pp = cmul(pl, pc);
+        maxerr = fmaxf(maxerr, fmaxf(fabsf(pf.x - pp.x), fabsf(pf.y - pp.y)));
+    }
+    atomicAdd(&cnt_sh, bad);
+    atomicMax(&err_sh, __float_as_uint(maxerr));
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        atomicAdd(a.mismatches, cnt_sh);
+        atomicMax(a.max_err_bits, err_sh);
+    }
+}
+
 cudaError_t launch_fact_check(const FactArgs &a, cudaStream_t st) {
-    fact_check_kernel<<<148 * 8, 256, 0, st>>>(a);
+    if (a.contiguous) {
+        const int c0 = a.c0;
+        fact_check_contig_kernel<<<(unsigned)(1ull << (a.n - c0)), 256, 0, st>>>(a);
+    } else {
+        fact_check_kernel<<<148 * 8, 256, 0, st>>>(a);
+    }
     return cudaGetLastError();
 }
 

@@ -59,6 +59,8 @@ struct FactArgs {
     unsigned long long phi;   // probe phase multiplier
     unsigned long long *mismatches;
     unsigned int *max_err_bits;
+    int contiguous;           // QPU m owns the contiguous bit range [q_start[m], q_start[m+1])
+    int c0;                   // size of QPU 0 (contiguous case)
 };
 cudaError_t launch_fact_check(const FactArgs &a, cudaStream_t st);
 

@@ -15,157 +15,9 @@
 // Reverse pass: undoes one forward pass on (psi, lambda) and accumulates
 // 2 Im<lambda| sum_j X_j |psi> (d/d beta) and 2 Im<lambda|H_C|psi> (d/d gamma)
 // as block partial sums.
-#include "pass_common.cuh"
+#include "pass_body.cuh"
 
 namespace qaoa {
-
-template <int T, int A>
-__device__ __forceinline__ size_t roff(int m, int lo) {
-    return goff<T>(local_idx<T, A>(0u, (uint32_t)m, 0u), lo);
-}
-
-template <int T, int A>
-__device__ __forceinline__ void load_arr(float2 (&v)[32], const float2 *__restrict__ p, uint32_t l,
-                                         uint32_t w, int lo) {
-    const float2 *q = p + goff<T>(local_idx<T, A>(l, 0u, w), lo);
-    if (T == 0 && A == 1) {  // runs of 8 contiguous amplitudes per thread
-#pragma unroll
-        for (int m = 0; m < 32; m += 2) {
-            const float4 t = *reinterpret_cast<const float4 *>(q + roff<T, A>(m, lo));
-            v[m] = make_float2(t.x, t.y);
-            v[m + 1] = make_float2(t.z, t.w);
-        }
-    } else {
-#pragma unroll
-        for (int m = 0; m < 32; ++m) v[m] = q[roff<T, A>(m, lo)];
-    }
-}
-
-template <int T, int A>
-__device__ __forceinline__ void store_arr(const float2 (&v)[32], float2 *__restrict__ p, uint32_t l,
-                                          uint32_t w, int lo) {
-    float2 *q = p + goff<T>(local_idx<T, A>(l, 0u, w), lo);
-    if (T == 0 && A == 1) {
-#pragma unroll
-        for (int m = 0; m < 32; m += 2)
-            __stcs(reinterpret_cast<float4 *>(q + roff<T, A>(m, lo)),
-                   make_float4(v[m].x, v[m].y, v[m + 1].x, v[m + 1].y));
-    } else {
-#pragma unroll
-        for (int m = 0; m < 32; ++m) __stcs(q + roff<T, A>(m, lo), v[m]);
-    }
-}
-
-template <int T, int A>
-__device__ __forceinline__ void load_cost(int32_t (&c)[32], const int32_t *__restrict__ p, uint32_t l,
-                                          uint32_t w, int lo) {
-    const int32_t *q = p + goff<T>(local_idx<T, A>(l, 0u, w), lo);
-    if (T == 0 && A == 1) {
-#pragma unroll
-        for (int m = 0; m < 32; m += 4) {
-            const int4 t = __ldg(reinterpret_cast<const int4 *>(q + roff<T, A>(m, lo)));
-            c[m] = t.x;
-            c[m + 1] = t.y;
-            c[m + 2] = t.z;
-            c[m + 3] = t.w;
-        }
-    } else {
-#pragma unroll
-        for (int m = 0; m < 32; ++m) c[m] = __ldg(q + roff<T, A>(m, lo));
-    }
-}
-
-// Transpose one state from arrangement A to arrangement B through shared memory.
-template <int T, int A, int B>
-__device__ __forceinline__ void transpose1(float2 (&v)[32], float2 *sm, uint32_t l, uint32_t w) {
-    __syncthreads();
-    const uint32_t ta = swz<T>(local_idx<T, A>(l, 0u, w));
-#pragma unroll
-    for (int m = 0; m < 32; ++m) sm[ta ^ swz<T>(local_idx<T, A>(0u, (uint32_t)m, 0u))] = v[m];
-    __syncthreads();
-    const uint32_t tb = swz<T>(local_idx<T, B>(l, 0u, w));
-#pragma unroll
-    for (int m = 0; m < 32; ++m) v[m] = sm[tb ^ swz<T>(local_idx<T, B>(0u, (uint32_t)m, 0u))];
-}
-
-template <int T, int A, int B>
-__device__ __forceinline__ void transpose2(float2 (&v)[32], float2 (&u)[32], float2 *sm, uint32_t l,
-                                           uint32_t w) {
-    __syncthreads();
-    const uint32_t ta = swz<T>(local_idx<T, A>(l, 0u, w));
-#pragma unroll
-    for (int m = 0; m < 32; ++m) {
-        const uint32_t s = ta ^ swz<T>(local_idx<T, A>(0u, (uint32_t)m, 0u));
-        sm[s] = v[m];
-        sm[s + 8192] = u[m];
-    }
-    __syncthreads();
-    const uint32_t tb = swz<T>(local_idx<T, B>(l, 0u, w));
-#pragma unroll
-    for (int m = 0; m < 32; ++m) {
-        const uint32_t s = tb ^ swz<T>(local_idx<T, B>(0u, (uint32_t)m, 0u));
-        v[m] = sm[s];
-        u[m] = sm[s + 8192];
-    }
-}
-
-// Top-K (K <= 16) of the block's |psi|^2 by key (P desc, index asc):
-// key = (bits(P) << 33) | (2^33 - 1 - x); keys are unique since x is.
-// Writes K keys to out (global), using smk (shared, >= 8*16 keys).
-template <int T, int A>
-__device__ __forceinline__ void block_topk(const float2 (&v)[32], size_t xthread, int lo, int K,
-                                           unsigned long long *out, unsigned long long *smk) {
-    const uint32_t l = threadIdx.x & 31, w = threadIdx.x >> 5;
-    uint32_t taken = 0;
-    unsigned long long bk = 0;
-    int bm = -1;
-    auto scan = [&]() {
-        bk = 0;
-        bm = -1;
-#pragma unroll
-        for (int m = 0; m < 32; ++m) {
-            if ((taken >> m) & 1u) continue;
-            const float P = fmaf(v[m].x, v[m].x, v[m].y * v[m].y);
-            const unsigned long long x = xthread + roff<T, A>(m, lo);
-            const unsigned long long key =
-                ((unsigned long long)__float_as_uint(P) << 33) | (0x1FFFFFFFFull - x);
-            if (key > bk) {
-                bk = key;
-                bm = m;
-            }
-        }
-    };
-    scan();
-    for (int r = 0; r < K; ++r) {
-        unsigned long long wb = bk;
-#pragma unroll
-        for (int o = 16; o; o >>= 1) {
-            const unsigned long long t = __shfl_xor_sync(0xffffffffu, wb, o);
-            wb = t > wb ? t : wb;
-        }
-        if (l == 0) smk[w * 16 + r] = wb;
-        if (bk == wb && bm >= 0) {
-            taken |= 1u << bm;
-            scan();
-        }
-    }
-    __syncthreads();
-    if (w == 0) {
-        // merge the 8 sorted warp lists: lane i (< 8) walks list i
-        int head = 0;
-        for (int r = 0; r < K; ++r) {
-            unsigned long long mine = (l < 8 && head < K) ? smk[l * 16 + head] : 0ull;
-            unsigned long long wb = mine;
-#pragma unroll
-            for (int o = 16; o; o >>= 1) {
-                const unsigned long long t = __shfl_xor_sync(0xffffffffu, wb, o);
-                wb = t > wb ? t : wb;
-            }
-            if (mine == wb && l < 8) ++head;
-            if (l == 0) out[r] = wb;
-        }
-    }
-}
 
 // ---------------------------------------------------------------------------
 // forward pass
@@ -192,7 +44,7 @@ __global__ void __launch_bounds__(PASS_THREADS, EPI ? 1 : 2) fwd_pass_kernel(con
     }
     if (pre) {
         round_mix<T, 0>(v, a.pre, a.mask);
-        transpose1<T, 0, 1>(v, sm, l, w);
+        transpose1<T, 0, 1>(v, sm, l, w, a.pre.flip ? a.mask : 0u);
         round_mix<T, 1>(v, a.pre, a.mask);
     }
     // arrangement Y
@@ -205,7 +57,7 @@ __global__ void __launch_bounds__(PASS_THREADS, EPI ? 1 : 2) fwd_pass_kernel(con
     if constexpr (!EPI) {
         if (a.post.mode) {
             round_mix<T, 1>(v, a.post, a.mask);
-            transpose1<T, 1, 0>(v, sm, l, w);
+            transpose1<T, 1, 0>(v, sm, l, w, a.post.flip ? a.mask : 0u);
             round_mix<T, 0>(v, a.post, a.mask);
             if (!a.has_cost) {
 #pragma unroll
@@ -242,10 +94,10 @@ __global__ void __launch_bounds__(PASS_THREADS, EPI ? 1 : 2) fwd_pass_kernel(con
             block_topk<T, 1>(v, xthread, a.lo, a.ktop, a.topk_keys + (size_t)blockIdx.x * a.ktop, smk);
         }
         const float x1 = xterm<T, 1>(u, v, a.mask);
-        const MixOp ip = {a.pre.mode, -a.pre.t};
+        const MixOp ip = {a.pre.mode, a.pre.flip, -a.pre.t};
         round_mix<T, 1>(u, ip, a.mask);
         round_mix<T, 1>(v, ip, a.mask);
-        transpose2<T, 1, 0>(v, u, sm, l, w);
+        transpose2<T, 1, 0>(v, u, sm, l, w, a.pre.flip ? a.mask : 0u);
         const float x0 = xterm<T, 0>(u, v, a.mask);
         round_mix<T, 0>(u, ip, a.mask);
 #pragma unroll
@@ -277,11 +129,11 @@ __global__ void __launch_bounds__(PASS_THREADS, 1) rev_pass_kernel(const PassArg
     if (post) {
         load_arr<T, 0>(v, pb, l, w, a.lo);
         load_arr<T, 0>(u, lb, l, w, a.lo);
-        const MixOp ib = {a.post.mode, -a.post.t};
+        const MixOp ib = {a.post.mode, a.post.flip, -a.post.t};
         acc[0] = xterm<T, 0>(u, v, a.mask);
         round_mix<T, 0>(v, ib, a.mask);
         round_mix<T, 0>(u, ib, a.mask);
-        transpose2<T, 0, 1>(v, u, sm, l, w);
+        transpose2<T, 0, 1>(v, u, sm, l, w, a.post.flip ? a.mask : 0u);
         acc[1] = xterm<T, 1>(u, v, a.mask);
         round_mix<T, 1>(v, ib, a.mask);
         round_mix<T, 1>(u, ib, a.mask);
@@ -304,11 +156,11 @@ __global__ void __launch_bounds__(PASS_THREADS, 1) rev_pass_kernel(const PassArg
         acc[2] = g;
     }
     if (pre) {
-        const MixOp ia = {a.pre.mode, -a.pre.t};
+        const MixOp ia = {a.pre.mode, a.pre.flip, -a.pre.t};
         acc[3] = xterm<T, 1>(u, v, a.mask);
         round_mix<T, 1>(v, ia, a.mask);
         round_mix<T, 1>(u, ia, a.mask);
-        transpose2<T, 1, 0>(v, u, sm, l, w);
+        transpose2<T, 1, 0>(v, u, sm, l, w, a.pre.flip ? a.mask : 0u);
         acc[4] = xterm<T, 0>(u, v, a.mask);
         round_mix<T, 0>(v, ia, a.mask);
         round_mix<T, 0>(u, ia, a.mask);
@@ -461,7 +313,8 @@ cudaError_t launch_reduce_partials(const double *partials, int nblocks, int nslo
 // together with `in` (which is overwritten).  The final list is left in
 // whichever buffer *nout points to: 0 = in, 1 = out.
 cudaError_t launch_topk_merge(const unsigned long long *in_c, int nlists, int k, unsigned long long *out,
-                              int *nout, cudaStream_t st) {
+                              int *nout, int *nlaunch, cudaStream_t st) {
+    *nlaunch = 0;
     unsigned long long *bufs[2] = {const_cast<unsigned long long *>(in_c), out};
     int cur = 0;
     while (nlists > 1) {
@@ -472,6 +325,7 @@ cudaError_t launch_topk_merge(const unsigned long long *in_c, int nlists, int k,
         if (e) return e;
         cur = 1 - cur;
         nlists = ctas;
+        ++*nlaunch;
     }
     *nout = cur;
     return cudaSuccess;

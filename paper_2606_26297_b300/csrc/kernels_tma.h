@@ -1,0 +1,19 @@
+// Launchers of the TMA-pipelined persistent layer-pass kernels.
+#pragma once
+
+#include <cstring>
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include "qaoa_internal.h"
+
+namespace qaoa {
+
+// grid: number of persistent CTAs (one per SM); status: device word set to a
+// non-zero value if a bounded wait timed out.
+cudaError_t launch_fwd_tma(int type, bool epi, const PassArgs &a, int grid, unsigned int *status, cudaStream_t st);
+cudaError_t launch_rev_tma(int type, const PassArgs &a, int grid, unsigned int *status, cudaStream_t st);
+
+}  // namespace qaoa

@@ -1,0 +1,189 @@
+// Register/shared-memory building blocks of a layer pass, shared by the
+// direct-load kernels (kernels_pass.cu) and the TMA-pipelined persistent
+// kernels (kernels_tma.cu).
+#pragma once
+
+#include "pass_common.cuh"
+
+namespace qaoa {
+
+template <int T, int A>
+__device__ __forceinline__ size_t roff(int m, int lo) {
+    return goff<T>(local_idx<T, A>(0u, (uint32_t)m, 0u), lo);
+}
+
+template <int T, int A>
+__device__ __forceinline__ void load_arr(float2 (&v)[32], const float2 *__restrict__ p, uint32_t l,
+                                         uint32_t w, int lo) {
+    const float2 *q = p + goff<T>(local_idx<T, A>(l, 0u, w), lo);
+    if (T == 0 && A == 1) {  // runs of 8 contiguous amplitudes per thread
+#pragma unroll
+        for (int m = 0; m < 32; m += 2) {
+            const float4 t = *reinterpret_cast<const float4 *>(q + roff<T, A>(m, lo));
+            v[m] = make_float2(t.x, t.y);
+            v[m + 1] = make_float2(t.z, t.w);
+        }
+    } else {
+#pragma unroll
+        for (int m = 0; m < 32; ++m) v[m] = q[roff<T, A>(m, lo)];
+    }
+}
+
+template <int T, int A>
+__device__ __forceinline__ void store_arr(const float2 (&v)[32], float2 *__restrict__ p, uint32_t l,
+                                          uint32_t w, int lo) {
+    float2 *q = p + goff<T>(local_idx<T, A>(l, 0u, w), lo);
+    if (T == 0 && A == 1) {
+#pragma unroll
+        for (int m = 0; m < 32; m += 2)
+            __stcs(reinterpret_cast<float4 *>(q + roff<T, A>(m, lo)),
+                   make_float4(v[m].x, v[m].y, v[m + 1].x, v[m + 1].y));
+    } else {
+#pragma unroll
+        for (int m = 0; m < 32; ++m) __stcs(q + roff<T, A>(m, lo), v[m]);
+    }
+}
+
+template <int T, int A>
+__device__ __forceinline__ void load_cost(int32_t (&c)[32], const int32_t *__restrict__ p, uint32_t l,
+                                          uint32_t w, int lo) {
+    const int32_t *q = p + goff<T>(local_idx<T, A>(l, 0u, w), lo);
+    if (T == 0 && A == 1) {
+#pragma unroll
+        for (int m = 0; m < 32; m += 4) {
+            const int4 t = __ldg(reinterpret_cast<const int4 *>(q + roff<T, A>(m, lo)));
+            c[m] = t.x;
+            c[m + 1] = t.y;
+            c[m + 2] = t.z;
+            c[m + 3] = t.w;
+        }
+    } else {
+#pragma unroll
+        for (int m = 0; m < 32; ++m) c[m] = __ldg(q + roff<T, A>(m, lo));
+    }
+}
+
+// Transpose one state from arrangement A to arrangement B through shared
+// memory.  fm: local-bit mask of a bit flip X applied on the way (the
+// amplitude of local index e lands at e ^ fm).
+template <int T, int A, int B>
+__device__ __forceinline__ void transpose1(float2 (&v)[32], float2 *sm, uint32_t l, uint32_t w, uint32_t fm) {
+    __syncthreads();
+    const uint32_t ta = swz<T>(local_idx<T, A>(l, 0u, w) ^ fm);
+#pragma unroll
+    for (int m = 0; m < 32; ++m) sm[ta ^ swz<T>(local_idx<T, A>(0u, (uint32_t)m, 0u))] = v[m];
+    __syncthreads();
+    const uint32_t tb = swz<T>(local_idx<T, B>(l, 0u, w));
+#pragma unroll
+    for (int m = 0; m < 32; ++m) v[m] = sm[tb ^ swz<T>(local_idx<T, B>(0u, (uint32_t)m, 0u))];
+}
+
+template <int T, int A, int B>
+__device__ __forceinline__ void transpose2(float2 (&v)[32], float2 (&u)[32], float2 *sm, uint32_t l,
+                                           uint32_t w, uint32_t fm) {
+    __syncthreads();
+    const uint32_t ta = swz<T>(local_idx<T, A>(l, 0u, w) ^ fm);
+#pragma unroll
+    for (int m = 0; m < 32; ++m) {
+        const uint32_t s = ta ^ swz<T>(local_idx<T, A>(0u, (uint32_t)m, 0u));
+        sm[s] = v[m];
+        sm[s + 8192] = u[m];
+    }
+    __syncthreads();
+    const uint32_t tb = swz<T>(local_idx<T, B>(l, 0u, w));
+#pragma unroll
+    for (int m = 0; m < 32; ++m) {
+        const uint32_t s = tb ^ swz<T>(local_idx<T, B>(0u, (uint32_t)m, 0u));
+        v[m] = sm[s];
+        u[m] = sm[s + 8192];
+    }
+}
+
+// Top-K (K <= 16) of the block's |psi|^2 by key (P desc, index asc):
+// key = (bits(P) << 33) | (2^33 - 1 - x); keys are unique since x is.
+// Writes K keys to out (global), using smk (shared, >= 8*16 keys).
+template <int T, int A>
+__device__ __forceinline__ void block_topk(const float2 (&v)[32], size_t xthread, int lo, int K,
+                                           unsigned long long *out, unsigned long long *smk) {
+    const uint32_t l = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t taken = 0;
+    unsigned long long bk = 0;
+    int bm = -1;
+    auto scan = [&]() {
+        bk = 0;
+        bm = -1;
+#pragma unroll
+        for (int m = 0; m < 32; ++m) {
+            if ((taken >> m) & 1u) continue;
+            const float P = fmaf(v[m].x, v[m].x, v[m].y * v[m].y);
+            const unsigned long long x = xthread + roff<T, A>(m, lo);
+            const unsigned long long key =
+                ((unsigned long long)__float_as_uint(P) << 33) | (0x1FFFFFFFFull - x);
+            if (key > bk) {
+                bk = key;
+                bm = m;
+            }
+        }
+    };
+    scan();
+    for (int r = 0; r < K; ++r) {
+        unsigned long long wb = bk;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            const unsigned long long t = __shfl_xor_sync(0xffffffffu, wb, o);
+            wb = t > wb ? t : wb;
+        }
+        if (l == 0) smk[w * 16 + r] = wb;
+        if (bk == wb && bm >= 0) {
+            taken |= 1u << bm;
+            scan();
+        }
+    }
+    __syncthreads();
+    if (w == 0) {
+        // merge the 8 sorted warp lists: lane i (< 8) walks list i
+        int head = 0;
+        for (int r = 0; r < K; ++r) {
+            unsigned long long mine = (l < 8 && head < K) ? smk[l * 16 + head] : 0ull;
+            unsigned long long wb = mine;
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                const unsigned long long t = __shfl_xor_sync(0xffffffffu, wb, o);
+                wb = t > wb ? t : wb;
+            }
+            if (mine == wb && l < 8) ++head;
+            if (l == 0) out[r] = wb;
+        }
+    }
+}
+
+// Read 32 amplitudes of arrangement A from a TMA-staged block (natural local
+// order, unswizzled).
+template <int T, int A>
+__device__ __forceinline__ void read_stage(float2 (&v)[32], const float2 *stage, uint32_t l, uint32_t w) {
+    const uint32_t t = local_idx<T, A>(l, 0u, w);
+#pragma unroll
+    for (int m = 0; m < 32; ++m) v[m] = stage[t | local_idx<T, A>(0u, (uint32_t)m, 0u)];
+}
+
+// Read the 32 table entries of arrangement A from a TMA-staged block of the
+// objective table (natural local order).
+template <int T, int A>
+__device__ __forceinline__ void read_cost_stage(int32_t (&c)[32], const int32_t *cst, uint32_t l, uint32_t w) {
+    const uint32_t t = local_idx<T, A>(l, 0u, w);
+    if (T == 0 && A == 1) {
+#pragma unroll
+        for (int m = 0; m < 32; m += 4) {
+            const int4 q = *reinterpret_cast<const int4 *>(cst + (t | local_idx<T, A>(0u, (uint32_t)m, 0u)));
+            c[m] = q.x;
+            c[m + 1] = q.y;
+            c[m + 2] = q.z;
+            c[m + 3] = q.w;
+        }
+    } else {
+#pragma unroll
+        for (int m = 0; m < 32; ++m) c[m] = cst[t | local_idx<T, A>(0u, (uint32_t)m, 0u)];
+    }
+}
+
+}  // namespace qaoa

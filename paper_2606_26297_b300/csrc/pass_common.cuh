@@ -20,26 +20,28 @@ namespace qaoa {
 // lane (5 bits), register slot m (5 bits) and warp (3 bits) select the local
 // index.  Butterflies act on the 5 register bits; a transpose through shared
 // memory swaps which local bits are register bits.
-//   type 0  X: lanes {0,1,2,8,9}  regs {3..7}        warps {10,11,12}
-//           Y: lanes {3..7}       regs {0,1,2,8,9}   warps {10,11,12}
-//   type 1  X: lanes {0..4}       regs {5..9}        warps {10,11,12}
-//           Y: lanes {0,1,2,5,6}  regs {3,4,10,11,12} warps {7,8,9}
-// Every arrangement keeps global bits 0..2 (or 0..4) in lanes or in a
-// thread-contiguous run, so global accesses stay in >= 64-byte segments.
+//   type 0  X: lanes {0,1,2,8,9}  regs {3..7}         warps {10,11,12}
+//           Y: lanes {3..7}       regs {0,1,2,8,9}    warps {10,11,12}
+//   type 1  X: lanes {0,1,2,5,6}  regs {3,4,10,11,12} warps {7,8,9}
+//           Y: lanes {0..4}       regs {5..9}         warps {10,11,12}
+// Every arrangement keeps global bits 0..2 in lanes or in a thread-contiguous
+// run, so global accesses stay in >= 64-byte segments; the cost phase is
+// applied in arrangement Y, where reading the staged table is conflict free
+// (type 1) or nearly so (type 0, 16-byte reads).
 // ---------------------------------------------------------------------------
 
 template <int T, int A>
 __device__ __forceinline__ constexpr int regbit(int i) {
     return T == 0 ? (A == 0 ? 3 + i : (i < 3 ? i : 5 + i))
-                  : (A == 0 ? 5 + i : (i < 2 ? 3 + i : 8 + i));
+                  : (A == 0 ? (i < 2 ? 3 + i : 8 + i) : 5 + i);
 }
 
 template <int T, int A>
 __device__ __forceinline__ constexpr uint32_t local_idx(uint32_t l, uint32_t m, uint32_t w) {
     return T == 0 ? (A == 0 ? ((l & 7u) | ((l >> 3) << 8) | (m << 3) | (w << 10))
                             : ((l << 3) | (m & 7u) | ((m >> 3) << 8) | (w << 10)))
-                  : (A == 0 ? (l | (m << 5) | (w << 10))
-                            : ((l & 7u) | ((l >> 3) << 5) | ((m & 3u) << 3) | ((m >> 2) << 10) | (w << 7)));
+                  : (A == 0 ? ((l & 7u) | ((l >> 3) << 5) | ((m & 3u) << 3) | ((m >> 2) << 10) | (w << 7))
+                            : (l | (m << 5) | (w << 10)));
 }
 
 // XOR swizzle of the shared-memory slot; linear over GF(2), and conflict free
@@ -71,19 +73,15 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 }
 __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 
-// RX(2 beta) pair update without its common factor.  Tangent form (mode 1):
+// RX(2 beta) pair update without its common factor, tangent form:
 // (a, b) <- (a - i t b, b - i t a); the true result is cos(beta) times this.
+// For |sin beta| > |cos beta| the host passes t = tan(beta - pi/2) and sets
+// MixOp.flip: RX(2 beta) = (-i X) RX(2 beta - pi) on every mixed qubit, and
+// the bit flip X of the whole group is applied for free by the transpose
+// inside the same mixer (an XOR of the shared-memory slot).
 __device__ __forceinline__ void bfly_tan(float2 &a, float2 &b, float t) {
     const float2 na = make_float2(fmaf(t, b.y, a.x), fmaf(-t, b.x, a.y));
     const float2 nb = make_float2(fmaf(t, a.y, b.x), fmaf(-t, a.x, b.y));
-    a = na;
-    b = nb;
-}
-// Cotangent form (mode 2): (a, b) <- (b + i u a, a + i u b); the true result
-// is -i sin(beta) times this.
-__device__ __forceinline__ void bfly_cot(float2 &a, float2 &b, float u) {
-    const float2 na = make_float2(fmaf(-u, a.y, b.x), fmaf(u, a.x, b.y));
-    const float2 nb = make_float2(fmaf(-u, b.y, a.x), fmaf(u, b.x, a.y));
     a = na;
     b = nb;
 }
@@ -91,22 +89,12 @@ __device__ __forceinline__ void bfly_cot(float2 &a, float2 &b, float u) {
 // One register round: the butterflies of every mixed register bit.
 template <int T, int A>
 __device__ __forceinline__ void round_mix(float2 (&v)[32], MixOp op, uint32_t mask) {
-    if (op.mode == 1) {
 #pragma unroll
-        for (int i = 0; i < 5; ++i) {
-            if (!((mask >> regbit<T, A>(i)) & 1u)) continue;
+    for (int i = 0; i < 5; ++i) {
+        if (!((mask >> regbit<T, A>(i)) & 1u)) continue;
 #pragma unroll
-            for (int m = 0; m < 32; ++m)
-                if (!(m & (1 << i))) bfly_tan(v[m], v[m | (1 << i)], op.t);
-        }
-    } else if (op.mode == 2) {
-#pragma unroll
-        for (int i = 0; i < 5; ++i) {
-            if (!((mask >> regbit<T, A>(i)) & 1u)) continue;
-#pragma unroll
-            for (int m = 0; m < 32; ++m)
-                if (!(m & (1 << i))) bfly_cot(v[m], v[m | (1 << i)], op.t);
-        }
+        for (int m = 0; m < 32; ++m)
+            if (!(m & (1 << i))) bfly_tan(v[m], v[m | (1 << i)], op.t);
     }
 }
 

@@ -52,12 +52,14 @@ void classify(const Canonical &c, const int32_t *qpu_of, int64_t *n_local, int64
 
 // ---- device-side argument blocks ---------------------------------------------
 
-// One mixer application: RX(2 beta) on every mixed qubit, as a butterfly in
-// tangent form (mode 1: pair (a,b) -> (a - i t b, b - i t a), t = tan beta,
-// common factor cos beta) or cotangent form (mode 2: (a,b) -> (b + i u a,
-// a + i u b), u = cot beta, common factor -i sin beta).  mode 0: no mixer.
+// One mixer application: RX(2 beta) on every mixed qubit, as the butterfly
+// (a, b) -> (a - i t b, b - i t a) with common factor cos(beta') where
+// beta' = beta (flip = 0, t = tan beta) or beta' = beta - pi/2 (flip = 1,
+// t = tan(beta - pi/2), followed by the group bit flip X and a factor -i).
+// mode 0: no mixer; 1: mixer present.
 struct MixOp {
     int mode;
+    int flip;
     float t;
 };
 
@@ -97,6 +99,6 @@ cudaError_t launch_rev_pass(int type, const PassArgs &a, cudaStream_t st);
 cudaError_t launch_reduce_partials(const double *partials, int nblocks, int nslot, double *out,
                                    cudaStream_t st);
 cudaError_t launch_topk_merge(const unsigned long long *in, int nlists, int k,
-                              unsigned long long *out, int *nout, cudaStream_t st);
+                              unsigned long long *out, int *nout, int *nlaunch, cudaStream_t st);
 
 }  // namespace qaoa

@@ -327,3 +327,41 @@ def test_error_paths(q, ctx):
     q.qaoa_state_destroy(st)
     q.qaoa_cost_destroy(cost)
     q.qaoa_cost_destroy(cost2)
+
+
+# ---- kernel variants -----------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,p,kind", [(13, 2, "normal"), (17, 3, "int"), (22, 2, "maxcut"), (26, 1, "normal")])
+def test_tma_and_direct_variants_bitwise_equal(q, n, p, kind):
+    """The TMA-pipelined persistent kernels and the direct-load kernels run the
+    same arithmetic; their results must agree bit for bit."""
+    Q = _instance(kind, n, 1200 + n)
+    g, b = _angles(Q, p, kind)
+    outs = []
+    for variant in (1, 2):
+        c = q.qaoa_ctx_create(0, pass_variant=variant)
+        cost = _cost(q, c, Q)
+        r = q.qaoa_grad(c, cost, g, b, k_top=8)
+        st = q.qaoa_forward(c, cost, g, b)
+        psi = q.qaoa_state_copy_to_host(c, st, n)
+        outs.append((r, psi))
+        q.qaoa_state_destroy(st)
+        q.qaoa_cost_destroy(cost)
+        q.qaoa_ctx_destroy(c)
+    (r1, s1), (r2, s2) = outs
+    assert r1[0] == r2[0]
+    for k in range(1, 5):
+        assert np.array_equal(r1[k], r2[k])
+    assert np.array_equal(s1.view(np.uint32), s2.view(np.uint32))
+
+
+def test_factorisation_noncontiguous(q, ctx):
+    """A manual (non-contiguous) allocation goes through the general check."""
+    n = 14
+    Q = inst.normal_qubo(n, 77)
+    cost = _cost(q, ctx, Q)
+    manual = [(i * 7) % 3 for i in range(n)]
+    qpu_of = q.qaoa_partition(n, 3, caps=[5, 5, 5], manual=manual)
+    mism, perr = q.qaoa_check_factorisation(ctx, cost, qpu_of, 1.3)
+    assert mism == 0 and perr < 1e-5
+    q.qaoa_cost_destroy(cost)
