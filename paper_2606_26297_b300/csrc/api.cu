@@ -78,7 +78,7 @@ struct qaoa_ctx_s {
     cudaStream_t stream = nullptr;
     qaoa_options opt{};
     int64_t held = 0;
-    DevBuf work_psi, lam, partials, pass_sums, topk_a, topk_b, items, small_out, misc;
+    DevBuf work_psi, lam, pl, partials, pass_sums, topk_a, topk_b, items, small_out, misc;
     std::vector<ProfRec> pending;
     std::vector<cudaEvent_t> ev_free;
     int64_t prof_launches[5] = {0, 0, 0, 0, 0};
@@ -450,7 +450,10 @@ qaoa_status ensure_scratch(qaoa_ctx c, int n, int npasses, int ktop, bool grad) 
     const size_t N = (size_t)1 << n;
     const int nb = n >= BLOCK_BITS ? (1 << (n - BLOCK_BITS)) : 1;
     QAOA_TRY(c->work_psi.ensure(N * sizeof(float2), &c->held, c->opt.memory_budget));
-    if (grad) QAOA_TRY(c->lam.ensure(N * sizeof(float2), &c->held, c->opt.memory_budget));
+    if (grad && n >= BLOCK_BITS) {
+        if (c->opt.pass_variant == 1) QAOA_TRY(c->lam.ensure(N * sizeof(float2), &c->held, c->opt.memory_budget));
+        else QAOA_TRY(c->pl.ensure(N * sizeof(float4), &c->held, c->opt.memory_budget));
+    }
     QAOA_TRY(c->partials.ensure((size_t)nb * NSLOT * sizeof(double), &c->held, c->opt.memory_budget));
     QAOA_TRY(c->pass_sums.ensure((size_t)(npasses + 1) * NSLOT * sizeof(double), &c->held, c->opt.memory_budget));
     const int kk = std::max(ktop, 1);
@@ -484,7 +487,9 @@ qaoa_status run_passes(qaoa_ctx c, const qaoa_cost_s *cost, int p, const double 
     const int nb = 1 << (n - BLOCK_BITS);
     const int npasses = (int)sched.size() * (grad ? 2 : 1);
     QAOA_TRY(ensure_scratch(c, n, npasses, grad ? ktop : 0, grad));
-    float2 *lam = grad ? c->lam.as<float2>() : nullptr;
+    const bool use_tma = c->opt.pass_variant != 1;
+    float2 *lam = (grad && !use_tma) ? c->lam.as<float2>() : nullptr;
+    float4 *pl = (grad && use_tma) ? c->pl.as<float4>() : nullptr;
     double *partials = c->partials.as<double>();
     double *sums = c->pass_sums.as<double>();
     std::vector<PassRun> runs;
@@ -494,7 +499,10 @@ qaoa_status run_passes(qaoa_ctx c, const qaoa_cost_s *cost, int p, const double 
     if (grad)
         for (int i = (int)sched.size() - 2; i >= 0; --i)
             runs.push_back(rev_args(groups[sched[i].group], sched[i], cost, gamma, beta, psi, lam, partials, p));
-    const bool use_tma = c->opt.pass_variant != 1;
+    for (auto &r : runs) {
+        r.args.pl = pl;
+        if (use_tma && r.epi) r.bytes = std::ldexp(28.0, n);  // psi + table in, (psi, lambda) out
+    }
     if (use_tma) {
         QAOA_TRY(c->status.ensure(16, &c->held, c->opt.memory_budget));
         CUDA_TRY(cudaMemsetAsync(c->status.p, 0, 16, c->stream));
@@ -507,9 +515,11 @@ qaoa_status run_passes(qaoa_ctx c, const qaoa_cost_s *cost, int p, const double 
         {
             ProfScope ps(c, rev ? 1 : 0, r.bytes);
             cudaError_t e;
+            unsigned int *stw = c->status.as<unsigned int>();
             if (use_tma)
-                e = rev ? launch_rev_tma(r.type, r.args, c->num_sms, c->status.as<unsigned int>(), c->stream)
-                        : launch_fwd_tma(r.type, r.epi, r.args, c->num_sms, c->status.as<unsigned int>(), c->stream);
+                e = rev ? launch_rev_pl(r.type, r.args, c->num_sms, stw, c->stream)
+                        : (r.epi ? launch_epi_pl(r.type, r.args, c->num_sms, stw, c->stream)
+                                 : launch_fwd_tma(r.type, false, r.args, c->num_sms, stw, c->stream));
             else
                 e = rev ? launch_rev_pass(r.type, r.args, c->stream)
                         : launch_fwd_pass(r.type, r.epi, r.args, c->stream);

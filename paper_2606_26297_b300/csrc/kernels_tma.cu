@@ -12,60 +12,9 @@
 
 #include "pass_body.cuh"
 #include "kernels_tma.h"
+#include "tma_util.cuh"
 
 namespace qaoa {
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(unsigned long long *m, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(m)), "r"(count) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long *m, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(m)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long *m, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(m)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait: gives up after ~2 s of clock or 2^26 polls.
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *m, uint32_t parity) {
-    const long long t0 = clock64();
-    uint32_t it = 0;
-    while (!mbar_try_wait(m, parity)) {
-        if (++it > (1u << 26) || clock64() - t0 > 4000000000ll) return false;
-    }
-    return true;
-}
-
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-__device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, int c1, int c4,
-                                            unsigned long long *mbar) {
-    asm volatile(
-        "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::
-            "r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(c1), "r"(0), "r"(0), "r"(c4), "r"(smem_u32(mbar))
-        : "memory");
-}
-
-__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, unsigned long long *mbar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(mbar))
-                 : "memory");
-}
 
 // Issue the copies of block b (psi, and lambda when TWO) into the stage.
 template <int T, bool TWO>
@@ -94,20 +43,6 @@ __device__ __forceinline__ void issue_cost(uint32_t b, const PassArgs &a, const 
         const int nlow = a.lo - 3;
         tma_load_5d(cstage, mcost, (int)(b & ((1u << nlow) - 1u)), (int)(b >> nlow), mbar);
     }
-}
-
-// Wait for the stage; returns false (uniformly across the CTA) on timeout,
-// after recording it in the status word.
-__device__ __forceinline__ bool stage_ready(unsigned long long *mbar, uint32_t parity, unsigned int *status) {
-    const bool ok = mbar_wait_bounded(mbar, parity);
-    const int bad = __syncthreads_or(!ok);
-    if (bad) {
-        if (threadIdx.x == 0) atomicExch(status, 1u);
-        // give the copy in flight a last bounded chance to land before the CTA exits
-        mbar_wait_bounded(mbar, parity);
-        return false;
-    }
-    return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -364,17 +299,20 @@ static cudaError_t get_encoder() {
 
 // 5-D view of a high-group block: (carried bits 0..2) x (bits 3..lo-1) x
 // (group bits 0..4) x (group bits 5..9) x (bits lo+10..n-1), elements of
-// `esize` bytes (8: complex64 amplitudes, 4: int32 table entries).
+// `esize` bytes (16: interleaved (psi, lambda), 8: complex64 amplitudes,
+// 4: int32 table entries).
 cudaError_t make_block_map(CUtensorMap *map, const void *base, int n, int lo, int esize) {
     std::memset(map, 0, sizeof(*map));
     cudaError_t e = get_encoder();
     if (e) return e;
+    // 16-byte elements are described as pairs of 8-byte elements in dim 0
     const cuuint64_t es = (cuuint64_t)esize;
-    cuuint64_t dims[5] = {8ull, 1ull << (lo - 3), 32ull, 32ull, 1ull << (n - lo - 10)};
+    const cuuint64_t d0 = esize == 16 ? 16ull : 8ull;
+    cuuint64_t dims[5] = {d0, 1ull << (lo - 3), 32ull, 32ull, 1ull << (n - lo - 10)};
     cuuint64_t strides[4] = {8ull * es, es << lo, es << (lo + 5), es << (lo + 10)};
-    cuuint32_t box[5] = {8u, 1u, 32u, 32u, 1u};
+    cuuint32_t box[5] = {(cuuint32_t)d0, 1u, 32u, 32u, 1u};
     cuuint32_t estr[5] = {1u, 1u, 1u, 1u, 1u};
-    CUresult r = g_encode(map, esize == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_INT32, 5,
+    CUresult r = g_encode(map, esize == 4 ? CU_TENSOR_MAP_DATA_TYPE_INT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 5,
                           const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);

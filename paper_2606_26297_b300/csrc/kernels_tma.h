@@ -16,4 +16,12 @@ namespace qaoa {
 cudaError_t launch_fwd_tma(int type, bool epi, const PassArgs &a, int grid, unsigned int *status, cudaStream_t st);
 cudaError_t launch_rev_tma(int type, const PassArgs &a, int grid, unsigned int *status, cudaStream_t st);
 
+// Final forward pass writing the interleaved (psi, lambda) buffer a.pl, and the
+// reverse pass on that buffer (kernels_rev2.cu).
+cudaError_t launch_epi_pl(int type, const PassArgs &a, int grid, unsigned int *status, cudaStream_t st);
+cudaError_t launch_rev_pl(int type, const PassArgs &a, int grid, unsigned int *status, cudaStream_t st);
+
+// Tensor map of the 5-D high-group block view (see kernels_tma.cu).
+cudaError_t make_block_map(CUtensorMap *map, const void *base, int n, int lo, int esize);
+
 }  // namespace qaoa

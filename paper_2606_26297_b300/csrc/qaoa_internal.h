@@ -67,6 +67,7 @@ struct MixOp {
 struct PassArgs {
     float2 *psi;            // state (read and/or written)
     float2 *lam;            // adjoint state
+    float4 *pl;             // interleaved (psi.re, lambda.re, psi.im, lambda.im) per index
     const int32_t *C;       // objective table T
     double *partials;       // [block][NSLOT] per-block FP64 partial sums
     unsigned long long *topk_keys;  // [block][ktop] candidate keys (epilogue only)

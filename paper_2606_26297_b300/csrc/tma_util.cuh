@@ -1,0 +1,78 @@
+// PTX helpers for the TMA-pipelined kernels: mbarriers with transaction
+// counts, bulk and tensor copies into shared memory, and bounded waits.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+namespace qaoa {
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *m, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(m)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *m, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(m)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *m, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(m)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: gives up after ~2 s of clock or 2^26 polls.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *m, uint32_t parity) {
+    const long long t0 = clock64();
+    uint32_t it = 0;
+    while (!mbar_try_wait(m, parity)) {
+        if (++it > (1u << 26) || clock64() - t0 > 4000000000ll) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, int c1, int c4,
+                                            unsigned long long *mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::
+            "r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(c1), "r"(0), "r"(0), "r"(c4), "r"(smem_u32(mbar))
+        : "memory");
+}
+
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, unsigned long long *mbar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+                 : "memory");
+}
+
+// Wait for the stage; returns false (uniformly across the CTA) on timeout,
+// after recording it in the status word.
+__device__ __forceinline__ bool stage_ready(unsigned long long *mbar, uint32_t parity, unsigned int *status) {
+    const bool ok = mbar_wait_bounded(mbar, parity);
+    const int bad = __syncthreads_or(!ok);
+    if (bad) {
+        if (threadIdx.x == 0) atomicExch(status, 1u);
+        // give the copy in flight a last bounded chance to land before the CTA exits
+        mbar_wait_bounded(mbar, parity);
+        return false;
+    }
+    return true;
+}
+
+}  // namespace qaoa

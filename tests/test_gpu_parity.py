@@ -334,7 +334,9 @@ def test_error_paths(q, ctx):
 @pytest.mark.parametrize("n,p,kind", [(13, 2, "normal"), (17, 3, "int"), (22, 2, "maxcut"), (26, 1, "normal")])
 def test_tma_and_direct_variants_bitwise_equal(q, n, p, kind):
     """The TMA-pipelined persistent kernels and the direct-load kernels run the
-    same arithmetic; their results must agree bit for bit."""
+    same forward arithmetic: forward states, E and top-K agree bit for bit.
+    The TMA reverse sweep recomputes psi from the final pass (interleaved
+    psi/lambda layout), so its gradient agrees to rounding."""
     Q = _instance(kind, n, 1200 + n)
     g, b = _angles(Q, p, kind)
     outs = []
@@ -350,8 +352,9 @@ def test_tma_and_direct_variants_bitwise_equal(q, n, p, kind):
         q.qaoa_ctx_destroy(c)
     (r1, s1), (r2, s2) = outs
     assert r1[0] == r2[0]
-    for k in range(1, 5):
-        assert np.array_equal(r1[k], r2[k])
+    assert np.array_equal(r1[3], r2[3]) and np.array_equal(r1[4], r2[4])
+    sc = max(np.abs(r1[1]).max(), np.abs(r1[2]).max())
+    assert max(np.abs(r1[1] - r2[1]).max(), np.abs(r1[2] - r2[2]).max()) <= 1e-5 * sc
     assert np.array_equal(s1.view(np.uint32), s2.view(np.uint32))
 
 
