@@ -85,8 +85,11 @@ typedef struct {
     int64_t memory_budget;  /* bytes of device memory the context may hold; 0 = free memory */
     int32_t max_fused_qubits; /* qubits per mixer pass: 0 = default (10), else 3..10 */
     int32_t state_fp64;     /* 1: complex128 states and arithmetic (n <= 12 only) */
-    int32_t pass_variant;   /* layer-pass kernels: 0 = default (TMA-pipelined persistent),
-                               1 = direct global loads, 2 = TMA-pipelined persistent */
+    int32_t pass_variant;   /* layer-pass kernels: 0 = default (forward passes with direct
+                               loads, final pass and reverse sweep TMA-pipelined on the
+                               interleaved (psi, lambda) buffer), 1 = all direct loads,
+                               2 = all TMA-pipelined (256 threads), 3 = all TMA-pipelined
+                               (512 threads, three register rounds) */
     int32_t reserved[5];
 } qaoa_options;
 

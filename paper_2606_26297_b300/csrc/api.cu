@@ -172,7 +172,8 @@ struct Group {
     int type;      // 0: low group (block = global bits 0..12), 1: high group
     int lo;        // window offset (type 1)
     uint32_t mask; // mixed local bits
-    int kX, kY;    // mixed bits in the register rounds of arrangements X and Y
+    int kX, kY;    // mixed bits in the register rounds of arrangements X and Y (256-thread kernels)
+    int k3[3];     // mixed bits in rounds A, B, C (512-thread kernels)
 };
 
 struct PassDesc {
@@ -183,6 +184,7 @@ struct PassDesc {
 
 constexpr uint32_t REGS_X[2] = {0x0F8u, 0x1C18u};  // type 0: bits 3..7; type 1: {3,4,10,11,12}
 constexpr uint32_t REGS_Y[2] = {0x307u, 0x3E0u};   // type 0: {0,1,2,8,9}; type 1: bits 5..9
+constexpr uint32_t ROUND3[2][3] = {{0x0018u, 0x0207u, 0x01E0u}, {0x1800u, 0x0618u, 0x01E0u}};
 
 std::vector<Group> make_groups(int n, int maxq) {
     const int G = (n + maxq - 1) / maxq;
@@ -203,6 +205,7 @@ std::vector<Group> make_groups(int n, int maxq) {
         }
         gr.kX = __builtin_popcount(gr.mask & REGS_X[gr.type]);
         gr.kY = __builtin_popcount(gr.mask & REGS_Y[gr.type]);
+        for (int r = 0; r < 3; ++r) gr.k3[r] = __builtin_popcount(gr.mask & ROUND3[gr.type][r]);
         gs.push_back(gr);
         q0 += k;
     }
@@ -446,6 +449,144 @@ PassRun rev_args(const Group &g, const PassDesc &d, const qaoa_cost_s *cost, con
     return r;
 }
 
+// Arguments of the 512-thread kernels.  Same scalar bookkeeping as fwd_args /
+// rev_args (computed = true * S), with three register rounds per mixer:
+// forward mixers run rounds A, B, C (pre) and C, B, A (post).
+PassRun fwd3_args(const Group &g, const PassDesc &d, const qaoa_cost_s *cost, const double *gamma,
+                  const double *beta, float2 *psi, float4 *pl, double *partials, unsigned long long *topk, int ktop) {
+    PassRun r{};
+    PassArgs &a = r.args;
+    a.psi = psi;
+    a.pl = pl;
+    a.C = cost->T;
+    a.partials = partials;
+    a.topk_keys = topk;
+    a.n = cost->n;
+    a.lo = g.lo;
+    a.mask = g.mask;
+    a.init = d.init;
+    a.has_cost = d.lc >= 0;
+    a.store_psi = 1;
+    a.ktop = d.epi ? ktop : 0;
+    a.amp0 = (float)std::pow(2.0, -0.5 * cost->n);
+    a.cscale = (float)std::ldexp(1.0, -cost->fp.s);
+    a.kmag = 1.f;
+    a.kend = make_float2(1.f, 0.f);
+    a.kend2 = make_float2(1.f, 0.f);
+    const int k = g.kX + g.kY;
+    cd S(1.0, 0.0);
+    Mix ma{}, mb{};
+    if (d.la >= 0) {
+        ma = mix_of(beta[d.la]);
+        a.pre = ma.op;
+        S /= cpow_int(ma.f, k);
+    }
+    if (d.lb >= 0) {
+        mb = mix_of(beta[d.lb]);
+        a.post = mb.op;
+    }
+    if (d.lc >= 0) {
+        const uint64_t phi = phase_multiplier(gamma[d.lc], cost->fp.s);
+        const cd Kf = (d.lb >= 0 ? cpow_int(mb.f, k) : cd(1.0, 0.0)) / S;
+        a.phi = phi;
+        a.off = (uint64_t)cost->fp.k_c * phi + turns_of_arg(Kf);
+        a.kmag = (float)std::abs(Kf);
+        S = (d.lb >= 0 ? cpow_int(mb.f, k) : cd(1.0, 0.0));
+    }
+    if (d.lb >= 0) S /= cpow_int(mb.f, k);
+    for (int s = 0; s < NSLOT; ++s) {
+        r.slot_scale[s] = 0.0;
+        r.slot_param[s] = -1;
+    }
+    const double N = std::ldexp(1.0, cost->n);
+    if (!d.epi) {
+        if (d.lc < 0) a.kend = f2(1.0 / S);
+        r.has_partials = false;
+        r.bytes = N * ((d.init ? 0.0 : 8.0) + 8.0 + (d.lc >= 0 ? 4.0 : 0.0));
+    } else {
+        a.kend = f2(1.0 / S);
+        cd Sl(1.0, 0.0);
+        r.slot_param[0] = -2;
+        r.slot_param[1] = -2;
+        const int order[3] = {2, 1, 0};  // lambda undo: rounds C, B, A -> slots 2, 3, 4
+        for (int j = 0; j < 3; ++j) {
+            r.slot_scale[2 + j] = 1.0 / std::norm(Sl);
+            r.slot_param[2 + j] = d.la;
+            Sl /= cpow_int(std::conj(ma.f), g.k3[order[j]]);
+        }
+        a.kend2 = f2(1.0 / Sl);
+        r.has_partials = true;
+        r.bytes = N * (8.0 + 4.0 + 16.0);
+    }
+    r.type = g.type;
+    r.epi = d.epi;
+    return r;
+}
+
+PassRun rev3_args(const Group &g, const PassDesc &d, const qaoa_cost_s *cost, const double *gamma,
+                  const double *beta, float4 *pl, double *partials, int p) {
+    PassRun r{};
+    PassArgs &a = r.args;
+    a.pl = pl;
+    a.C = cost->T;
+    a.partials = partials;
+    a.n = cost->n;
+    a.lo = g.lo;
+    a.mask = g.mask;
+    a.has_cost = d.lc >= 0;
+    a.store_psi = d.init ? 0 : 1;
+    a.cscale = (float)std::ldexp(1.0, -cost->fp.s);
+    a.kmag = 1.f;
+    a.kend = make_float2(1.f, 0.f);
+    const int k = g.kX + g.kY;
+    Mix ma{}, mb{};
+    if (d.la >= 0) {
+        ma = mix_of(beta[d.la]);
+        a.pre = ma.op;
+    }
+    if (d.lb >= 0) {
+        mb = mix_of(beta[d.lb]);
+        a.post = mb.op;
+    }
+    for (int s = 0; s < NSLOT; ++s) {
+        r.slot_scale[s] = 0.0;
+        r.slot_param[s] = -1;
+    }
+    cd S(1.0, 0.0);
+    if (d.lb >= 0) {  // undo the post mixer: rounds A, B, C -> slots 0, 1, 2
+        for (int j = 0; j < 3; ++j) {
+            r.slot_scale[j] = 1.0 / std::norm(S);
+            r.slot_param[j] = d.lb;
+            S /= cpow_int(std::conj(mb.f), g.k3[j]);
+        }
+    }
+    if (d.lc >= 0) {
+        r.slot_scale[3] = 1.0 / std::norm(S);
+        r.slot_param[3] = p + d.lc;
+        const uint64_t phi = phase_multiplier(gamma[d.lc], cost->fp.s);
+        const cd Kf = (d.la >= 0 ? cpow_int(std::conj(ma.f), k) : cd(1.0, 0.0)) / S;
+        a.phi = (uint64_t)0 - phi;
+        a.off = (uint64_t)0 - (uint64_t)cost->fp.k_c * phi + turns_of_arg(Kf);
+        a.kmag = (float)std::abs(Kf);
+        S *= Kf;
+    }
+    if (d.la >= 0) {  // undo the pre mixer: rounds C, B, A -> slots 4, 5, 6
+        const int order[3] = {2, 1, 0};
+        for (int j = 0; j < 3; ++j) {
+            r.slot_scale[4 + j] = 1.0 / std::norm(S);
+            r.slot_param[4 + j] = d.la;
+            S /= cpow_int(std::conj(ma.f), g.k3[order[j]]);
+        }
+    }
+    if (d.lc < 0) a.kend = f2(1.0 / S);
+    r.has_partials = true;
+    r.type = g.type;
+    r.epi = false;
+    const double N = std::ldexp(1.0, cost->n);
+    r.bytes = N * (16.0 + (a.store_psi ? 16.0 : 0.0) + (d.lc >= 0 ? 4.0 : 0.0));
+    return r;
+}
+
 qaoa_status ensure_scratch(qaoa_ctx c, int n, int npasses, int ktop, bool grad) {
     const size_t N = (size_t)1 << n;
     const int nb = n >= BLOCK_BITS ? (1 << (n - BLOCK_BITS)) : 1;
@@ -492,16 +633,31 @@ qaoa_status run_passes(qaoa_ctx c, const qaoa_cost_s *cost, int p, const double 
     float4 *pl = (grad && use_tma) ? c->pl.as<float4>() : nullptr;
     double *partials = c->partials.as<double>();
     double *sums = c->pass_sums.as<double>();
+    // variant 0 (default): forward passes with direct loads (256 threads, two
+    // CTAs per SM), final pass and reverse sweep TMA-pipelined on the
+    // interleaved (psi, lambda) buffer
+    const int variant = c->opt.pass_variant;
     std::vector<PassRun> runs;
-    for (const auto &d : sched)
-        runs.push_back(fwd_args(groups[d.group], d, cost, gamma, beta, psi, lam, partials,
-                                c->topk_a.as<unsigned long long>(), ktop, p));
-    if (grad)
-        for (int i = (int)sched.size() - 2; i >= 0; --i)
-            runs.push_back(rev_args(groups[sched[i].group], sched[i], cost, gamma, beta, psi, lam, partials, p));
+    if (variant == 3) {
+        for (const auto &d : sched)
+            runs.push_back(fwd3_args(groups[d.group], d, cost, gamma, beta, psi, c->pl.as<float4>(), partials,
+                                     c->topk_a.as<unsigned long long>(), ktop));
+        if (grad)
+            for (int i = (int)sched.size() - 2; i >= 0; --i)
+                runs.push_back(rev3_args(groups[sched[i].group], sched[i], cost, gamma, beta, c->pl.as<float4>(),
+                                         partials, p));
+    } else {
+        for (const auto &d : sched)
+            runs.push_back(fwd_args(groups[d.group], d, cost, gamma, beta, psi, lam, partials,
+                                    c->topk_a.as<unsigned long long>(), ktop, p));
+        if (grad)
+            for (int i = (int)sched.size() - 2; i >= 0; --i)
+                runs.push_back(rev_args(groups[sched[i].group], sched[i], cost, gamma, beta, psi, lam, partials, p));
+    }
     for (auto &r : runs) {
         r.args.pl = pl;
         if (use_tma && r.epi) r.bytes = std::ldexp(28.0, n);  // psi + table in, (psi, lambda) out
+        if (variant == 3) r.args.psi = psi;
     }
     if (use_tma) {
         QAOA_TRY(c->status.ensure(16, &c->held, c->opt.memory_budget));
@@ -516,10 +672,15 @@ qaoa_status run_passes(qaoa_ctx c, const qaoa_cost_s *cost, int p, const double 
             ProfScope ps(c, rev ? 1 : 0, r.bytes);
             cudaError_t e;
             unsigned int *stw = c->status.as<unsigned int>();
-            if (use_tma)
+            if (variant == 3)
+                e = rev ? launch_rev3(r.type, r.args, c->num_sms, stw, c->stream)
+                        : (r.epi ? launch_epi3(r.type, r.args, c->num_sms, stw, c->stream)
+                                 : launch_fwd3(r.type, r.args, c->num_sms, stw, c->stream));
+            else if (use_tma)
                 e = rev ? launch_rev_pl(r.type, r.args, c->num_sms, stw, c->stream)
                         : (r.epi ? launch_epi_pl(r.type, r.args, c->num_sms, stw, c->stream)
-                                 : launch_fwd_tma(r.type, false, r.args, c->num_sms, stw, c->stream));
+                                 : (variant == 0 ? launch_fwd_pass(r.type, false, r.args, c->stream)
+                                                 : launch_fwd_tma(r.type, false, r.args, c->num_sms, stw, c->stream)));
             else
                 e = rev ? launch_rev_pass(r.type, r.args, c->stream)
                         : launch_fwd_pass(r.type, r.epi, r.args, c->stream);
@@ -638,9 +799,9 @@ qaoa_status qaoa_ctx_create(int device, void *cuda_stream, const qaoa_options *o
     c->stream = (cudaStream_t)cuda_stream;
     if (opt) c->opt = *opt;
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
-    if (c->opt.pass_variant < 0 || c->opt.pass_variant > 2) {
+    if (c->opt.pass_variant < 0 || c->opt.pass_variant > 3) {
         delete c;
-        return fail(QAOA_ERR_INVALID_ARG, "pass_variant must be 0, 1 or 2");
+        return fail(QAOA_ERR_INVALID_ARG, "pass_variant must be 0, 1, 2 or 3");
     }
     if (c->opt.max_fused_qubits != 0 && (c->opt.max_fused_qubits < 3 || c->opt.max_fused_qubits > 10)) {
         delete c;

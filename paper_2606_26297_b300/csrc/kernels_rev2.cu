@@ -44,23 +44,22 @@ __device__ __forceinline__ void round_mix_pq(float2 (&P)[32], float2 (&Q)[32], f
 // per pair, cross(P_a, Q_b) + cross(P_b, Q_a) with cross(u, v) = u.y v.x - u.x v.y.
 template <int T, int A>
 __device__ __forceinline__ float xterm_pq(const float2 (&P)[32], const float2 (&Q)[32], uint32_t mask) {
-    float acc = 0.f;
+    // four independent partial sums keep the FMA dependency chains short
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
         if (!((mask >> regbit<T, A>(i)) & 1u)) continue;
-        float s = 0.f;
 #pragma unroll
         for (int m = 0; m < 32; ++m) {
             if (m & (1 << i)) continue;
             const int q = m | (1 << i);
-            s = fmaf(P[m].y, Q[q].x, s);
-            s = fmaf(-P[m].x, Q[q].y, s);
-            s = fmaf(P[q].y, Q[m].x, s);
-            s = fmaf(-P[q].x, Q[m].y, s);
+            s0 = fmaf(P[m].y, Q[q].x, s0);
+            s1 = fmaf(-P[m].x, Q[q].y, s1);
+            s2 = fmaf(P[q].y, Q[m].x, s2);
+            s3 = fmaf(-P[q].x, Q[m].y, s3);
         }
-        acc += s;
     }
-    return acc;
+    return (s0 + s1) + (s2 + s3);
 }
 
 // (P, Q) <- (P, Q) * z for a complex scalar z applied to both states

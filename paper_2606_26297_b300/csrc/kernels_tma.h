@@ -21,6 +21,12 @@ cudaError_t launch_rev_tma(int type, const PassArgs &a, int grid, unsigned int *
 cudaError_t launch_epi_pl(int type, const PassArgs &a, int grid, unsigned int *status, cudaStream_t st);
 cudaError_t launch_rev_pl(int type, const PassArgs &a, int grid, unsigned int *status, cudaStream_t st);
 
+// 512-thread variants (kernels_v3.cu): forward pass, final forward pass of a
+// gradient evaluation (writes a.pl), reverse pass on a.pl.
+cudaError_t launch_fwd3(int type, const PassArgs &a, int grid, unsigned int *status, cudaStream_t st);
+cudaError_t launch_epi3(int type, const PassArgs &a, int grid, unsigned int *status, cudaStream_t st);
+cudaError_t launch_rev3(int type, const PassArgs &a, int grid, unsigned int *status, cudaStream_t st);
+
 // Tensor map of the 5-D high-group block view (see kernels_tma.cu).
 cudaError_t make_block_map(CUtensorMap *map, const void *base, int n, int lo, int esize);
 

@@ -90,7 +90,7 @@ struct PassArgs {
     float cscale;           // 2^-s
 };
 
-constexpr int NSLOT = 5;
+constexpr int NSLOT = 8;
 constexpr int BLOCK_BITS = 13;
 constexpr int PASS_THREADS = 256;
 

@@ -332,30 +332,35 @@ def test_error_paths(q, ctx):
 # ---- kernel variants -----------------------------------------------------------------------
 
 @pytest.mark.parametrize("n,p,kind", [(13, 2, "normal"), (17, 3, "int"), (22, 2, "maxcut"), (26, 1, "normal")])
-def test_tma_and_direct_variants_bitwise_equal(q, n, p, kind):
-    """The TMA-pipelined persistent kernels and the direct-load kernels run the
-    same forward arithmetic: forward states, E and top-K agree bit for bit.
-    The TMA reverse sweep recomputes psi from the final pass (interleaved
-    psi/lambda layout), so its gradient agrees to rounding."""
+def test_kernel_variants_agree(q, n, p, kind):
+    """The layer-pass kernel families (1: 256 threads, direct loads; 2: 256
+    threads, TMA-pipelined; 3: 512 threads, TMA-pipelined) compute the same
+    method.  Variants 1 and 2 run identical forward arithmetic (bitwise equal
+    states, E and top-K); variant 3 applies the butterflies in a different
+    order, so it agrees to rounding."""
     Q = _instance(kind, n, 1200 + n)
     g, b = _angles(Q, p, kind)
-    outs = []
-    for variant in (1, 2):
+    outs = {}
+    for variant in (1, 2, 3, 0):
         c = q.qaoa_ctx_create(0, pass_variant=variant)
         cost = _cost(q, c, Q)
         r = q.qaoa_grad(c, cost, g, b, k_top=8)
         st = q.qaoa_forward(c, cost, g, b)
         psi = q.qaoa_state_copy_to_host(c, st, n)
-        outs.append((r, psi))
+        outs[variant] = (r, psi)
         q.qaoa_state_destroy(st)
         q.qaoa_cost_destroy(cost)
         q.qaoa_ctx_destroy(c)
-    (r1, s1), (r2, s2) = outs
+    (r1, s1), (r2, s2), (r3, s3), (r0, s0) = outs[1], outs[2], outs[3], outs[0]
+    assert r0[0] == r1[0] and np.array_equal(s0.view(np.uint32), s1.view(np.uint32))
     assert r1[0] == r2[0]
     assert np.array_equal(r1[3], r2[3]) and np.array_equal(r1[4], r2[4])
-    sc = max(np.abs(r1[1]).max(), np.abs(r1[2]).max())
-    assert max(np.abs(r1[1] - r2[1]).max(), np.abs(r1[2] - r2[2]).max()) <= 1e-5 * sc
     assert np.array_equal(s1.view(np.uint32), s2.view(np.uint32))
+    for r in (r2, r3, r0):
+        sc = max(np.abs(r1[1]).max(), np.abs(r1[2]).max())
+        assert max(np.abs(r1[1] - r[1]).max(), np.abs(r1[2] - r[2]).max()) <= 1e-5 * sc
+    assert abs(r3[0] - r1[0]) <= 1e-6 * max(1.0, abs(r1[0]))
+    assert np.linalg.norm(s3.astype(np.complex128) - s1.astype(np.complex128)) <= 1e-6
 
 
 def test_factorisation_noncontiguous(q, ctx):
