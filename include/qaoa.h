@@ -214,6 +214,36 @@ qaoa_status qaoa_classify(qaoa_cost cost, const int32_t *qpu_of, int p, int64_t 
 qaoa_status qaoa_check_factorisation(qaoa_ctx ctx, qaoa_cost cost, const int32_t *qpu_of,
                                      double gamma_probe, int64_t *mismatches, double *max_phase_err);
 
+/* ---- allocation-free expectation -----------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that must not allocate device memory when they evaluate <H_C>: a host
+ * framework that owns all device memory behind a capped pool of its own, a
+ * latency-critical loop that cannot afford the implicit device
+ * synchronisation a cudaMalloc or cudaFree may trigger, or code that holds
+ * only raw device pointers and no qaoa_ctx to keep scratch in.
+ *
+ * Same result as qaoa_expect (the same reduction, in the same order):
+ * sum_x |psi_x|^2 (T[x] + k_c) 2^-shift_bits.
+ *   amps:        device pointer, 2^n complex64 amplitudes (caller-owned)
+ *   table:       device pointer, the 2^n int32 table T of a qaoa_cost
+ *                (qaoa_cost_copy_to_host / qaoa_cost_info give T, s and k_c)
+ *   n:           1 <= n <= 30; larger n is rejected with QAOA_ERR_INVALID_ARG
+ *   shift_bits, k_c: the fixed-point parameters s and k_c of that table
+ *   cuda_stream: cudaStream_t the work is ordered on (NULL = default stream);
+ *                the call synchronises it before returning
+ *   out_expect:  host pointer, receives the expectation
+ * Memory: allocates nothing.  Its scratch is one fixed device array of
+ * 2 * 2^17 + 2 doubles (about 2 MiB) defined in the library, present on every
+ * GPU that loads the library until the process exits.  All calls share that
+ * array, so calls that overlap on the GPU (two host threads, or two streams
+ * without ordering between them) race and may return wrong values; order them.
+ * The array keeps the previous call's contents, but every value a call reads
+ * is written earlier in the same call.  The first call on each device looks
+ * up the array's device address with that device current; make that first
+ * call before any stream capture begins. */
+qaoa_status qaoa_expect_noalloc(const void *amps, const int32_t *table, int n, int32_t shift_bits,
+                                int64_t k_c, void *cuda_stream, double *out_expect);
+
 /* ---- profiling ---------------------------------------------------------- */
 
 /* With options.profile = 1, every kernel launch of the given kind is timed

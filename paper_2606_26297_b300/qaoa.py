@@ -73,6 +73,7 @@ _SIGS = {
     "qaoa_classify": ([_P, _PI32, _I, _PI64, _PI64, _PI64, _PI64], _I),
     "qaoa_check_factorisation": ([_P, _P, _PI32, _D, _PI64, _PD], _I),
     "qaoa_profile_read": ([_P, _I, _PI64, _PD, _PD, _I], _I),
+    "qaoa_expect_noalloc": ([_P, _P, _I, ctypes.c_int32, ctypes.c_int64, _P, _PD], _I),
 }
 for _name, (_args, _res) in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -266,6 +267,16 @@ def qaoa_check_factorisation(ctx, cost, qpu_of, gamma_probe: float = 0.7):
     _check(_lib.qaoa_check_factorisation(ctx, cost, q.ctypes.data_as(_PI32), float(gamma_probe), ctypes.byref(mm),
                                          ctypes.byref(pe)))
     return mm.value, pe.value
+
+
+def qaoa_expect_noalloc(amps_ptr: int, table_ptr: int, n: int, shift_bits: int, k_c: int,
+                        stream: int | None = None) -> float:
+    """<H_C> from raw device pointers, without any device allocation (the
+    library keeps this call's scratch in a fixed device array; n <= 30)."""
+    e = ctypes.c_double()
+    _check(_lib.qaoa_expect_noalloc(_P(amps_ptr), _P(table_ptr), int(n), int(shift_bits), int(k_c),
+                                    _P(stream or 0), ctypes.byref(e)))
+    return e.value
 
 
 def qaoa_profile_read(ctx, kind: int, reset: bool = False):
