@@ -85,12 +85,7 @@ typedef struct {
     int64_t memory_budget;  /* bytes of device memory the context may hold; 0 = free memory */
     int32_t max_fused_qubits; /* qubits per mixer pass: 0 = default (10), else 3..10 */
     int32_t state_fp64;     /* 1: complex128 states and arithmetic (n <= 12 only) */
-    int32_t pass_variant;   /* layer-pass kernels: 0 = default (forward passes with direct
-                               loads, final pass and reverse sweep TMA-pipelined on the
-                               interleaved (psi, lambda) buffer), 1 = all direct loads,
-                               2 = all TMA-pipelined (256 threads), 3 = all TMA-pipelined
-                               (512 threads, three register rounds) */
-    int32_t reserved[5];
+    int32_t reserved[6];    /* must be zero */
 } qaoa_options;
 
 typedef struct qaoa_ctx_s *qaoa_ctx;     /* device, stream, options, scratch, plan cache */
@@ -185,6 +180,34 @@ qaoa_status qaoa_grad(qaoa_ctx ctx, qaoa_cost cost, int p, const double *gamma,
 qaoa_status qaoa_grad_batch(qaoa_ctx ctx, int nq, const qaoa_cost *costs, const int32_t *item_cost,
                             int B, int p, const double *gamma, const double *beta,
                             double *expect, double *dgamma, double *dbeta);
+
+/* ---- parameter optimisation (Sec. 3.4) ---------------------------------- */
+
+/* Hyper-parameters of qaoa_optimize_adam.  Zero fields take the defaults
+ * lr = 0.01, beta1 = 0.9, beta2 = 0.999, eps = 1e-8. */
+typedef struct {
+    double lr, beta1, beta2, eps;
+    int32_t iterations;    /* Adam steps, >= 1 */
+    int32_t disable_graph; /* 1: launch every step eagerly instead of replaying a CUDA graph */
+    int32_t reserved[6];
+} qaoa_adam_options;
+
+/* Minimise the objective of Sec. 3.4 (Eq. training_objective_mean_cost,
+ * evaluated exactly rather than from shots) for B parameter sets at once with
+ * Adam on the exact adjoint gradient: theta <- theta - lr mhat/(sqrt(vhat)+eps)
+ * with bias-corrected moments, theta = (gamma, beta) of each item.  Items and
+ * costs as in qaoa_grad_batch.  gamma, beta: host, B*p doubles each, read as
+ * the starting point and overwritten with the final parameters.
+ * history: host, iterations*B doubles or NULL; history[t*B + b] = E of item b
+ * at the parameters before step t+1.  final_expect: host, B doubles or NULL;
+ * E at the final parameters.  The first step runs eagerly; the remaining
+ * iterations-1 steps replay one CUDA graph of a whole step (scalars, passes,
+ * reductions, gradient assembly, Adam update), with no host work between
+ * steps.  Runs on a stream owned by the context; `ctx`'s stream is ordered
+ * after it on return. */
+qaoa_status qaoa_optimize_adam(qaoa_ctx ctx, int nq, const qaoa_cost *costs, const int32_t *item_cost,
+                               int B, int p, double *gamma, double *beta,
+                               const qaoa_adam_options *opt, double *history, double *final_expect);
 
 /* ---- DQAOA bookkeeping (host) and the GPU factorisation invariant ------- */
 

@@ -1,34 +1,34 @@
-// C ABI of the QAOA statevector library (include/qaoa.h): handles, the layer
-// pass schedule, gradient assembly, and the DQAOA entry points.
+// C ABI of the QAOA statevector library (include/qaoa.h): handles, execution
+// of the layer-pass plan for one item or a batch, gradient assembly, the
+// Adam loop captured in a CUDA graph, and the DQAOA entry points.
 #include <algorithm>
 #include <cmath>
-#include <complex>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <vector>
 
 #include "kernels_misc.h"
-#include "kernels_tma.h"
 #include "qaoa_internal.h"
+#include "schedule.cuh"
 
 using namespace qaoa;
-using cd = std::complex<double>;
 
 namespace qaoa {
 const char *last_error();
 }
 
-#define CUDA_TRY(expr)                                                                      \
-    do {                                                                                    \
-        cudaError_t e__ = (expr);                                                           \
-        if (e__ != cudaSuccess)                                                             \
+#define CUDA_TRY(expr)                                                                             \
+    do {                                                                                           \
+        cudaError_t e__ = (expr);                                                                  \
+        if (e__ != cudaSuccess)                                                                    \
             return fail(e__ == cudaErrorMemoryAllocation ? QAOA_ERR_OUT_OF_MEMORY : QAOA_ERR_CUDA, \
-                        "%s: %s (%s:%d)", #expr, cudaGetErrorString(e__), __FILE__, __LINE__); \
+                        "%s: %s (%s:%d)", #expr, cudaGetErrorString(e__), __FILE__, __LINE__);     \
     } while (0)
 
-#define QAOA_TRY(expr)                 \
-    do {                               \
-        qaoa_status s__ = (expr);      \
+#define QAOA_TRY(expr)                  \
+    do {                                \
+        qaoa_status s__ = (expr);       \
         if (s__ != QAOA_OK) return s__; \
     } while (0)
 
@@ -38,6 +38,9 @@ namespace {
 struct DevBuf {
     void *p = nullptr;
     size_t cap = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
     ~DevBuf() {
         if (p) cudaFree(p);
     }
@@ -71,6 +74,12 @@ struct ProfRec {
     double bytes;
 };
 
+// Device buffers of one plan execution (one n, a batch of items).
+struct PlanBufs {
+    DevBuf psi, pl, partials, sums, scal, slot_scale, plan, gamma, beta, item_s, item_kc, item_table, tables,
+        out_E, out_dg, out_db, topk_a, topk_b, adam_m, adam_v, adam_step, history, small_items, small_out;
+};
+
 }  // namespace
 
 struct qaoa_ctx_s {
@@ -78,15 +87,17 @@ struct qaoa_ctx_s {
     cudaStream_t stream = nullptr;
     qaoa_options opt{};
     int64_t held = 0;
-    DevBuf work_psi, lam, pl, partials, pass_sums, topk_a, topk_b, items, small_out, misc;
+    int num_sms = 148;
+    PlanBufs single;                  // qaoa_grad / qaoa_forward working set
+    std::map<int, std::unique_ptr<PlanBufs>> groups;  // batched working sets, by n
+    DevBuf partials_e, sums_e, topk_a, topk_b, small_items, small_out, misc, status;
     std::vector<ProfRec> pending;
     std::vector<cudaEvent_t> ev_free;
     int64_t prof_launches[5] = {0, 0, 0, 0, 0};
     double prof_ms[5] = {0, 0, 0, 0, 0};
     double prof_bytes[5] = {0, 0, 0, 0, 0};
     int64_t launches_total = 0;  // every kernel launched by this context
-    int num_sms = 148;
-    DevBuf status;               // device status word of the bounded waits
+    cudaStream_t aux_stream = nullptr;  // owned; runs captured optimisation loops
 };
 
 struct qaoa_cost_s {
@@ -130,15 +141,17 @@ struct ProfScope {
     qaoa_ctx c;
     int kind;
     double bytes;
+    bool on;
     cudaEvent_t a = nullptr;
-    ProfScope(qaoa_ctx c_, int kind_, double bytes_) : c(c_), kind(kind_), bytes(bytes_) {
-        if (c->opt.profile) {
+    ProfScope(qaoa_ctx c_, int kind_, double bytes_, bool allow = true)
+        : c(c_), kind(kind_), bytes(bytes_), on(c_->opt.profile != 0 && allow) {
+        if (on) {
             a = get_event(c);
             cudaEventRecord(a, c->stream);
         }
     }
     ~ProfScope() {
-        if (c->opt.profile) {
+        if (on) {
             cudaEvent_t b = get_event(c);
             cudaEventRecord(b, c->stream);
             c->pending.push_back({kind, a, b, bytes});
@@ -166,442 +179,16 @@ qaoa_status set_device(int dev) {
     return QAOA_OK;
 }
 
-// ---- layer-pass schedule (Eq. qaoa_state with boundary fusion) -----------------------
-
-struct Group {
-    int type;      // 0: low group (block = global bits 0..12), 1: high group
-    int lo;        // window offset (type 1)
-    uint32_t mask; // mixed local bits
-    int kX, kY;    // mixed bits in the register rounds of arrangements X and Y (256-thread kernels)
-    int k3[3];     // mixed bits in rounds A, B, C (512-thread kernels)
-};
-
-struct PassDesc {
-    int group;
-    bool init = false, epi = false;
-    int la = -1, lc = -1, lb = -1;  // layers (0-based) of pre mixer, cost, post mixer
-};
-
-constexpr uint32_t REGS_X[2] = {0x0F8u, 0x1C18u};  // type 0: bits 3..7; type 1: {3,4,10,11,12}
-constexpr uint32_t REGS_Y[2] = {0x307u, 0x3E0u};   // type 0: {0,1,2,8,9}; type 1: bits 5..9
-constexpr uint32_t ROUND3[2][3] = {{0x0018u, 0x0207u, 0x01E0u}, {0x1800u, 0x0618u, 0x01E0u}};
-
-std::vector<Group> make_groups(int n, int maxq) {
-    const int G = (n + maxq - 1) / maxq;
-    std::vector<Group> gs;
-    int q0 = 0;
-    for (int g = 0; g < G; ++g) {
-        const int k = n / G + (g < n % G ? 1 : 0);
-        Group gr{};
-        if (g == 0) {
-            gr.type = 0;
-            gr.lo = 0;
-            gr.mask = (1u << k) - 1u;
-        } else {
-            gr.type = 1;
-            gr.lo = std::min(q0, n - 10);
-            gr.mask = 0;
-            for (int q = q0; q < q0 + k; ++q) gr.mask |= 1u << (3 + q - gr.lo);
-        }
-        gr.kX = __builtin_popcount(gr.mask & REGS_X[gr.type]);
-        gr.kY = __builtin_popcount(gr.mask & REGS_Y[gr.type]);
-        for (int r = 0; r < 3; ++r) gr.k3[r] = __builtin_popcount(gr.mask & ROUND3[gr.type][r]);
-        gs.push_back(gr);
-        q0 += k;
-    }
-    return gs;
-}
-
-std::vector<PassDesc> make_schedule(int G, int p, bool grad) {
-    std::vector<PassDesc> s;
-    auto order = [&](int l) {  // layer l (0-based): ascending for even l, descending for odd l
-        std::vector<int> o(G);
-        for (int g = 0; g < G; ++g) o[g] = (l % 2 == 0) ? g : G - 1 - g;
-        return o;
-    };
-    if (p == 0) {  // |+>^n only
-        PassDesc d;
-        d.group = 0;
-        d.init = true;
-        s.push_back(d);
-        return s;
-    }
-    {
-        PassDesc d;
-        d.group = order(0)[0];
-        d.init = true;
-        d.lc = 0;
-        d.lb = 0;
-        s.push_back(d);
-    }
-    for (int l = 0; l < p; ++l) {
-        auto o = order(l);
-        for (int g = 1; g < G - 1; ++g) {
-            PassDesc d;
-            d.group = o[g];
-            d.lb = l;
-            s.push_back(d);
-        }
-        PassDesc d;
-        d.group = o[G - 1];
-        if (l + 1 < p) {
-            d.la = l;
-            d.lc = l + 1;
-            d.lb = l + 1;
-        } else if (grad) {
-            d.la = l;
-            d.epi = true;
-        } else {
-            d.lb = l;  // final mixer of a forward-only run
-        }
-        s.push_back(d);
-    }
-    return s;
-}
-
-struct Mix {
-    MixOp op;
-    cd f;  // common factor of one level (true = f * computed)
-};
-
-Mix mix_of(double beta) {
-    Mix m{};
-    const double c = std::cos(beta), s = std::sin(beta);
-    m.op.mode = 1;
-    if (std::fabs(c) >= std::fabs(s)) {  // RX(2 beta) = cos(beta) (1 - i tan(beta) X)
-        m.op.flip = 0;
-        m.op.t = (float)(s / c);
-        m.f = cd(c, 0.0);
-    } else {  // RX(2 beta) = -i X RX(2 beta - pi) = -i sin(beta) X (1 - i tan(beta - pi/2) X)
-        m.op.flip = 1;
-        m.op.t = (float)(-c / s);
-        m.f = cd(0.0, -s);
-    }
-    return m;
-}
-
-cd cpow_int(cd f, int k) {
-    cd r(1.0, 0.0);
-    for (int i = 0; i < k; ++i) r *= f;
-    return r;
-}
-
-float2 f2(cd z) { return make_float2((float)z.real(), (float)z.imag()); }
-
-// turns offset (units of 2^-64 turn) that multiplies the phase by e^{i arg z}
-uint64_t turns_of_arg(cd z) {
-    const double turns = -std::arg(z) / (2.0 * M_PI);  // e^{-2 pi i t} = e^{i arg z}
-    const double sc = turns * 18446744073709551616.0;   // 2^64
-    return (uint64_t)(int64_t)std::llround(sc);
-}
-
-struct PassRun {
-    PassArgs args;
-    int type;
-    bool epi;
-    bool has_partials;
-    double slot_scale[NSLOT];
-    int slot_param[NSLOT];  // 0..p-1: beta_l ; p..2p-1: gamma_l ; -1 none ; -2: E slots
-    double bytes;
-};
-
-// forward pass arguments (psi in place)
-PassRun fwd_args(const Group &g, const PassDesc &d, const qaoa_cost_s *cost, const double *gamma,
-                 const double *beta, float2 *psi, float2 *lam, double *partials,
-                 unsigned long long *topk, int ktop, int p) {
-    PassRun r{};
-    PassArgs &a = r.args;
-    a.psi = psi;
-    a.lam = lam;
-    a.C = cost->T;
-    a.partials = partials;
-    a.topk_keys = topk;
-    a.n = cost->n;
-    a.lo = g.lo;
-    a.mask = g.mask;
-    a.init = d.init;
-    a.has_cost = d.lc >= 0;
-    a.store_psi = 1;
-    a.precise_phase = 0;
-    a.ktop = d.epi ? ktop : 0;
-    a.amp0 = (float)std::pow(2.0, -0.5 * cost->n);
-    a.cscale = (float)std::ldexp(1.0, -cost->fp.s);
-    a.kmag = 1.f;
-    a.kend = make_float2(1.f, 0.f);
-    a.kend2 = make_float2(1.f, 0.f);
-    const int k = g.kX + g.kY;
-    cd S(1.0, 0.0);  // computed = true * S
-    Mix ma{}, mb{};
-    if (d.la >= 0) {
-        ma = mix_of(beta[d.la]);
-        a.pre = ma.op;
-        S /= cpow_int(ma.f, k);
-    }
-    if (d.lb >= 0) {
-        mb = mix_of(beta[d.lb]);
-        a.post = mb.op;
-    }
-    if (d.lc >= 0) {
-        const uint64_t phi = phase_multiplier(gamma[d.lc], cost->fp.s);
-        const cd Kf = (d.lb >= 0 ? cpow_int(mb.f, k) : cd(1.0, 0.0)) / S;
-        a.phi = phi;
-        a.off = (uint64_t)cost->fp.k_c * phi + turns_of_arg(Kf);
-        a.kmag = (float)std::abs(Kf);
-        S = (d.lb >= 0 ? cpow_int(mb.f, k) : cd(1.0, 0.0));
-    }
-    if (d.lb >= 0) S /= cpow_int(mb.f, k);
-    for (int s = 0; s < NSLOT; ++s) {
-        r.slot_scale[s] = 0.0;
-        r.slot_param[s] = -1;
-    }
-    const double N = std::ldexp(1.0, cost->n);
-    if (!d.epi) {
-        if (d.lc < 0) a.kend = f2(1.0 / S);
-        r.has_partials = false;
-        r.bytes = N * ((d.init ? 0.0 : 8.0) + 8.0 + (d.lc >= 0 ? 4.0 : 0.0));
-    } else {
-        // S = 1/fa^k after the pre mixer; psi_p = fa^k * computed
-        a.kend = f2(1.0 / S);
-        cd Sl(1.0, 0.0);
-        r.slot_param[0] = -2;
-        r.slot_param[1] = -2;
-        r.slot_scale[2] = 1.0;
-        r.slot_param[2] = d.la;
-        Sl /= cpow_int(std::conj(ma.f), g.kY);
-        r.slot_scale[3] = 1.0 / std::norm(Sl);
-        r.slot_param[3] = d.la;
-        Sl /= cpow_int(std::conj(ma.f), g.kX);
-        a.kend2 = f2(1.0 / Sl);
-        r.has_partials = true;
-        r.bytes = N * (8.0 + 4.0 + 8.0);
-    }
-    r.type = g.type;
-    r.epi = d.epi;
-    (void)p;
-    return r;
-}
-
-// reverse pass arguments: undo forward pass d on (psi, lambda)
-PassRun rev_args(const Group &g, const PassDesc &d, const qaoa_cost_s *cost, const double *gamma,
-                 const double *beta, float2 *psi, float2 *lam, double *partials, int p) {
-    PassRun r{};
-    PassArgs &a = r.args;
-    a.psi = psi;
-    a.lam = lam;
-    a.C = cost->T;
-    a.partials = partials;
-    a.n = cost->n;
-    a.lo = g.lo;
-    a.mask = g.mask;
-    a.has_cost = d.lc >= 0;
-    a.store_psi = d.init ? 0 : 1;
-    a.precise_phase = 0;
-    a.cscale = (float)std::ldexp(1.0, -cost->fp.s);
-    a.kmag = 1.f;
-    a.kend = make_float2(1.f, 0.f);
-    const int k = g.kX + g.kY;
-    Mix ma{}, mb{};
-    if (d.la >= 0) {
-        ma = mix_of(beta[d.la]);
-        a.pre = ma.op;
-    }
-    if (d.lb >= 0) {
-        mb = mix_of(beta[d.lb]);
-        a.post = mb.op;
-    }
-    for (int s = 0; s < NSLOT; ++s) {
-        r.slot_scale[s] = 0.0;
-        r.slot_param[s] = -1;
-    }
-    cd S(1.0, 0.0);
-    if (d.lb >= 0) {
-        r.slot_scale[0] = 1.0 / std::norm(S);
-        r.slot_param[0] = d.lb;
-        S /= cpow_int(std::conj(mb.f), g.kX);
-        r.slot_scale[1] = 1.0 / std::norm(S);
-        r.slot_param[1] = d.lb;
-        S /= cpow_int(std::conj(mb.f), g.kY);
-    }
-    if (d.lc >= 0) {
-        r.slot_scale[2] = 1.0 / std::norm(S);
-        r.slot_param[2] = p + d.lc;
-        const uint64_t phi = phase_multiplier(gamma[d.lc], cost->fp.s);
-        const cd Kf = (d.la >= 0 ? cpow_int(std::conj(ma.f), k) : cd(1.0, 0.0)) / S;
-        a.phi = (uint64_t)0 - phi;
-        a.off = (uint64_t)0 - (uint64_t)cost->fp.k_c * phi + turns_of_arg(Kf);
-        a.kmag = (float)std::abs(Kf);
-        S *= Kf;
-    }
-    if (d.la >= 0) {
-        r.slot_scale[3] = 1.0 / std::norm(S);
-        r.slot_param[3] = d.la;
-        S /= cpow_int(std::conj(ma.f), g.kY);
-        r.slot_scale[4] = 1.0 / std::norm(S);
-        r.slot_param[4] = d.la;
-        S /= cpow_int(std::conj(ma.f), g.kX);
-    }
-    if (d.lc < 0) a.kend = f2(1.0 / S);
-    r.has_partials = true;
-    r.type = g.type;
-    r.epi = false;
-    const double N = std::ldexp(1.0, cost->n);
-    r.bytes = N * (16.0 + (a.store_psi ? 16.0 : 0.0) + (d.lc >= 0 ? 4.0 : 0.0));
-    return r;
-}
-
-// Arguments of the 512-thread kernels.  Same scalar bookkeeping as fwd_args /
-// rev_args (computed = true * S), with three register rounds per mixer:
-// forward mixers run rounds A, B, C (pre) and C, B, A (post).
-PassRun fwd3_args(const Group &g, const PassDesc &d, const qaoa_cost_s *cost, const double *gamma,
-                  const double *beta, float2 *psi, float4 *pl, double *partials, unsigned long long *topk, int ktop) {
-    PassRun r{};
-    PassArgs &a = r.args;
-    a.psi = psi;
-    a.pl = pl;
-    a.C = cost->T;
-    a.partials = partials;
-    a.topk_keys = topk;
-    a.n = cost->n;
-    a.lo = g.lo;
-    a.mask = g.mask;
-    a.init = d.init;
-    a.has_cost = d.lc >= 0;
-    a.store_psi = 1;
-    a.ktop = d.epi ? ktop : 0;
-    a.amp0 = (float)std::pow(2.0, -0.5 * cost->n);
-    a.cscale = (float)std::ldexp(1.0, -cost->fp.s);
-    a.kmag = 1.f;
-    a.kend = make_float2(1.f, 0.f);
-    a.kend2 = make_float2(1.f, 0.f);
-    const int k = g.kX + g.kY;
-    cd S(1.0, 0.0);
-    Mix ma{}, mb{};
-    if (d.la >= 0) {
-        ma = mix_of(beta[d.la]);
-        a.pre = ma.op;
-        S /= cpow_int(ma.f, k);
-    }
-    if (d.lb >= 0) {
-        mb = mix_of(beta[d.lb]);
-        a.post = mb.op;
-    }
-    if (d.lc >= 0) {
-        const uint64_t phi = phase_multiplier(gamma[d.lc], cost->fp.s);
-        const cd Kf = (d.lb >= 0 ? cpow_int(mb.f, k) : cd(1.0, 0.0)) / S;
-        a.phi = phi;
-        a.off = (uint64_t)cost->fp.k_c * phi + turns_of_arg(Kf);
-        a.kmag = (float)std::abs(Kf);
-        S = (d.lb >= 0 ? cpow_int(mb.f, k) : cd(1.0, 0.0));
-    }
-    if (d.lb >= 0) S /= cpow_int(mb.f, k);
-    for (int s = 0; s < NSLOT; ++s) {
-        r.slot_scale[s] = 0.0;
-        r.slot_param[s] = -1;
-    }
-    const double N = std::ldexp(1.0, cost->n);
-    if (!d.epi) {
-        if (d.lc < 0) a.kend = f2(1.0 / S);
-        r.has_partials = false;
-        r.bytes = N * ((d.init ? 0.0 : 8.0) + 8.0 + (d.lc >= 0 ? 4.0 : 0.0));
-    } else {
-        a.kend = f2(1.0 / S);
-        cd Sl(1.0, 0.0);
-        r.slot_param[0] = -2;
-        r.slot_param[1] = -2;
-        const int order[3] = {2, 1, 0};  // lambda undo: rounds C, B, A -> slots 2, 3, 4
-        for (int j = 0; j < 3; ++j) {
-            r.slot_scale[2 + j] = 1.0 / std::norm(Sl);
-            r.slot_param[2 + j] = d.la;
-            Sl /= cpow_int(std::conj(ma.f), g.k3[order[j]]);
-        }
-        a.kend2 = f2(1.0 / Sl);
-        r.has_partials = true;
-        r.bytes = N * (8.0 + 4.0 + 16.0);
-    }
-    r.type = g.type;
-    r.epi = d.epi;
-    return r;
-}
-
-PassRun rev3_args(const Group &g, const PassDesc &d, const qaoa_cost_s *cost, const double *gamma,
-                  const double *beta, float4 *pl, double *partials, int p) {
-    PassRun r{};
-    PassArgs &a = r.args;
-    a.pl = pl;
-    a.C = cost->T;
-    a.partials = partials;
-    a.n = cost->n;
-    a.lo = g.lo;
-    a.mask = g.mask;
-    a.has_cost = d.lc >= 0;
-    a.store_psi = d.init ? 0 : 1;
-    a.cscale = (float)std::ldexp(1.0, -cost->fp.s);
-    a.kmag = 1.f;
-    a.kend = make_float2(1.f, 0.f);
-    const int k = g.kX + g.kY;
-    Mix ma{}, mb{};
-    if (d.la >= 0) {
-        ma = mix_of(beta[d.la]);
-        a.pre = ma.op;
-    }
-    if (d.lb >= 0) {
-        mb = mix_of(beta[d.lb]);
-        a.post = mb.op;
-    }
-    for (int s = 0; s < NSLOT; ++s) {
-        r.slot_scale[s] = 0.0;
-        r.slot_param[s] = -1;
-    }
-    cd S(1.0, 0.0);
-    if (d.lb >= 0) {  // undo the post mixer: rounds A, B, C -> slots 0, 1, 2
-        for (int j = 0; j < 3; ++j) {
-            r.slot_scale[j] = 1.0 / std::norm(S);
-            r.slot_param[j] = d.lb;
-            S /= cpow_int(std::conj(mb.f), g.k3[j]);
-        }
-    }
-    if (d.lc >= 0) {
-        r.slot_scale[3] = 1.0 / std::norm(S);
-        r.slot_param[3] = p + d.lc;
-        const uint64_t phi = phase_multiplier(gamma[d.lc], cost->fp.s);
-        const cd Kf = (d.la >= 0 ? cpow_int(std::conj(ma.f), k) : cd(1.0, 0.0)) / S;
-        a.phi = (uint64_t)0 - phi;
-        a.off = (uint64_t)0 - (uint64_t)cost->fp.k_c * phi + turns_of_arg(Kf);
-        a.kmag = (float)std::abs(Kf);
-        S *= Kf;
-    }
-    if (d.la >= 0) {  // undo the pre mixer: rounds C, B, A -> slots 4, 5, 6
-        const int order[3] = {2, 1, 0};
-        for (int j = 0; j < 3; ++j) {
-            r.slot_scale[4 + j] = 1.0 / std::norm(S);
-            r.slot_param[4 + j] = d.la;
-            S /= cpow_int(std::conj(ma.f), g.k3[order[j]]);
-        }
-    }
-    if (d.lc < 0) a.kend = f2(1.0 / S);
-    r.has_partials = true;
-    r.type = g.type;
-    r.epi = false;
-    const double N = std::ldexp(1.0, cost->n);
-    r.bytes = N * (16.0 + (a.store_psi ? 16.0 : 0.0) + (d.lc >= 0 ? 4.0 : 0.0));
-    return r;
-}
-
-qaoa_status ensure_scratch(qaoa_ctx c, int n, int npasses, int ktop, bool grad) {
-    const size_t N = (size_t)1 << n;
-    const int nb = n >= BLOCK_BITS ? (1 << (n - BLOCK_BITS)) : 1;
-    QAOA_TRY(c->work_psi.ensure(N * sizeof(float2), &c->held, c->opt.memory_budget));
-    if (grad && n >= BLOCK_BITS) {
-        if (c->opt.pass_variant == 1) QAOA_TRY(c->lam.ensure(N * sizeof(float2), &c->held, c->opt.memory_budget));
-        else QAOA_TRY(c->pl.ensure(N * sizeof(float4), &c->held, c->opt.memory_budget));
-    }
-    QAOA_TRY(c->partials.ensure((size_t)nb * NSLOT * sizeof(double), &c->held, c->opt.memory_budget));
-    QAOA_TRY(c->pass_sums.ensure((size_t)(npasses + 1) * NSLOT * sizeof(double), &c->held, c->opt.memory_budget));
-    const int kk = std::max(ktop, 1);
-    QAOA_TRY(c->topk_a.ensure((size_t)nb * kk * 8 + 64, &c->held, c->opt.memory_budget));
-    QAOA_TRY(c->topk_b.ensure((size_t)((nb + 255) / 256 + 1) * kk * 8 + 64, &c->held, c->opt.memory_budget));
+qaoa_status check_angles(int p, const double *gamma, const double *beta) {
+    if (p < 0) return fail(QAOA_ERR_INVALID_ARG, "p=%d < 0", p);
+    if (p > 0 && (!gamma || !beta)) return fail(QAOA_ERR_INVALID_ARG, "gamma/beta is null");
+    for (int l = 0; l < p; ++l)
+        if (!std::isfinite(gamma[l]) || !std::isfinite(beta[l]))
+            return fail(QAOA_ERR_INVALID_ARG, "non-finite angle at parameter %d", l);
     return QAOA_OK;
 }
+
+int maxq_of(qaoa_ctx c) { return c->opt.max_fused_qubits ? c->opt.max_fused_qubits : 10; }
 
 // Decode top-K keys: x = 2^33-1 - low33, P = float bits of the high part.
 void decode_keys(const unsigned long long *keys, int k, uint64_t *idx, float *prob) {
@@ -617,130 +204,110 @@ void decode_keys(const unsigned long long *keys, int k, uint64_t *idx, float *pr
     }
 }
 
-// Evolve with the pass schedule on a complex64 buffer; optional gradient.
-qaoa_status run_passes(qaoa_ctx c, const qaoa_cost_s *cost, int p, const double *gamma,
-                       const double *beta, float2 *psi, bool grad, double *E, double *dg, double *db,
-                       int ktop, uint64_t *top_idx, float *top_prob) {
-    const int n = cost->n;
-    const int maxq = c->opt.max_fused_qubits ? c->opt.max_fused_qubits : 10;
-    const auto groups = make_groups(n, maxq);
-    const auto sched = make_schedule((int)groups.size(), p, grad);
-    const int nb = 1 << (n - BLOCK_BITS);
-    const int npasses = (int)sched.size() * (grad ? 2 : 1);
-    QAOA_TRY(ensure_scratch(c, n, npasses, grad ? ktop : 0, grad));
-    const bool use_tma = c->opt.pass_variant != 1;
-    float2 *lam = (grad && !use_tma) ? c->lam.as<float2>() : nullptr;
-    float4 *pl = (grad && use_tma) ? c->pl.as<float4>() : nullptr;
-    double *partials = c->partials.as<double>();
-    double *sums = c->pass_sums.as<double>();
-    // variant 0 (default): forward passes with direct loads (256 threads, two
-    // CTAs per SM), final pass and reverse sweep TMA-pipelined on the
-    // interleaved (psi, lambda) buffer
-    const int variant = c->opt.pass_variant;
-    std::vector<PassRun> runs;
-    if (variant == 3) {
-        for (const auto &d : sched)
-            runs.push_back(fwd3_args(groups[d.group], d, cost, gamma, beta, psi, c->pl.as<float4>(), partials,
-                                     c->topk_a.as<unsigned long long>(), ktop));
-        if (grad)
-            for (int i = (int)sched.size() - 2; i >= 0; --i)
-                runs.push_back(rev3_args(groups[sched[i].group], sched[i], cost, gamma, beta, c->pl.as<float4>(),
-                                         partials, p));
-    } else {
-        for (const auto &d : sched)
-            runs.push_back(fwd_args(groups[d.group], d, cost, gamma, beta, psi, lam, partials,
-                                    c->topk_a.as<unsigned long long>(), ktop, p));
-        if (grad)
-            for (int i = (int)sched.size() - 2; i >= 0; --i)
-                runs.push_back(rev_args(groups[sched[i].group], sched[i], cost, gamma, beta, psi, lam, partials, p));
-    }
-    for (auto &r : runs) {
-        r.args.pl = pl;
-        if (use_tma && r.epi) r.bytes = std::ldexp(28.0, n);  // psi + table in, (psi, lambda) out
-        if (variant == 3) r.args.psi = psi;
-    }
-    if (use_tma) {
-        QAOA_TRY(c->status.ensure(16, &c->held, c->opt.memory_budget));
-        CUDA_TRY(cudaMemsetAsync(c->status.p, 0, 16, c->stream));
-    }
-    int ns = 0;
-    std::vector<int> sum_index(runs.size(), -1);
-    for (size_t i = 0; i < runs.size(); ++i) {
-        const PassRun &r = runs[i];
-        const bool rev = grad && i >= sched.size();
-        {
-            ProfScope ps(c, rev ? 1 : 0, r.bytes);
-            cudaError_t e;
-            unsigned int *stw = c->status.as<unsigned int>();
-            if (variant == 3)
-                e = rev ? launch_rev3(r.type, r.args, c->num_sms, stw, c->stream)
-                        : (r.epi ? launch_epi3(r.type, r.args, c->num_sms, stw, c->stream)
-                                 : launch_fwd3(r.type, r.args, c->num_sms, stw, c->stream));
-            else if (use_tma)
-                e = rev ? launch_rev_pl(r.type, r.args, c->num_sms, stw, c->stream)
-                        : (r.epi ? launch_epi_pl(r.type, r.args, c->num_sms, stw, c->stream)
-                                 : (variant == 0 ? launch_fwd_pass(r.type, false, r.args, c->stream)
-                                                 : launch_fwd_tma(r.type, false, r.args, c->num_sms, stw, c->stream)));
-            else
-                e = rev ? launch_rev_pass(r.type, r.args, c->stream)
-                        : launch_fwd_pass(r.type, r.epi, r.args, c->stream);
-            c->launches_total += 1;
-            if (e) return fail(QAOA_ERR_CUDA, "pass launch failed: %s", cudaGetErrorString(e));
-        }
-        if (r.has_partials) {
-            CUDA_TRY(launch_reduce_partials(partials, nb, NSLOT, sums + (size_t)ns * NSLOT, c->stream));
-            c->launches_total += 1;
-            sum_index[i] = ns++;
-        }
-    }
-    unsigned int hstatus = 0;
-    if (use_tma) CUDA_TRY(cudaMemcpyAsync(&hstatus, c->status.p, 4, cudaMemcpyDeviceToHost, c->stream));
-    if (!grad) {
-        if (use_tma) {
-            CUDA_TRY(cudaStreamSynchronize(c->stream));
-            if (hstatus) return fail(QAOA_ERR_TIMEOUT, "a bounded wait of a layer-pass kernel expired");
-        }
-        return QAOA_OK;
-    }
-    std::vector<double> h((size_t)ns * NSLOT);
-    std::vector<unsigned long long> keys(std::max(ktop, 1));
-    if (ktop > 0) {
-        int which = 0;
-        int nl = 0;
-        CUDA_TRY(launch_topk_merge(c->topk_a.as<unsigned long long>(), nb, ktop,
-                                   c->topk_b.as<unsigned long long>(), &which, &nl, c->stream));
-        c->launches_total += nl;
-        const unsigned long long *src = which ? c->topk_b.as<unsigned long long>() : c->topk_a.as<unsigned long long>();
-        CUDA_TRY(cudaMemcpyAsync(keys.data(), src, (size_t)ktop * 8, cudaMemcpyDeviceToHost, c->stream));
-    }
-    CUDA_TRY(cudaMemcpyAsync(h.data(), sums, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    CUDA_TRY(cudaStreamSynchronize(c->stream));
-    if (hstatus) return fail(QAOA_ERR_TIMEOUT, "a bounded wait of a layer-pass kernel expired");
-    const double cs = std::ldexp(1.0, -cost->fp.s);
-    for (int l = 0; l < p; ++l) dg[l] = db[l] = 0.0;
-    double S0 = 0, S1 = 0;
-    for (size_t i = 0; i < runs.size(); ++i) {
-        if (sum_index[i] < 0) continue;
-        const double *v = &h[(size_t)sum_index[i] * NSLOT];
-        const PassRun &r = runs[i];
-        for (int s = 0; s < NSLOT; ++s) {
-            const int prm = r.slot_param[s];
-            if (prm == -2) {
-                if (s == 0) S0 = v[s];
-                else S1 = v[s];
-            } else if (prm >= 0 && prm < p) {
-                db[prm] += 2.0 * v[s] * r.slot_scale[s];
-            } else if (prm >= p) {
-                dg[prm - p] += 2.0 * cs * v[s] * r.slot_scale[s];
-            }
-        }
-    }
-    *E = cs * (S0 + (double)cost->fp.k_c * S1);
-    if (ktop > 0) decode_keys(keys.data(), ktop, top_idx, top_prob);
+// ---- plan execution ---------------------------------------------------------------
+
+struct PlanRun {
+    int n, p, nitems, ntables;
+    bool grad;
+    int ktop;
+    std::vector<PassPlan> plan;
+    int rows;
+    float2 *psi_ext = nullptr;  // forward-only: evolve in this caller buffer instead of b.psi
+};
+
+// Allocate the working set of a plan for `nitems` items of size n.
+qaoa_status ensure_plan_bufs(qaoa_ctx c, PlanBufs &b, const PlanRun &r) {
+    const size_t N = (size_t)1 << r.n;
+    const int nb = 1 << (r.n - BLOCK_BITS);
+    const size_t B = (size_t)r.nitems;
+    const int64_t bud = c->opt.memory_budget;
+    int64_t *h = &c->held;
+    if (!r.psi_ext) QAOA_TRY(b.psi.ensure(B * N * sizeof(float2), h, bud));
+    if (r.grad) QAOA_TRY(b.pl.ensure(B * N * sizeof(float4), h, bud));
+    QAOA_TRY(b.partials.ensure(B * nb * NSLOT * sizeof(double), h, bud));
+    QAOA_TRY(b.sums.ensure((size_t)std::max(r.rows, 1) * B * NSLOT * sizeof(double), h, bud));
+    QAOA_TRY(b.scal.ensure(r.plan.size() * B * sizeof(PassScal), h, bud));
+    QAOA_TRY(b.slot_scale.ensure(r.plan.size() * B * NSLOT * sizeof(double), h, bud));
+    QAOA_TRY(b.plan.ensure(r.plan.size() * sizeof(PassPlan), h, bud));
+    QAOA_TRY(b.gamma.ensure(B * std::max(r.p, 1) * sizeof(double), h, bud));
+    QAOA_TRY(b.beta.ensure(B * std::max(r.p, 1) * sizeof(double), h, bud));
+    QAOA_TRY(b.item_s.ensure(B * sizeof(int), h, bud));
+    QAOA_TRY(b.item_kc.ensure(B * sizeof(long long), h, bud));
+    QAOA_TRY(b.out_E.ensure(B * sizeof(double), h, bud));
+    QAOA_TRY(b.out_dg.ensure(B * std::max(r.p, 1) * sizeof(double), h, bud));
+    QAOA_TRY(b.out_db.ensure(B * std::max(r.p, 1) * sizeof(double), h, bud));
+    const int kk = std::max(r.ktop, 1);
+    QAOA_TRY(b.topk_a.ensure((size_t)nb * kk * 8 + 64, h, bud));
+    QAOA_TRY(b.topk_b.ensure((size_t)((nb + 255) / 256 + 1) * kk * 8 + 64, h, bud));
+    QAOA_TRY(c->status.ensure(16, h, bud));
     return QAOA_OK;
 }
 
-// Fill one small-n item (n <= 12).
+// Enqueue every pass of the plan (and the partial-sum reductions) on the
+// context stream.  Device-side scalars (b.scal) must be ready.
+qaoa_status enqueue_plan(qaoa_ctx c, PlanBufs &b, const PlanRun &r, const int32_t *tables, const int *item_table,
+                         bool profile) {
+    const int n = r.n;
+    const int nb = 1 << (n - BLOCK_BITS);
+    PassScal *scal = b.scal.as<PassScal>();
+    unsigned int *stw = c->status.as<unsigned int>();
+    for (size_t i = 0; i < r.plan.size(); ++i) {
+        const PassPlan &pl = r.plan[i];
+        PassArgs a{};
+        a.psi = r.psi_ext ? r.psi_ext : b.psi.as<float2>();
+        a.pl = b.pl.as<float4>();
+        a.C = tables;
+        a.item_table = item_table;
+        a.scal = scal + i * r.nitems;
+        a.partials = b.partials.as<double>();
+        a.topk_keys = b.topk_a.as<unsigned long long>();
+        a.n = n;
+        a.lo = pl.lo;
+        a.mask = pl.mask;
+        a.nitems = r.nitems;
+        a.ntables = r.ntables;
+        a.init = pl.init;
+        a.has_pre = pl.la >= 0;
+        a.has_cost = pl.lc >= 0;
+        a.has_post = pl.lb >= 0;
+        a.store = pl.kind == 2 ? !pl.init : 1;
+        a.precise_phase = 0;
+        a.ktop = pl.kind == 1 ? r.ktop : 0;
+        a.amp0 = (float)std::pow(2.0, -0.5 * n);
+        const double bytes = pass_bytes_per_amp(pl) * std::ldexp((double)r.nitems, n);
+        {
+            ProfScope ps(c, pl.kind == 2 ? 1 : 0, bytes, profile);
+            cudaError_t e = pl.kind == 0   ? launch_fwd_pass(pl.type, a, c->stream)
+                            : pl.kind == 1 ? launch_final_pass(pl.type, a, c->num_sms, stw, c->stream)
+                                           : launch_rev_pass(pl.type, a, c->num_sms, stw, c->stream);
+            if (e) return fail(QAOA_ERR_CUDA, "layer-pass launch failed: %s", cudaGetErrorString(e));
+            c->launches_total += 1;
+        }
+        if (pl.sum_index >= 0) {
+            CUDA_TRY(launch_reduce_partials(a.partials, r.nitems, nb,
+                                            b.sums.as<double>() + (size_t)pl.sum_index * r.nitems * NSLOT, c->stream));
+            c->launches_total += 1;
+        }
+    }
+    return QAOA_OK;
+}
+
+DevPlan dev_plan(PlanBufs &b, const PlanRun &r) {
+    DevPlan d{};
+    d.plan = b.plan.as<PassPlan>();
+    d.npasses = (int)r.plan.size();
+    d.p = r.p;
+    d.nitems = r.nitems;
+    d.gamma = b.gamma.as<double>();
+    d.beta = b.beta.as<double>();
+    d.item_s = b.item_s.as<int>();
+    d.item_kc = b.item_kc.as<long long>();
+    d.scal = b.scal.as<PassScal>();
+    d.slot_scale = b.slot_scale.as<double>();
+    return d;
+}
+
+// Fill the small-item block for one parameter set (n <= 12).
 void fill_small(SmallItem &it, const qaoa_cost_s *cost, int p, const double *gamma, const double *beta) {
     std::memset(&it, 0, sizeof(it));
     it.T = cost->T;
@@ -757,32 +324,270 @@ void fill_small(SmallItem &it, const qaoa_cost_s *cost, int p, const double *gam
     }
 }
 
-qaoa_status run_small(qaoa_ctx c, const std::vector<SmallItem> &items, bool fp64, bool grad, int max_n) {
-    QAOA_TRY(c->items.ensure(items.size() * sizeof(SmallItem), &c->held, c->opt.memory_budget));
-    CUDA_TRY(cudaMemcpyAsync(c->items.p, items.data(), items.size() * sizeof(SmallItem), cudaMemcpyHostToDevice,
+qaoa_status run_small(qaoa_ctx c, DevBuf &items_buf, const std::vector<SmallItem> &items, bool fp64, bool grad,
+                      int max_n) {
+    QAOA_TRY(items_buf.ensure(items.size() * sizeof(SmallItem), &c->held, c->opt.memory_budget));
+    CUDA_TRY(cudaMemcpyAsync(items_buf.p, items.data(), items.size() * sizeof(SmallItem), cudaMemcpyHostToDevice,
                              c->stream));
     double bytes = 0;
     for (auto &it : items) bytes += std::ldexp(4.0, it.n);
     ProfScope ps(c, 3, bytes);
-    CUDA_TRY(launch_small(c->items.as<SmallItem>(), (int)items.size(), max_n, fp64, grad, c->stream));
+    CUDA_TRY(launch_small(items_buf.as<SmallItem>(), (int)items.size(), max_n, fp64, grad, c->stream));
     c->launches_total += 1;
     return QAOA_OK;
 }
 
-qaoa_status check_angles(int p, const double *gamma, const double *beta) {
-    if (p < 0) return fail(QAOA_ERR_INVALID_ARG, "p=%d < 0", p);
-    if (p > 0 && (!gamma || !beta)) return fail(QAOA_ERR_INVALID_ARG, "gamma/beta is null");
-    for (int l = 0; l < p; ++l)
-        if (!std::isfinite(gamma[l]) || !std::isfinite(beta[l]))
-            return fail(QAOA_ERR_INVALID_ARG, "non-finite angle at layer %d", l + 1);
+qaoa_status status_check(qaoa_ctx c) {
+    unsigned int hs = 0;
+    CUDA_TRY(cudaMemcpyAsync(&hs, c->status.p, 4, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (hs) return fail(QAOA_ERR_TIMEOUT, "a bounded wait of a layer-pass kernel expired");
+    return QAOA_OK;
+}
+
+// Single-item evaluation on the pass path (n >= 13): forward only (psi ends in
+// b.psi) or forward + adjoint (E, gradient, optional top-K).
+qaoa_status run_single(qaoa_ctx c, const qaoa_cost_s *cost, int p, const double *gamma, const double *beta,
+                       bool grad, float2 *psi_out, double *E, double *dg, double *db, int ktop, uint64_t *top_idx,
+                       float *top_prob) {
+    PlanRun r;
+    r.n = cost->n;
+    r.p = p;
+    r.nitems = 1;
+    r.ntables = 1;
+    r.grad = grad;
+    r.ktop = grad ? ktop : 0;
+    r.plan = make_plan(cost->n, p, grad, maxq_of(c));
+    r.rows = plan_rows(r.plan);
+    r.psi_ext = grad ? nullptr : psi_out;
+    PlanBufs &b = c->single;
+    QAOA_TRY(ensure_plan_bufs(c, b, r));
+    // scalars on the host (one item)
+    std::vector<PassScal> sc(r.plan.size());
+    std::vector<double> ss(r.plan.size() * NSLOT);
+    for (size_t i = 0; i < r.plan.size(); ++i)
+        pass_scalars(r.plan[i], gamma, beta, cost->fp.s, cost->fp.k_c, &sc[i], &ss[i * NSLOT]);
+    const int s_h = cost->fp.s;
+    const long long kc_h = cost->fp.k_c;
+    CUDA_TRY(cudaMemcpyAsync(b.scal.p, sc.data(), sc.size() * sizeof(PassScal), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(b.slot_scale.p, ss.data(), ss.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(b.plan.p, r.plan.data(), r.plan.size() * sizeof(PassPlan), cudaMemcpyHostToDevice,
+                             c->stream));
+    CUDA_TRY(cudaMemcpyAsync(b.item_s.p, &s_h, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(b.item_kc.p, &kc_h, sizeof(long long), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(cudaMemsetAsync(c->status.p, 0, 16, c->stream));
+    QAOA_TRY(enqueue_plan(c, b, r, cost->T, nullptr, true));
+    if (!grad) return status_check(c);
+    DevPlan d = dev_plan(b, r);
+    CUDA_TRY(launch_assemble(d, b.sums.as<double>(), b.out_E.as<double>(), b.out_dg.as<double>(),
+                             b.out_db.as<double>(), c->stream));
+    c->launches_total += 1;
+    std::vector<unsigned long long> keys(std::max(ktop, 1));
+    if (ktop > 0) {
+        int which = 0, nl = 0;
+        const int nb = 1 << (r.n - BLOCK_BITS);
+        CUDA_TRY(launch_topk_merge(b.topk_a.as<unsigned long long>(), nb, ktop, b.topk_b.as<unsigned long long>(),
+                                   &which, &nl, c->stream));
+        c->launches_total += nl;
+        const void *src = which ? b.topk_b.p : b.topk_a.p;
+        CUDA_TRY(cudaMemcpyAsync(keys.data(), src, (size_t)ktop * 8, cudaMemcpyDeviceToHost, c->stream));
+    }
+    CUDA_TRY(cudaMemcpyAsync(E, b.out_E.p, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(dg, b.out_dg.p, p * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(db, b.out_db.p, p * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    QAOA_TRY(status_check(c));
+    if (ktop > 0) decode_keys(keys.data(), ktop, top_idx, top_prob);
     return QAOA_OK;
 }
 
 }  // namespace
 
-// ============================================================================
-// ABI
-// ============================================================================
+namespace {
+
+// ---- batches -------------------------------------------------------------------------
+
+// Items of one n evaluated together on the pass path.
+struct BatchGroup {
+    int n = 0;
+    std::vector<int> items;               // indices into the caller's batch
+    std::vector<const qaoa_cost_s *> tabs;  // distinct tables
+    std::vector<int> item_table;          // per item, index into tabs
+    PlanRun r;
+    PlanBufs *b = nullptr;
+    const int32_t *tables = nullptr;      // contiguous tables (device)
+    const int *item_table_dev = nullptr;
+};
+
+// Small items (n <= 12) evaluated by the shared-memory-resident kernel.
+struct SmallSet {
+    std::vector<int> items;
+    std::vector<SmallItem> host;
+    std::vector<int> item_s;
+    std::vector<long long> item_kc;
+    int max_n = 1;
+    PlanBufs *b = nullptr;  // gamma/beta/item_s/item_kc/adam/history buffers
+};
+
+qaoa_status build_groups(qaoa_ctx c, int nq, const qaoa_cost *costs, const int32_t *item_cost, int B, int p,
+                         bool grad, std::vector<BatchGroup> &groups, SmallSet &small) {
+    std::map<int, int> gi;
+    for (int b = 0; b < B; ++b) {
+        const int ci = item_cost ? item_cost[b] : 0;
+        if (ci < 0 || ci >= nq || !costs[ci]) return fail(QAOA_ERR_INVALID_ARG, "item %d: bad cost index %d", b, ci);
+        const qaoa_cost_s *cs = costs[ci];
+        if (cs->n <= SMALL_MAXN) {
+            small.items.push_back(b);
+            small.max_n = std::max(small.max_n, cs->n);
+            continue;
+        }
+        auto it = gi.find(cs->n);
+        if (it == gi.end()) {
+            it = gi.emplace(cs->n, (int)groups.size()).first;
+            groups.emplace_back();
+            groups.back().n = cs->n;
+        }
+        BatchGroup &g = groups[it->second];
+        g.items.push_back(b);
+        int t = -1;
+        for (size_t k = 0; k < g.tabs.size(); ++k)
+            if (g.tabs[k] == cs) t = (int)k;
+        if (t < 0) {
+            t = (int)g.tabs.size();
+            g.tabs.push_back(cs);
+        }
+        g.item_table.push_back(t);
+    }
+    for (BatchGroup &g : groups) {
+        g.r.n = g.n;
+        g.r.p = p;
+        g.r.nitems = (int)g.items.size();
+        g.r.ntables = (int)g.tabs.size();
+        g.r.grad = grad;
+        g.r.ktop = 0;
+        g.r.plan = make_plan(g.n, p, grad, maxq_of(c));
+        g.r.rows = plan_rows(g.r.plan);
+        auto &slot = c->groups[g.n];
+        if (!slot) slot.reset(new PlanBufs());
+        g.b = slot.get();
+        QAOA_TRY(ensure_plan_bufs(c, *g.b, g.r));
+        const size_t N = (size_t)1 << g.n;
+        if (g.tabs.size() == 1) {
+            g.tables = g.tabs[0]->T;
+            g.item_table_dev = nullptr;
+        } else {
+            QAOA_TRY(g.b->tables.ensure(g.tabs.size() * N * 4, &c->held, c->opt.memory_budget));
+            for (size_t k = 0; k < g.tabs.size(); ++k)
+                CUDA_TRY(cudaMemcpyAsync(g.b->tables.as<int32_t>() + k * N, g.tabs[k]->T, N * 4,
+                                         cudaMemcpyDeviceToDevice, c->stream));
+            QAOA_TRY(g.b->item_table.ensure(g.items.size() * sizeof(int), &c->held, c->opt.memory_budget));
+            CUDA_TRY(cudaMemcpyAsync(g.b->item_table.p, g.item_table.data(), g.items.size() * sizeof(int),
+                                     cudaMemcpyHostToDevice, c->stream));
+            g.tables = g.b->tables.as<int32_t>();
+            g.item_table_dev = g.b->item_table.as<int>();
+        }
+        std::vector<int> s_h(g.items.size());
+        std::vector<long long> kc_h(g.items.size());
+        for (size_t i = 0; i < g.items.size(); ++i) {
+            s_h[i] = g.tabs[g.item_table[i]]->fp.s;
+            kc_h[i] = g.tabs[g.item_table[i]]->fp.k_c;
+        }
+        CUDA_TRY(cudaMemcpyAsync(g.b->item_s.p, s_h.data(), s_h.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                 c->stream));
+        CUDA_TRY(cudaMemcpyAsync(g.b->item_kc.p, kc_h.data(), kc_h.size() * sizeof(long long),
+                                 cudaMemcpyHostToDevice, c->stream));
+        CUDA_TRY(cudaMemcpyAsync(g.b->plan.p, g.r.plan.data(), g.r.plan.size() * sizeof(PassPlan),
+                                 cudaMemcpyHostToDevice, c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));  // host vectors above are about to go out of scope
+    }
+    return QAOA_OK;
+}
+
+// Upload the angles of the group's items ([items][p], gathered from the batch).
+qaoa_status upload_angles(qaoa_ctx c, const std::vector<int> &items, int p, const double *gamma, const double *beta,
+                          DevBuf &dg, DevBuf &db) {
+    std::vector<double> g((size_t)items.size() * p), b((size_t)items.size() * p);
+    for (size_t i = 0; i < items.size(); ++i)
+        for (int l = 0; l < p; ++l) {
+            g[i * p + l] = gamma[(size_t)items[i] * p + l];
+            b[i * p + l] = beta[(size_t)items[i] * p + l];
+        }
+    QAOA_TRY(dg.ensure(g.size() * sizeof(double), &c->held, c->opt.memory_budget));
+    QAOA_TRY(db.ensure(b.size() * sizeof(double), &c->held, c->opt.memory_budget));
+    CUDA_TRY(cudaMemcpyAsync(dg.p, g.data(), g.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(db.p, b.data(), b.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return QAOA_OK;
+}
+
+// One evaluation of a group from its device angles: scalars, passes,
+// reductions, and (grad) the assembled E and gradient in b.out_*.
+qaoa_status enqueue_group(qaoa_ctx c, BatchGroup &g, bool profile) {
+    DevPlan d = dev_plan(*g.b, g.r);
+    CUDA_TRY(launch_prep_scalars(d, c->stream));
+    c->launches_total += 1;
+    QAOA_TRY(enqueue_plan(c, *g.b, g.r, g.tables, g.item_table_dev, profile));
+    if (g.r.grad) {
+        CUDA_TRY(launch_assemble(d, g.b->sums.as<double>(), g.b->out_E.as<double>(), g.b->out_dg.as<double>(),
+                                 g.b->out_db.as<double>(), c->stream));
+        c->launches_total += 1;
+    }
+    return QAOA_OK;
+}
+
+// Small items: host blocks with device output pointers; the resident kernel
+// reads angles from the blocks (refreshed on the device by small_prep).
+qaoa_status build_small(qaoa_ctx c, SmallSet &s, const qaoa_cost *costs, const int32_t *item_cost, int p,
+                        const double *gamma, const double *beta, bool grad) {
+    if (s.items.empty()) return QAOA_OK;
+    auto &slot = c->groups[0];
+    if (!slot) slot.reset(new PlanBufs());
+    s.b = slot.get();
+    const size_t per = 1 + 2 * (size_t)p;
+    const size_t K = s.items.size();
+    QAOA_TRY(s.b->small_out.ensure(K * per * sizeof(double) + 64, &c->held, c->opt.memory_budget));
+    s.host.resize(K);
+    s.item_s.resize(K);
+    s.item_kc.resize(K);
+    for (size_t i = 0; i < K; ++i) {
+        const int b = s.items[i];
+        const qaoa_cost_s *cs = costs[item_cost ? item_cost[b] : 0];
+        fill_small(s.host[i], cs, p, gamma + (size_t)b * p, beta + (size_t)b * p);
+        s.host[i].grad = grad ? 1 : 0;
+        s.host[i].out = s.b->small_out.as<double>() + i * per;
+        s.item_s[i] = cs->fp.s;
+        s.item_kc[i] = cs->fp.k_c;
+    }
+    QAOA_TRY(s.b->small_items.ensure(K * sizeof(SmallItem), &c->held, c->opt.memory_budget));
+    CUDA_TRY(cudaMemcpyAsync(s.b->small_items.p, s.host.data(), K * sizeof(SmallItem), cudaMemcpyHostToDevice,
+                             c->stream));
+    QAOA_TRY(s.b->item_s.ensure(K * sizeof(int), &c->held, c->opt.memory_budget));
+    QAOA_TRY(s.b->item_kc.ensure(K * sizeof(long long), &c->held, c->opt.memory_budget));
+    CUDA_TRY(cudaMemcpyAsync(s.b->item_s.p, s.item_s.data(), K * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(s.b->item_kc.p, s.item_kc.data(), K * sizeof(long long), cudaMemcpyHostToDevice,
+                             c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return QAOA_OK;
+}
+
+qaoa_status enqueue_small(qaoa_ctx c, SmallSet &s, int p, bool from_device_angles) {
+    if (s.items.empty()) return QAOA_OK;
+    const int K = (int)s.items.size();
+    if (from_device_angles) {
+        CUDA_TRY(launch_small_prep(s.b->small_items.as<SmallItem>(), K, s.b->gamma.as<double>(),
+                                   s.b->beta.as<double>(), p, s.b->item_s.as<int>(), s.b->item_kc.as<long long>(),
+                                   c->stream));
+        c->launches_total += 1;
+    }
+    double bytes = 0;
+    for (auto &it : s.host) bytes += std::ldexp(4.0, it.n);
+    ProfScope ps(c, 3, bytes, !from_device_angles);
+    CUDA_TRY(launch_small(s.b->small_items.as<SmallItem>(), K, s.max_n, false, s.host[0].grad != 0, c->stream));
+    c->launches_total += 1;
+    return QAOA_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char *qaoa_last_error(void) { return qaoa::last_error(); }
@@ -792,21 +597,20 @@ qaoa_status qaoa_ctx_create(int device, void *cuda_stream, const qaoa_options *o
     *out = nullptr;
     int count = 0;
     CUDA_TRY(cudaGetDeviceCount(&count));
-    if (device < 0 || device >= count) return fail(QAOA_ERR_INVALID_ARG, "device %d not present (%d devices)", device, count);
+    if (device < 0 || device >= count)
+        return fail(QAOA_ERR_INVALID_ARG, "device %d not present (%d devices)", device, count);
     QAOA_TRY(set_device(device));
+    qaoa_options o{};
+    if (opt) o = *opt;
+    if (o.max_fused_qubits != 0 && (o.max_fused_qubits < 3 || o.max_fused_qubits > 10))
+        return fail(QAOA_ERR_INVALID_ARG, "max_fused_qubits must be 0 or in [3, 10]");
+    for (int k = 0; k < 6; ++k)
+        if (o.reserved[k]) return fail(QAOA_ERR_INVALID_ARG, "options.reserved[%d] must be zero", k);
     auto *c = new qaoa_ctx_s();
     c->device = device;
     c->stream = (cudaStream_t)cuda_stream;
-    if (opt) c->opt = *opt;
+    c->opt = o;
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
-    if (c->opt.pass_variant < 0 || c->opt.pass_variant > 3) {
-        delete c;
-        return fail(QAOA_ERR_INVALID_ARG, "pass_variant must be 0, 1, 2 or 3");
-    }
-    if (c->opt.max_fused_qubits != 0 && (c->opt.max_fused_qubits < 3 || c->opt.max_fused_qubits > 10)) {
-        delete c;
-        return fail(QAOA_ERR_INVALID_ARG, "max_fused_qubits must be 0 or in [3, 10]");
-    }
     *out = c;
     return QAOA_OK;
 }
@@ -820,6 +624,7 @@ void qaoa_ctx_destroy(qaoa_ctx c) {
         cudaEventDestroy(r.b);
     }
     for (auto e : c->ev_free) cudaEventDestroy(e);
+    if (c->aux_stream) cudaStreamDestroy(c->aux_stream);
     delete c;
 }
 
@@ -935,12 +740,11 @@ qaoa_status qaoa_forward(qaoa_ctx c, qaoa_cost cost, int p, const double *gamma,
         QAOA_TRY(c->small_out.ensure(8 * (1 + 2 * (size_t)p) + 64, &c->held, c->opt.memory_budget));
         items[0].out = c->small_out.as<double>();
         items[0].psi_out = st->amps;
-        QAOA_TRY(run_small(c, items, fp64, false, n));
+        QAOA_TRY(run_small(c, c->small_items, items, fp64, false, n));
         CUDA_TRY(cudaStreamSynchronize(c->stream));
     } else {
-        QAOA_TRY(run_passes(c, cost, p, gamma, beta, (float2 *)st->amps, false, nullptr, nullptr, nullptr, 0,
-                            nullptr, nullptr));
-        CUDA_TRY(cudaStreamSynchronize(c->stream));
+        QAOA_TRY(run_single(c, cost, p, gamma, beta, false, static_cast<float2 *>(st->amps), nullptr, nullptr,
+                            nullptr, 0, nullptr, nullptr));
     }
     if (fresh) *inout = fresh.release();
     return QAOA_OK;
@@ -971,17 +775,19 @@ qaoa_status qaoa_state_device_ptr(qaoa_state s, void **amps, int64_t *count) {
 qaoa_status qaoa_expect(qaoa_ctx c, qaoa_cost cost, qaoa_state s, double *out) {
     if (!c || !cost || !s || !out) return fail(QAOA_ERR_INVALID_ARG, "null argument");
     if (s->n != cost->n) return fail(QAOA_ERR_INVALID_ARG, "state and cost differ in n");
-    if (s->fp64) return fail(QAOA_ERR_INVALID_ARG, "qaoa_expect takes complex64 states; complex128 states report E from qaoa_grad");
+    if (s->fp64)
+        return fail(QAOA_ERR_INVALID_ARG,
+                    "qaoa_expect takes complex64 states; complex128 states report E from qaoa_grad");
     QAOA_TRY(set_device(c->device));
     const int n = s->n;
     const int nb = (int)((((size_t)1 << n) + 8191) / 8192);
-    QAOA_TRY(c->partials.ensure((size_t)nb * NSLOT * 8, &c->held, c->opt.memory_budget));
-    QAOA_TRY(c->pass_sums.ensure(NSLOT * 8 * 2, &c->held, c->opt.memory_budget));
-    CUDA_TRY(launch_expect((const float2 *)s->amps, cost->T, n, c->partials.as<double>(), c->stream));
+    QAOA_TRY(c->partials_e.ensure((size_t)nb * NSLOT * 8, &c->held, c->opt.memory_budget));
+    QAOA_TRY(c->sums_e.ensure(NSLOT * 8, &c->held, c->opt.memory_budget));
+    CUDA_TRY(launch_expect((const float2 *)s->amps, cost->T, n, c->partials_e.as<double>(), c->stream));
+    CUDA_TRY(launch_reduce_partials(c->partials_e.as<double>(), 1, nb, c->sums_e.as<double>(), c->stream));
     c->launches_total += 2;
-    CUDA_TRY(launch_reduce_partials(c->partials.as<double>(), nb, NSLOT, c->pass_sums.as<double>(), c->stream));
     double h[NSLOT];
-    CUDA_TRY(cudaMemcpyAsync(h, c->pass_sums.p, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(h, c->sums_e.p, sizeof h, cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
     *out = std::ldexp(h[0] + (double)cost->fp.k_c * h[1], -cost->fp.s);
     return QAOA_OK;
@@ -1008,12 +814,12 @@ qaoa_status qaoa_topk(qaoa_ctx c, qaoa_cost cost, qaoa_state s, int k, uint64_t 
     std::vector<unsigned long long> keys(k);
     const void *src = which ? c->topk_b.p : c->topk_a.p;
     CUDA_TRY(cudaMemcpyAsync(keys.data(), src, (size_t)k * 8, cudaMemcpyDeviceToHost, c->stream));
-    std::vector<int32_t> tv(k);
     float2 amp_min = make_float2(0, 0);
     CUDA_TRY(cudaMemcpyAsync(&amp_min, (const float2 *)s->amps + cost->argmin, 8, cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
     decode_keys(keys.data(), k, idx, prob);
     if (cost_out) {
+        std::vector<int32_t> tv(k);
         for (int i = 0; i < k; ++i)
             CUDA_TRY(cudaMemcpyAsync(&tv[i], cost->T + idx[i], 4, cudaMemcpyDeviceToHost, c->stream));
         CUDA_TRY(cudaStreamSynchronize(c->stream));
@@ -1046,7 +852,7 @@ qaoa_status qaoa_grad(qaoa_ctx c, qaoa_cost cost, int p, const double *gamma, co
         items[0].out = c->small_out.as<double>();
         items[0].ktop = k_top;
         items[0].topk = reinterpret_cast<unsigned long long *>(c->small_out.as<double>() + 1 + 2 * p);
-        QAOA_TRY(run_small(c, items, fp64, true, n));
+        QAOA_TRY(run_small(c, c->small_items, items, fp64, true, n));
         std::vector<double> h(1 + 2 * p + 16);
         CUDA_TRY(cudaMemcpyAsync(h.data(), c->small_out.p, h.size() * 8, cudaMemcpyDeviceToHost, c->stream));
         CUDA_TRY(cudaStreamSynchronize(c->stream));
@@ -1055,52 +861,57 @@ qaoa_status qaoa_grad(qaoa_ctx c, qaoa_cost cost, int p, const double *gamma, co
             dgamma[l] = h[1 + l];
             dbeta[l] = h[1 + p + l];
         }
-        if (k_top > 0) decode_keys(reinterpret_cast<const unsigned long long *>(&h[1 + 2 * p]), k_top, top_idx, top_prob);
+        if (k_top > 0)
+            decode_keys(reinterpret_cast<const unsigned long long *>(&h[1 + 2 * p]), k_top, top_idx, top_prob);
         return QAOA_OK;
     }
     if (fp64) return fail(QAOA_ERR_INVALID_ARG, "complex128 states are limited to n <= 12");
-    QAOA_TRY(ensure_scratch(c, n, 1, k_top, true));
-    return run_passes(c, cost, p, gamma, beta, c->work_psi.as<float2>(), true, out_expect, dgamma, dbeta, k_top,
-                      top_idx, top_prob);
+    return run_single(c, cost, p, gamma, beta, true, nullptr, out_expect, dgamma, dbeta, k_top, top_idx, top_prob);
 }
 
 qaoa_status qaoa_grad_batch(qaoa_ctx c, int nq, const qaoa_cost *costs, const int32_t *item_cost, int B, int p,
                             const double *gamma, const double *beta, double *expect, double *dgamma, double *dbeta) {
     if (!c || !costs || nq < 1 || B < 1 || !gamma || !beta || !expect)
         return fail(QAOA_ERR_INVALID_ARG, "bad batch arguments");
-    if ((dgamma == nullptr) != (dbeta == nullptr)) return fail(QAOA_ERR_INVALID_ARG, "dgamma and dbeta must both be set or both be null");
+    if ((dgamma == nullptr) != (dbeta == nullptr))
+        return fail(QAOA_ERR_INVALID_ARG, "dgamma and dbeta must both be set or both be null");
     if (p < 1 || p > SMALL_MAXP) return fail(QAOA_ERR_INVALID_ARG, "p=%d not in [1, %d]", p, SMALL_MAXP);
-    for (int b = 0; b < B; ++b) {
-        const int ci = item_cost ? item_cost[b] : 0;
-        if (ci < 0 || ci >= nq || !costs[ci]) return fail(QAOA_ERR_INVALID_ARG, "item %d: bad cost index %d", b, ci);
-    }
+    if (c->opt.state_fp64) return fail(QAOA_ERR_INVALID_ARG, "batched evaluation runs in complex64 only");
     QAOA_TRY(check_angles(p * B, gamma, beta));
     QAOA_TRY(set_device(c->device));
     const bool grad = dgamma != nullptr;
-    // small items: one resident-kernel launch
-    std::vector<SmallItem> small;
-    std::vector<int> small_ids;
-    int max_small_n = 1;
-    for (int b = 0; b < B; ++b) {
-        const qaoa_cost_s *cs = costs[item_cost ? item_cost[b] : 0];
-        if (cs->n > SMALL_MAXN) continue;
-        SmallItem it;
-        fill_small(it, cs, p, gamma + (size_t)b * p, beta + (size_t)b * p);
-        it.grad = grad ? 1 : 0;
-        small.push_back(it);
-        small_ids.push_back(b);
-        max_small_n = std::max(max_small_n, cs->n);
+    std::vector<BatchGroup> groups;
+    SmallSet small;
+    QAOA_TRY(build_groups(c, nq, costs, item_cost, B, p, grad, groups, small));
+    QAOA_TRY(build_small(c, small, costs, item_cost, p, gamma, beta, grad));
+    CUDA_TRY(cudaMemsetAsync(c->status.p, 0, 16, c->stream));
+    QAOA_TRY(enqueue_small(c, small, p, false));
+    for (BatchGroup &g : groups) {
+        QAOA_TRY(upload_angles(c, g.items, p, gamma, beta, g.b->gamma, g.b->beta));
+        QAOA_TRY(enqueue_group(c, g, true));
+        if (!grad) {
+            // forward only: <H_C> of every item's final state
+            const int nb = 1 << (g.n - BLOCK_BITS);
+            const size_t N = (size_t)1 << g.n;
+            for (size_t i = 0; i < g.items.size(); ++i) {
+                CUDA_TRY(launch_expect(g.b->psi.as<float2>() + i * N, g.tabs[g.item_table[i]]->T, g.n,
+                                       g.b->partials.as<double>() + i * nb * NSLOT, c->stream));
+                c->launches_total += 1;
+            }
+            CUDA_TRY(launch_reduce_partials(g.b->partials.as<double>(), (int)g.items.size(), nb,
+                                            g.b->sums.as<double>(), c->stream));
+            c->launches_total += 1;
+        }
     }
-    if (!small.empty()) {
+    QAOA_TRY(status_check(c));
+    // results
+    if (!small.items.empty()) {
         const size_t per = 1 + 2 * (size_t)p;
-        QAOA_TRY(c->small_out.ensure(small.size() * per * 8 + 64, &c->held, c->opt.memory_budget));
-        for (size_t i = 0; i < small.size(); ++i) small[i].out = c->small_out.as<double>() + i * per;
-        QAOA_TRY(run_small(c, small, false, grad, max_small_n));
-        std::vector<double> h(small.size() * per);
-        CUDA_TRY(cudaMemcpyAsync(h.data(), c->small_out.p, h.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+        std::vector<double> h(small.items.size() * per);
+        CUDA_TRY(cudaMemcpyAsync(h.data(), small.b->small_out.p, h.size() * 8, cudaMemcpyDeviceToHost, c->stream));
         CUDA_TRY(cudaStreamSynchronize(c->stream));
-        for (size_t i = 0; i < small.size(); ++i) {
-            const int b = small_ids[i];
+        for (size_t i = 0; i < small.items.size(); ++i) {
+            const int b = small.items[i];
             expect[b] = h[i * per];
             if (grad)
                 for (int l = 0; l < p; ++l) {
@@ -1109,26 +920,189 @@ qaoa_status qaoa_grad_batch(qaoa_ctx c, int nq, const qaoa_cost *costs, const in
                 }
         }
     }
-    // large items: the pass schedule, one item at a time on the context stream
-    for (int b = 0; b < B; ++b) {
-        const qaoa_cost_s *cs = costs[item_cost ? item_cost[b] : 0];
-        if (cs->n <= SMALL_MAXN) continue;
+    for (BatchGroup &g : groups) {
+        const size_t K = g.items.size();
         if (grad) {
-            QAOA_TRY(qaoa_grad(c, const_cast<qaoa_cost>(cs), p, gamma + (size_t)b * p, beta + (size_t)b * p, &expect[b],
-                               dgamma + (size_t)b * p, dbeta + (size_t)b * p, 0, nullptr, nullptr));
+            std::vector<double> E(K), dg(K * p), db(K * p);
+            CUDA_TRY(cudaMemcpyAsync(E.data(), g.b->out_E.p, K * 8, cudaMemcpyDeviceToHost, c->stream));
+            CUDA_TRY(cudaMemcpyAsync(dg.data(), g.b->out_dg.p, K * p * 8, cudaMemcpyDeviceToHost, c->stream));
+            CUDA_TRY(cudaMemcpyAsync(db.data(), g.b->out_db.p, K * p * 8, cudaMemcpyDeviceToHost, c->stream));
+            CUDA_TRY(cudaStreamSynchronize(c->stream));
+            for (size_t i = 0; i < K; ++i) {
+                const int b = g.items[i];
+                expect[b] = E[i];
+                for (int l = 0; l < p; ++l) {
+                    dgamma[(size_t)b * p + l] = dg[i * p + l];
+                    dbeta[(size_t)b * p + l] = db[i * p + l];
+                }
+            }
         } else {
-            QAOA_TRY(ensure_scratch(c, cs->n, 1, 0, false));
-            QAOA_TRY(run_passes(c, cs, p, gamma + (size_t)b * p, beta + (size_t)b * p, c->work_psi.as<float2>(), false,
-                                nullptr, nullptr, nullptr, 0, nullptr, nullptr));
-            qaoa_state_s tmp;
-            tmp.n = cs->n;
-            tmp.amps = c->work_psi.p;
-            tmp.device = c->device;
-            qaoa_status st = qaoa_expect(c, const_cast<qaoa_cost>(cs), &tmp, &expect[b]);
-            tmp.amps = nullptr;
-            QAOA_TRY(st);
+            std::vector<double> S(K * NSLOT);
+            CUDA_TRY(cudaMemcpyAsync(S.data(), g.b->sums.p, S.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+            CUDA_TRY(cudaStreamSynchronize(c->stream));
+            for (size_t i = 0; i < K; ++i) {
+                const qaoa_cost_s *cs = g.tabs[g.item_table[i]];
+                expect[g.items[i]] = std::ldexp(S[i * NSLOT] + (double)cs->fp.k_c * S[i * NSLOT + 1], -cs->fp.s);
+            }
         }
     }
+    return QAOA_OK;
+}
+
+qaoa_status qaoa_optimize_adam(qaoa_ctx c, int nq, const qaoa_cost *costs, const int32_t *item_cost, int B, int p,
+                               double *gamma, double *beta, const qaoa_adam_options *aopt, double *history,
+                               double *final_expect) {
+    if (!c || !costs || nq < 1 || B < 1 || !gamma || !beta || !aopt)
+        return fail(QAOA_ERR_INVALID_ARG, "bad optimiser arguments");
+    if (p < 1 || p > SMALL_MAXP) return fail(QAOA_ERR_INVALID_ARG, "p=%d not in [1, %d]", p, SMALL_MAXP);
+    if (aopt->iterations < 1) return fail(QAOA_ERR_INVALID_ARG, "iterations=%d < 1", aopt->iterations);
+    if (c->opt.state_fp64) return fail(QAOA_ERR_INVALID_ARG, "the optimiser runs in complex64 only");
+    QAOA_TRY(check_angles(p * B, gamma, beta));
+    const double lr = aopt->lr > 0 ? aopt->lr : 0.01;
+    const double b1 = aopt->beta1 > 0 ? aopt->beta1 : 0.9;
+    const double b2 = aopt->beta2 > 0 ? aopt->beta2 : 0.999;
+    const double eps = aopt->eps > 0 ? aopt->eps : 1e-8;
+    if (!(lr < 1e6) || b1 >= 1.0 || b2 >= 1.0) return fail(QAOA_ERR_INVALID_ARG, "bad Adam hyper-parameters");
+    const int iters = aopt->iterations;
+    QAOA_TRY(set_device(c->device));
+    if (!c->aux_stream) CUDA_TRY(cudaStreamCreateWithFlags(&c->aux_stream, cudaStreamNonBlocking));
+    std::vector<BatchGroup> groups;
+    SmallSet small;
+    QAOA_TRY(build_groups(c, nq, costs, item_cost, B, p, true, groups, small));
+    QAOA_TRY(build_small(c, small, costs, item_cost, p, gamma, beta, true));
+    // every group (and the small set) keeps its angles, moments and history on the device
+    struct Opt {
+        PlanBufs *b;
+        const std::vector<int> *items;
+        AdamArgs a;
+    };
+    std::vector<Opt> opts;
+    auto setup = [&](PlanBufs *b, const std::vector<int> &items, const double *dg, const double *db, int gstride,
+                     const double *E, int estride) -> qaoa_status {
+        const size_t K = items.size();
+        QAOA_TRY(upload_angles(c, items, p, gamma, beta, b->gamma, b->beta));
+        QAOA_TRY(b->adam_m.ensure(2 * K * p * 8, &c->held, c->opt.memory_budget));
+        QAOA_TRY(b->adam_v.ensure(2 * K * p * 8, &c->held, c->opt.memory_budget));
+        QAOA_TRY(b->adam_step.ensure(16, &c->held, c->opt.memory_budget));
+        QAOA_TRY(b->history.ensure((size_t)iters * K * 8, &c->held, c->opt.memory_budget));
+        CUDA_TRY(cudaMemsetAsync(b->adam_m.p, 0, 2 * K * p * 8, c->stream));
+        CUDA_TRY(cudaMemsetAsync(b->adam_v.p, 0, 2 * K * p * 8, c->stream));
+        CUDA_TRY(cudaMemsetAsync(b->adam_step.p, 0, 16, c->stream));
+        AdamArgs a{};
+        a.gamma = b->gamma.as<double>();
+        a.beta = b->beta.as<double>();
+        a.dgamma = dg;
+        a.dbeta = db;
+        a.gstride = gstride;
+        a.m = b->adam_m.as<double>();
+        a.v = b->adam_v.as<double>();
+        a.step = b->adam_step.as<int>();
+        a.E = E;
+        a.estride = estride;
+        a.history = b->history.as<double>();
+        a.max_steps = iters;
+        a.nitems = (int)K;
+        a.p = p;
+        a.lr = lr;
+        a.beta1 = b1;
+        a.beta2 = b2;
+        a.eps = eps;
+        opts.push_back({b, &items, a});
+        return QAOA_OK;
+    };
+    if (!small.items.empty()) {
+        const int per = 1 + 2 * p;
+        double *o = small.b->small_out.as<double>();
+        QAOA_TRY(setup(small.b, small.items, o + 1, o + 1 + p, per, o, per));
+    }
+    for (BatchGroup &g : groups)
+        QAOA_TRY(setup(g.b, g.items, g.b->out_dg.as<double>(), g.b->out_db.as<double>(), p, g.b->out_E.as<double>(), 1));
+    CUDA_TRY(cudaMemsetAsync(c->status.p, 0, 16, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    // The loop runs on the context's own non-blocking stream (a capture cannot
+    // use the legacy default stream); the caller's stream is joined at the end.
+    cudaStream_t user = c->stream;
+    c->stream = c->aux_stream;
+    struct Restore {
+        qaoa_ctx c;
+        cudaStream_t s;
+        ~Restore() { c->stream = s; }
+    } restore{c, user};
+    auto eval = [&](bool profile) -> qaoa_status {
+        QAOA_TRY(enqueue_small(c, small, p, true));
+        for (BatchGroup &g : groups) QAOA_TRY(enqueue_group(c, g, profile));
+        return QAOA_OK;
+    };
+    auto step = [&](bool profile) -> qaoa_status {
+        QAOA_TRY(eval(profile));
+        for (Opt &o : opts) {
+            CUDA_TRY(launch_adam(o.a, c->stream));
+            c->launches_total += 2;
+        }
+        return QAOA_OK;
+    };
+    const int64_t before = c->launches_total;
+    QAOA_TRY(step(true));  // eager first step (also sets every kernel attribute before capture)
+    const int64_t per_step = c->launches_total - before;
+    if (iters > 1) {
+        if (aopt->disable_graph) {
+            for (int t = 1; t < iters; ++t) QAOA_TRY(step(true));
+        } else {
+            cudaGraph_t graph = nullptr;
+            cudaGraphExec_t exec = nullptr;
+            CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed));
+            qaoa_status st = step(false);
+            cudaError_t ce = cudaStreamEndCapture(c->stream, &graph);
+            if (st != QAOA_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return st;
+            }
+            CUDA_TRY(ce);
+            c->launches_total -= per_step;  // counted again per replay below
+            cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+            if (ie != cudaSuccess) {
+                cudaGraphDestroy(graph);
+                CUDA_TRY(ie);
+            }
+            cudaError_t le = cudaSuccess;
+            for (int t = 1; t < iters && le == cudaSuccess; ++t) le = cudaGraphLaunch(exec, c->stream);
+            c->launches_total += per_step * (iters - 1);
+            cudaError_t se = cudaStreamSynchronize(c->stream);
+            cudaGraphExecDestroy(exec);
+            cudaGraphDestroy(graph);
+            CUDA_TRY(le);
+            CUDA_TRY(se);
+        }
+    }
+    // objective at the final parameters
+    QAOA_TRY(eval(true));
+    QAOA_TRY(status_check(c));
+    for (Opt &o : opts) {
+        const std::vector<int> &items = *o.items;
+        const size_t K = items.size();
+        std::vector<double> g(K * p), bt(K * p), hist((size_t)iters * K), E(K);
+        CUDA_TRY(cudaMemcpyAsync(g.data(), o.a.gamma, K * p * 8, cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(cudaMemcpyAsync(bt.data(), o.a.beta, K * p * 8, cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(cudaMemcpyAsync(hist.data(), o.a.history, hist.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(cudaMemcpy2DAsync(E.data(), 8, o.a.E, (size_t)o.a.estride * 8, 8, K, cudaMemcpyDeviceToHost,
+                                   c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+        for (size_t i = 0; i < K; ++i) {
+            const int b = items[i];
+            for (int l = 0; l < p; ++l) {
+                gamma[(size_t)b * p + l] = g[i * p + l];
+                beta[(size_t)b * p + l] = bt[i * p + l];
+            }
+            if (history)
+                for (int t = 0; t < iters; ++t) history[(size_t)t * B + b] = hist[(size_t)t * K + i];
+            if (final_expect) final_expect[b] = E[i];
+        }
+    }
+    // order the caller's stream after the loop
+    cudaEvent_t done = get_event(c);
+    CUDA_TRY(cudaEventRecord(done, c->aux_stream));
+    CUDA_TRY(cudaStreamWaitEvent(user, done, 0));
+    c->ev_free.push_back(done);
     return QAOA_OK;
 }
 

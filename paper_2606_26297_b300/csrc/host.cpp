@@ -138,53 +138,6 @@ qaoa_status make_fixed_point(const Canonical &c, FixedPoint *out) {
     return fail(QAOA_ERR_RANGE, "could not fit the real objective into a 32-bit fixed-point table");
 }
 
-// ---- exact phase constants ------------------------------------------------------
-
-// floor(2^256 / (2 pi)), little-endian 64-bit limbs.
-static const uint64_t kInv2Pi256[4] = {0x7f9458eaf7aef158ull, 0x36d8a5664f10e410ull,
-                                       0x7f09d5f47d4d3770ull, 0x28be60db9391054aull};
-
-uint64_t phase_multiplier(double gamma, int s) {
-    if (gamma == 0.0 || !std::isfinite(gamma)) return 0;
-    int e2;
-    double m = std::frexp(std::fabs(gamma), &e2);  // |gamma| = m 2^e2, m in [0.5, 1)
-    uint64_t M = (uint64_t)std::ldexp(m, 53);      // exact 53-bit integer
-    int E = e2 - 53;                                // |gamma| = M 2^E
-    // P = M * K (5 limbs)
-    uint64_t P[5] = {0, 0, 0, 0, 0};
-    unsigned __int128 carry = 0;
-    for (int i = 0; i < 4; ++i) {
-        unsigned __int128 t = (unsigned __int128)M * kInv2Pi256[i] + carry;
-        P[i] = (uint64_t)t;
-        carry = t >> 64;
-    }
-    P[4] = (uint64_t)carry;
-    // phi = round(P 2^(E - s + 64 - 256)) mod 2^64
-    int sh = E - s + 64 - 256;
-    uint64_t phi = 0;
-    if (sh >= 0) {
-        // only for absurdly large gamma 2^-s; keep the low word of the shift
-        phi = sh < 64 ? (P[0] << sh) : 0;
-    } else {
-        int r = -sh;  // right shift, with rounding
-        if (r > 320) return 0;
-        // add 2^(r-1)
-        int wb = (r - 1) / 64, bb = (r - 1) % 64;
-        uint64_t add[5] = {0, 0, 0, 0, 0};
-        if (wb < 5) add[wb] = 1ull << bb;
-        unsigned __int128 c2 = 0;
-        for (int i = 0; i < 5; ++i) {
-            unsigned __int128 t = (unsigned __int128)P[i] + add[i] + c2;
-            P[i] = (uint64_t)t;
-            c2 = t >> 64;
-        }
-        int w = r / 64, b = r % 64;
-        uint64_t lo = w < 5 ? P[w] : 0, hi = (w + 1) < 5 ? P[w + 1] : 0;
-        phi = b == 0 ? lo : ((lo >> b) | (hi << (64 - b)));
-    }
-    return gamma < 0 ? (uint64_t)(0 - phi) : phi;
-}
-
 // ---- Sec. 3.1, Sec. 3.2 -----------------------------------------------------------
 
 qaoa_status partition(int n, int M, const int32_t *caps, const int32_t *manual, int32_t *qpu_of) {

@@ -1,0 +1,422 @@
+// Final forward pass and reverse (adjoint) passes on the interleaved
+// (psi, lambda) layout (sm_103a).
+//
+// The reverse sweep undoes the gates of Eq. qaoa_state layer by layer on both
+// psi and lambda = H_C psi_p, and accumulates the exact derivatives
+//   dE/dbeta_l  = 2 Im <lambda| sum_j X_j |psi>  (at the mixer of layer l),
+//   dE/dgamma_l = 2 Im <lambda| H_C |psi>        (at the cost layer l),
+// the exact counterpart of the gradient that Sec. 4.2 estimates by SPSA.
+// Storing the two states interleaved, one 16-byte element (psi.re,
+// lambda.re, psi.im, lambda.im) per basis index, lets every butterfly and
+// phase multiply advance both states with packed f32x2 FMAs: with
+// P = (psi.re, lambda.re) and Q = (psi.im, lambda.im), (a, b) -> (a - i t b,
+// b - i t a) becomes P_a += t Q_b, Q_a -= t P_b, P_b += t Q_a, Q_b -= t P_a;
+// rows of 8 elements are 128 bytes.
+//
+// Both kernels are persistent (one CTA per SM walking the (item, block)
+// units of a batch) and TMA-pipelined: the next unit's amplitudes (a 64 KB
+// psi block or a 128 KB (psi, lambda) block) and its 32 KB table block are
+// brought into shared memory by cp.async.bulk[.tensor] while the current unit
+// is computed.  Every mbarrier wait is bounded; a timeout sets the status word.
+#include <cstring>
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "pass_body.cuh"
+#include "tma_util.cuh"
+
+namespace qaoa {
+
+__device__ __forceinline__ float2 f2s(float s) { return make_float2(s, s); }
+
+// butterflies of every mixed register bit on the packed pair (P, Q)
+template <int T, int A>
+__device__ __forceinline__ void round_mix_pq(float2 (&P)[32], float2 (&Q)[32], float t, uint32_t mask) {
+    const float2 tt = f2s(t), nt = f2s(-t);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        if (!((mask >> regbit<T, A>(i)) & 1u)) continue;
+#pragma unroll
+        for (int m = 0; m < 32; ++m) {
+            if (m & (1 << i)) continue;
+            const int q = m | (1 << i);
+            const float2 pa = P[m], qa = Q[m], pb = P[q], qb = Q[q];
+            P[m] = __ffma2_rn(tt, qb, pa);
+            Q[m] = __ffma2_rn(nt, pb, qa);
+            P[q] = __ffma2_rn(tt, qa, pb);
+            Q[q] = __ffma2_rn(nt, pa, qb);
+        }
+    }
+}
+
+// Im<lambda| sum_j X_j |psi> over the mixed register bits (this thread's part):
+// per pair, cross(P_a, Q_b) + cross(P_b, Q_a) with cross(u, v) = u.y v.x - u.x v.y.
+template <int T, int A>
+__device__ __forceinline__ float xterm_pq(const float2 (&P)[32], const float2 (&Q)[32], uint32_t mask) {
+    // four independent partial sums keep the FMA dependency chains short
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        if (!((mask >> regbit<T, A>(i)) & 1u)) continue;
+#pragma unroll
+        for (int m = 0; m < 32; ++m) {
+            if (m & (1 << i)) continue;
+            const int q = m | (1 << i);
+            s0 = fmaf(P[m].y, Q[q].x, s0);
+            s1 = fmaf(-P[m].x, Q[q].y, s1);
+            s2 = fmaf(P[q].y, Q[m].x, s2);
+            s3 = fmaf(-P[q].x, Q[m].y, s3);
+        }
+    }
+    return (s0 + s1) + (s2 + s3);
+}
+
+// (P, Q) <- (P, Q) * z for a complex scalar z applied to both states
+__device__ __forceinline__ void cmul_pq(float2 &P, float2 &Q, float2 z) {
+    const float2 p = P, q = Q;
+    P = __ffma2_rn(p, f2s(z.x), __fmul2_rn(q, f2s(-z.y)));
+    Q = __ffma2_rn(p, f2s(z.y), __fmul2_rn(q, f2s(z.x)));
+}
+
+template <int T, int A>
+__device__ __forceinline__ void read_stage_pq(float2 (&P)[32], float2 (&Q)[32], const float4 *stage, uint32_t l,
+                                              uint32_t w) {
+    const uint32_t t = local_idx<T, A>(l, 0u, w);
+#pragma unroll
+    for (int m = 0; m < 32; ++m) {
+        const float4 e = stage[t | local_idx<T, A>(0u, (uint32_t)m, 0u)];
+        P[m] = make_float2(e.x, e.y);
+        Q[m] = make_float2(e.z, e.w);
+    }
+}
+
+template <int T, int A>
+__device__ __forceinline__ void store_pq(const float2 (&P)[32], const float2 (&Q)[32], float4 *__restrict__ p,
+                                         uint32_t l, uint32_t w, int lo) {
+    float4 *q = p + goff<T>(local_idx<T, A>(l, 0u, w), lo);
+#pragma unroll
+    for (int m = 0; m < 32; ++m) __stcs(q + roff<T, A>(m, lo), make_float4(P[m].x, P[m].y, Q[m].x, Q[m].y));
+}
+
+// unit u of a launch: item u >> nbits, block u & (2^nbits - 1)
+struct Unit {
+    uint32_t item, b;
+};
+__device__ __forceinline__ Unit unit_of(uint32_t u, int nbits) { return {u >> nbits, u & ((1u << nbits) - 1u)}; }
+
+// Issue the copy of a unit's amplitudes: the psi block (64 KB) or the
+// interleaved (psi, lambda) block (128 KB).  High-group tensor maps stack the
+// items of a batch along their outermost dimension.
+template <int T, bool PL>
+__device__ __forceinline__ void issue_amps(uint32_t u, const PassArgs &a, const CUtensorMap *map, void *stage,
+                                           unsigned long long *mbar) {
+    const int nbits = a.n - BLOCK_BITS;
+    const Unit un = unit_of(u, nbits);
+    const uint32_t bytes = PL ? 131072u : 65536u;
+    mbar_expect_tx(mbar, bytes);
+    if (T == 0) {
+        const size_t off = ((size_t)un.item << a.n) + ((size_t)un.b << 13);
+        const void *src = PL ? (const void *)(a.pl + off) : (const void *)(a.psi + off);
+        bulk_load(stage, src, bytes, mbar);
+    } else {
+        const int nlow = a.lo - 3;
+        const int c4 = (int)((un.b >> nlow) + (un.item << (a.n - a.lo - 10)));
+        tma_load_5d(stage, map, (int)(un.b & ((1u << nlow) - 1u)), c4, mbar);
+    }
+}
+
+template <int T>
+__device__ __forceinline__ void issue_table(uint32_t u, const PassArgs &a, const CUtensorMap *mcost, int32_t *cstage,
+                                            unsigned long long *mbar) {
+    const int nbits = a.n - BLOCK_BITS;
+    const Unit un = unit_of(u, nbits);
+    const uint32_t tab = a.item_table ? (uint32_t)a.item_table[un.item] : 0u;
+    mbar_expect_tx(mbar, 32768u);
+    if (T == 0) {
+        bulk_load(cstage, a.C + ((size_t)tab << a.n) + ((size_t)un.b << 13), 32768u, mbar);
+    } else {
+        const int nlow = a.lo - 3;
+        const int c4 = (int)((un.b >> nlow) + (tab << (a.n - a.lo - 10)));
+        tma_load_5d(cstage, mcost, (int)(un.b & ((1u << nlow) - 1u)), c4, mbar);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// final forward pass of a gradient evaluation: psi_in -> psi_p = RX_G psi_in;
+// E partials, top-K, lambda = H_C psi_p; X-terms of beta_p for group G; undo
+// RX_G on (psi, lambda) and write the interleaved (psi_in, lambda_in).
+// slots: 0 = sum P T, 1 = sum P, 2 = X-term (Y), 3 = X-term (X)
+// ---------------------------------------------------------------------------
+template <int T>
+__global__ void __launch_bounds__(PASS_THREADS, 1)
+    final_pass_kernel(const PassArgs a, const __grid_constant__ CUtensorMap mpsi,
+                      const __grid_constant__ CUtensorMap mcost, int nunits, unsigned int *status) {
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    float2 *stage = reinterpret_cast<float2 *>(smraw);                 // psi block, 64 KB
+    int32_t *cstage = reinterpret_cast<int32_t *>(smraw + 65536);      // table block, 32 KB
+    float2 *xbuf = reinterpret_cast<float2 *>(smraw + 65536 + 32768);  // transposes, 64 KB
+    __shared__ __align__(8) unsigned long long mbar, mbarc;
+    __shared__ double red[PASS_THREADS / 32][NSLOT];
+    __shared__ unsigned long long smk[8 * 16];
+    const uint32_t l = threadIdx.x & 31u, w = threadIdx.x >> 5;
+    const int nbits = a.n - BLOCK_BITS;
+    if (threadIdx.x == 0) {
+        mbar_init(&mbar, 1);
+        mbar_init(&mbarc, 1);
+    }
+    __syncthreads();
+    uint32_t parity = 0, parc = 0;
+    if (threadIdx.x == 0 && (int)blockIdx.x < nunits) {
+        issue_amps<T, false>(blockIdx.x, a, &mpsi, stage, &mbar);
+        issue_table<T>(blockIdx.x, a, &mcost, cstage, &mbarc);
+    }
+    for (uint32_t u = blockIdx.x; (int)u < nunits; u += gridDim.x) {
+        const Unit un = unit_of(u, nbits);
+        const PassScal sc = a.scal[un.item];
+        const uint32_t fm = sc.pre_flip ? a.mask : 0u;
+        const size_t base = block_base<T>(un.b, a.lo);
+        float2 v[32];
+        if (!stage_ready(&mbar, parity, status)) return;
+        parity ^= 1u;
+        read_stage<T, 0>(v, stage, l, w);
+        __syncthreads();
+        if (threadIdx.x == 0 && (int)(u + gridDim.x) < nunits) {
+            fence_proxy_async();
+            issue_amps<T, false>(u + gridDim.x, a, &mpsi, stage, &mbar);
+        }
+        round_mix<T, 0>(v, sc.pre_t, a.mask);
+        transpose1<T, 0, 1>(v, xbuf, l, w, fm);
+        round_mix<T, 1>(v, sc.pre_t, a.mask);
+        int32_t c[32];
+        if (!stage_ready(&mbarc, parc, status)) return;
+        parc ^= 1u;
+        read_cost_stage<T, 1>(c, cstage, l, w);
+        __syncthreads();
+        if (threadIdx.x == 0 && (int)(u + gridDim.x) < nunits) {
+            fence_proxy_async();
+            issue_table<T>(u + gridDim.x, a, &mcost, cstage, &mbarc);
+        }
+        // psi_p = kend * v; lambda = (T 2^-s) psi_p
+        float2 P[32], Q[32];
+        float e0 = 0.f, e1 = 0.f;
+#pragma unroll
+        for (int m = 0; m < 32; ++m) {
+            v[m] = cmul(v[m], sc.kend);
+            const float pr = fmaf(v[m].x, v[m].x, v[m].y * v[m].y);
+            const float cf = (float)c[m];
+            e0 = fmaf(pr, cf, e0);
+            e1 += pr;
+            const float lf = cf * sc.cscale;
+            P[m] = make_float2(v[m].x, v[m].x * lf);
+            Q[m] = make_float2(v[m].y, v[m].y * lf);
+        }
+        if (a.ktop > 0) {
+            const size_t xthread = base + goff<T>(local_idx<T, 1>(l, 0u, w), a.lo);
+            block_topk<T, 1>(v, xthread, a.lo, a.ktop, a.topk_keys + (size_t)un.b * a.ktop, smk);
+        }
+        const float x1 = xterm_pq<T, 1>(P, Q, a.mask);
+        round_mix_pq<T, 1>(P, Q, -sc.pre_t, a.mask);
+        transpose1<T, 1, 0>(P, xbuf, l, w, fm);
+        transpose1<T, 1, 0>(Q, xbuf, l, w, fm);
+        const float x0 = xterm_pq<T, 0>(P, Q, a.mask);
+        round_mix_pq<T, 0>(P, Q, -sc.pre_t, a.mask);
+#pragma unroll
+        for (int m = 0; m < 32; ++m) cmul_pq(P[m], Q[m], sc.kend2);
+        store_pq<T, 0>(P, Q, a.pl + ((size_t)un.item << a.n) + base, l, w, a.lo);
+        double vals[NSLOT] = {(double)e0, (double)e1, (double)x1, (double)x0, 0.0, 0.0, 0.0, 0.0};
+        block_sum_write(vals, red, a.partials, u);
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// reverse pass on the interleaved buffer: undoes one forward pass on
+// (psi, lambda).  slots: 0,1 = X-terms of the post mixer (arrangements X, Y);
+// 2 = cost term; 3,4 = X-terms of the pre mixer (Y, X).
+// ---------------------------------------------------------------------------
+template <int T>
+__global__ void __launch_bounds__(PASS_THREADS, 1)
+    rev_pass_kernel(const PassArgs a, const __grid_constant__ CUtensorMap mpl,
+                    const __grid_constant__ CUtensorMap mcost, int nunits, unsigned int *status) {
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    float4 *stage = reinterpret_cast<float4 *>(smraw);                  // (psi, lambda) block, 128 KB
+    int32_t *cstage = reinterpret_cast<int32_t *>(smraw + 131072);      // table block, 32 KB
+    float2 *xbuf = reinterpret_cast<float2 *>(smraw + 131072 + 32768);  // transposes, 64 KB
+    __shared__ __align__(8) unsigned long long mbar, mbarc;
+    __shared__ double red[PASS_THREADS / 32][NSLOT];
+    const uint32_t l = threadIdx.x & 31u, w = threadIdx.x >> 5;
+    const int nbits = a.n - BLOCK_BITS;
+    const bool pre = a.has_pre, post = a.has_post;
+    if (threadIdx.x == 0) {
+        mbar_init(&mbar, 1);
+        mbar_init(&mbarc, 1);
+    }
+    __syncthreads();
+    uint32_t parity = 0, parc = 0;
+    if (threadIdx.x == 0 && (int)blockIdx.x < nunits) {
+        issue_amps<T, true>(blockIdx.x, a, &mpl, stage, &mbar);
+        if (a.has_cost) issue_table<T>(blockIdx.x, a, &mcost, cstage, &mbarc);
+    }
+    for (uint32_t u = blockIdx.x; (int)u < nunits; u += gridDim.x) {
+        const Unit un = unit_of(u, nbits);
+        const PassScal sc = a.scal[un.item];
+        const uint32_t fa = sc.pre_flip ? a.mask : 0u, fb = sc.post_flip ? a.mask : 0u;
+        const size_t base = block_base<T>(un.b, a.lo);
+        float2 P[32], Q[32];
+        float acc[NSLOT] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (!stage_ready(&mbar, parity, status)) return;
+        parity ^= 1u;
+        if (post) read_stage_pq<T, 0>(P, Q, stage, l, w);
+        else read_stage_pq<T, 1>(P, Q, stage, l, w);
+        __syncthreads();
+        if (threadIdx.x == 0 && (int)(u + gridDim.x) < nunits) {
+            fence_proxy_async();
+            issue_amps<T, true>(u + gridDim.x, a, &mpl, stage, &mbar);
+        }
+        if (post) {
+            acc[0] = xterm_pq<T, 0>(P, Q, a.mask);
+            round_mix_pq<T, 0>(P, Q, -sc.post_t, a.mask);
+            transpose1<T, 0, 1>(P, xbuf, l, w, fb);
+            transpose1<T, 0, 1>(Q, xbuf, l, w, fb);
+            acc[1] = xterm_pq<T, 1>(P, Q, a.mask);
+            round_mix_pq<T, 1>(P, Q, -sc.post_t, a.mask);
+        }
+        if (a.has_cost) {
+            int32_t c[32];
+            if (!stage_ready(&mbarc, parc, status)) return;
+            parc ^= 1u;
+            read_cost_stage<T, 1>(c, cstage, l, w);
+            __syncthreads();
+            if (threadIdx.x == 0 && (int)(u + gridDim.x) < nunits) {
+                fence_proxy_async();
+                issue_table<T>(u + gridDim.x, a, &mcost, cstage, &mbarc);
+            }
+            float g0 = 0.f, g1 = 0.f;
+#pragma unroll
+            for (int m = 0; m < 32; ++m) {
+                // Im(conj(lambda) psi) = lambda.re psi.im - lambda.im psi.re
+                const float im = fmaf(P[m].y, Q[m].x, -Q[m].y * P[m].x);
+                if (m & 1) g1 = fmaf((float)c[m], im, g1);
+                else g0 = fmaf((float)c[m], im, g0);
+                cmul_pq(P[m], Q[m], cost_phase(c[m], sc.phi, sc.off, sc.kmag, a.precise_phase));
+            }
+            acc[2] = g0 + g1;
+        }
+        float4 *dst = a.pl + ((size_t)un.item << a.n) + base;
+        if (pre) {
+            acc[3] = xterm_pq<T, 1>(P, Q, a.mask);
+            round_mix_pq<T, 1>(P, Q, -sc.pre_t, a.mask);
+            transpose1<T, 1, 0>(P, xbuf, l, w, fa);
+            transpose1<T, 1, 0>(Q, xbuf, l, w, fa);
+            acc[4] = xterm_pq<T, 0>(P, Q, a.mask);
+            round_mix_pq<T, 0>(P, Q, -sc.pre_t, a.mask);
+            if (a.store) {
+                if (!a.has_cost) {
+#pragma unroll
+                    for (int m = 0; m < 32; ++m) cmul_pq(P[m], Q[m], sc.kend);
+                }
+                store_pq<T, 0>(P, Q, dst, l, w, a.lo);
+            }
+        } else if (a.store) {
+            if (!a.has_cost) {
+#pragma unroll
+                for (int m = 0; m < 32; ++m) cmul_pq(P[m], Q[m], sc.kend);
+            }
+            store_pq<T, 1>(P, Q, dst, l, w, a.lo);
+        }
+        double vals[NSLOT];
+#pragma unroll
+        for (int s = 0; s < NSLOT; ++s) vals[s] = (double)acc[s];
+        block_sum_write(vals, red, a.partials, u);
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side: tensor maps and launchers
+// ---------------------------------------------------------------------------
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+static cudaError_t get_encoder() {
+    if (g_encode) return cudaSuccess;
+    cudaDriverEntryPointQueryResult q;
+    void *fn = nullptr;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    return cudaSuccess;
+}
+
+// 5-D view of high-group blocks: (carried bits 0..2) x (bits 3..lo-1) x
+// (group bits 0..4) x (group bits 5..9) x (bits lo+10..n-1, then `count`
+// consecutive arrays of 2^n elements).  esize: 16 (interleaved psi/lambda,
+// described as pairs of 8-byte elements in dim 0), 8 (complex64) or 4 (int32).
+static cudaError_t make_block_map(CUtensorMap *map, const void *base, int n, int lo, int esize, int count) {
+    std::memset(map, 0, sizeof(*map));
+    cudaError_t e = get_encoder();
+    if (e) return e;
+    const cuuint64_t es = (cuuint64_t)esize;
+    const cuuint64_t d0 = esize == 16 ? 16ull : 8ull;
+    cuuint64_t dims[5] = {d0, 1ull << (lo - 3), 32ull, 32ull, (1ull << (n - lo - 10)) * (cuuint64_t)count};
+    cuuint64_t strides[4] = {8ull * es, es << lo, es << (lo + 5), es << (lo + 10)};
+    cuuint32_t box[5] = {(cuuint32_t)d0, 1u, 32u, 32u, 1u};
+    cuuint32_t estr[5] = {1u, 1u, 1u, 1u, 1u};
+    CUresult r = g_encode(map, esize == 4 ? CU_TENSOR_MAP_DATA_TYPE_INT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 5,
+                          const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <typename K>
+static cudaError_t set_smem(K kern, int bytes) {
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+cudaError_t launch_final_pass(int type, const PassArgs &a, int grid, unsigned int *status, cudaStream_t st) {
+    const int nunits = a.nitems << (a.n - BLOCK_BITS);
+    const int smem = 65536 + 32768 + 65536;
+    CUtensorMap m, mc;
+    std::memset(&m, 0, sizeof m);
+    std::memset(&mc, 0, sizeof mc);
+    cudaError_t e;
+    if (type == 1) {
+        if ((e = make_block_map(&m, a.psi, a.n, a.lo, 8, a.nitems))) return e;
+        if ((e = make_block_map(&mc, a.C, a.n, a.lo, 4, a.ntables))) return e;
+    }
+    if (grid > nunits) grid = nunits;
+    if (type == 0) {
+        if ((e = set_smem(final_pass_kernel<0>, smem))) return e;
+        final_pass_kernel<0><<<grid, PASS_THREADS, smem, st>>>(a, m, mc, nunits, status);
+    } else {
+        if ((e = set_smem(final_pass_kernel<1>, smem))) return e;
+        final_pass_kernel<1><<<grid, PASS_THREADS, smem, st>>>(a, m, mc, nunits, status);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rev_pass(int type, const PassArgs &a, int grid, unsigned int *status, cudaStream_t st) {
+    const int nunits = a.nitems << (a.n - BLOCK_BITS);
+    const int smem = 131072 + 32768 + 65536;
+    CUtensorMap m, mc;
+    std::memset(&m, 0, sizeof m);
+    std::memset(&mc, 0, sizeof mc);
+    cudaError_t e;
+    if (type == 1) {
+        if ((e = make_block_map(&m, a.pl, a.n, a.lo, 16, a.nitems))) return e;
+        if (a.has_cost && (e = make_block_map(&mc, a.C, a.n, a.lo, 4, a.ntables))) return e;
+    }
+    if (grid > nunits) grid = nunits;
+    if (type == 0) {
+        if ((e = set_smem(rev_pass_kernel<0>, smem))) return e;
+        rev_pass_kernel<0><<<grid, PASS_THREADS, smem, st>>>(a, m, mc, nunits, status);
+    } else {
+        if ((e = set_smem(rev_pass_kernel<1>, smem))) return e;
+        rev_pass_kernel<1><<<grid, PASS_THREADS, smem, st>>>(a, m, mc, nunits, status);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace qaoa

@@ -3,6 +3,7 @@
 // factorisation check (Sec. 3.2).
 #include "kernels_misc.h"
 #include "pass_common.cuh"
+#include "schedule.cuh"
 
 namespace qaoa {
 
@@ -431,6 +432,28 @@ __global__ void __launch_bounds__(512, 1) small_kernel(const SmallItem *__restri
         g = bsum512(g, red);
         if (tid == 0) it.out[1 + l] = 2.0 * it.cscale * g;
     }
+}
+
+// Recompute the angle-dependent fields of small items from device angles
+// (used inside captured optimisation steps).
+__global__ void small_prep_kernel(SmallItem *items, int count, const double *gamma, const double *beta, int p,
+                                  const int *item_s, const long long *item_kc) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= count * p) return;
+    const int it = idx / p, l = idx % p;
+    const double g = gamma[(size_t)it * p + l], b = beta[(size_t)it * p + l];
+    const unsigned long long phi = phase_multiplier(g, item_s[it]);
+    items[it].phi[l] = phi;
+    items[it].off[l] = (unsigned long long)item_kc[it] * phi;
+    items[it].cb[l] = cos(b);
+    items[it].sb[l] = sin(b);
+}
+
+cudaError_t launch_small_prep(SmallItem *items, int count, const double *gamma, const double *beta, int p,
+                              const int *item_s, const long long *item_kc, cudaStream_t st) {
+    const int total = count * p;
+    small_prep_kernel<<<(total + 127) / 128, 128, 0, st>>>(items, count, gamma, beta, p, item_s, item_kc);
+    return cudaGetLastError();
 }
 
 int small_smem_bytes(int n, bool fp64, bool grad) {

@@ -43,6 +43,8 @@ struct SmallItem {
 int small_smem_bytes(int n, bool fp64, bool grad);
 cudaError_t launch_small(const SmallItem *items_dev, int count, int max_n, bool fp64, bool grad,
                          cudaStream_t st);
+cudaError_t launch_small_prep(SmallItem *items, int count, const double *gamma, const double *beta, int p,
+                              const int *item_s, const long long *item_kc, cudaStream_t st);
 
 struct FactArgs {
     const int32_t *T;

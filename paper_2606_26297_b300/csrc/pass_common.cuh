@@ -75,8 +75,8 @@ __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2
 
 // RX(2 beta) pair update without its common factor, tangent form:
 // (a, b) <- (a - i t b, b - i t a); the true result is cos(beta) times this.
-// For |sin beta| > |cos beta| the host passes t = tan(beta - pi/2) and sets
-// MixOp.flip: RX(2 beta) = (-i X) RX(2 beta - pi) on every mixed qubit, and
+// For |sin beta| > |cos beta| the pass scalars carry t = tan(beta - pi/2) and
+// a flip flag: RX(2 beta) = (-i X) RX(2 beta - pi) on every mixed qubit, and
 // the bit flip X of the whole group is applied for free by the transpose
 // inside the same mixer (an XOR of the shared-memory slot).
 __device__ __forceinline__ void bfly_tan(float2 &a, float2 &b, float t) {
@@ -88,13 +88,13 @@ __device__ __forceinline__ void bfly_tan(float2 &a, float2 &b, float t) {
 
 // One register round: the butterflies of every mixed register bit.
 template <int T, int A>
-__device__ __forceinline__ void round_mix(float2 (&v)[32], MixOp op, uint32_t mask) {
+__device__ __forceinline__ void round_mix(float2 (&v)[32], float t, uint32_t mask) {
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
         if (!((mask >> regbit<T, A>(i)) & 1u)) continue;
 #pragma unroll
         for (int m = 0; m < 32; ++m)
-            if (!(m & (1 << i))) bfly_tan(v[m], v[m | (1 << i)], op.t);
+            if (!(m & (1 << i))) bfly_tan(v[m], v[m | (1 << i)], t);
     }
 }
 

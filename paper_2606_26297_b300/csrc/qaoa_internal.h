@@ -40,64 +40,61 @@ struct FixedPoint {
 qaoa_status canonicalize(const qaoa_qubo *q, Canonical *out);
 qaoa_status make_fixed_point(const Canonical &c, FixedPoint *out);
 
-// Phase multiplier for U_C(gamma): the table entry T contributes
-// (T + k_c) * phi turns (mod 2^64, units of 2^-64 turn), with
-// phi = round(gamma 2^-s / (2 pi) 2^64) mod 2^64.
-uint64_t phase_multiplier(double gamma, int s);
-
 // Sec. 3.1 allocation helpers and Sec. 3.2 classification.
 qaoa_status partition(int n, int M, const int32_t *caps, const int32_t *manual, int32_t *qpu_of);
 void classify(const Canonical &c, const int32_t *qpu_of, int64_t *n_local, int64_t *n_cross,
               int64_t *n_cross_all);
 
-// ---- device-side argument blocks ---------------------------------------------
-
-// One mixer application: RX(2 beta) on every mixed qubit, as the butterfly
-// (a, b) -> (a - i t b, b - i t a) with common factor cos(beta') where
-// beta' = beta (flip = 0, t = tan beta) or beta' = beta - pi/2 (flip = 1,
-// t = tan(beta - pi/2), followed by the group bit flip X and a factor -i).
-// mode 0: no mixer; 1: mixer present.
-struct MixOp {
-    int mode;
-    int flip;
-    float t;
-};
-
-// Arguments of one layer pass over a 2^13-element block per CTA.
-struct PassArgs {
-    float2 *psi;            // state (read and/or written)
-    float2 *lam;            // adjoint state
-    float4 *pl;             // interleaved (psi.re, lambda.re, psi.im, lambda.im) per index
-    const int32_t *C;       // objective table T
-    double *partials;       // [block][NSLOT] per-block FP64 partial sums
-    unsigned long long *topk_keys;  // [block][ktop] candidate keys (epilogue only)
-    int n;
-    int lo;                 // window offset of a high-group pass
-    uint32_t mask;          // which of the 13 block bits are mixed
-    int init;               // synthesise |+>^n instead of loading psi
-    int has_cost;
-    int store_psi;          // write psi back (reverse passes)
-    int precise_phase;      // 1: sincospif, 0: hardware sin/cos
-    int ktop;               // top-K candidates per block (epilogue), 0 = off
-    MixOp pre, post;
-    unsigned long long phi; // phase turns per table unit
-    unsigned long long off; // phase turns offset (k_c * phi)
-    float amp0;             // 2^{-n/2}
-    float kmag;             // real factor of the cost multiplier (the phase of any folded
-                            // complex scalar is already part of `off`)
-    float2 kend;            // complex scalar applied before the store when there is no cost
-    float2 kend2;           // epilogue: scalar applied to lambda before its store
-    float cscale;           // 2^-s
-};
+// ---- layer-pass arguments ----------------------------------------------------
 
 constexpr int NSLOT = 8;
 constexpr int BLOCK_BITS = 13;
 constexpr int PASS_THREADS = 256;
 
-// Launchers (kernels_pass.cu).
-cudaError_t launch_fwd_pass(int type, bool epilogue, const PassArgs &a, cudaStream_t st);
-cudaError_t launch_rev_pass(int type, const PassArgs &a, cudaStream_t st);
-cudaError_t launch_reduce_partials(const double *partials, int nblocks, int nslot, double *out,
+// Angle-dependent scalars of one pass for one item (one parameter set).  The
+// mixer is the butterfly (a, b) -> (a - i t b, b - i t a) with common factor
+// cos(beta') where beta' = beta (flip = 0, t = tan beta) or beta - pi/2
+// (flip = 1: t = tan(beta - pi/2), then the group bit flip X and a factor -i).
+// The cost phase is exp(-2 pi i (T phi + off) / 2^64) * kmag (any complex scalar
+// folded into it has its phase in `off`).  kend: scalar applied before a store
+// when the pass has no cost phase; kend2: the final pass's lambda scalar.
+struct PassScal {
+    float pre_t, post_t;
+    int pre_flip, post_flip;
+    unsigned long long phi, off;
+    float kmag, cscale;  // cscale = 2^-s of the item's table
+    float2 kend, kend2;
+};
+
+// Structural arguments of one layer pass, shared by the items of a launch.
+// Item i's state is psi + i * 2^n (pl likewise); its table is
+// C + item_table[i] * 2^n (item_table null: table 0 for all).
+struct PassArgs {
+    float2 *psi;
+    float4 *pl;                     // interleaved (psi.re, lambda.re, psi.im, lambda.im) per index
+    const int32_t *C;
+    const int *item_table;
+    const PassScal *scal;           // [nitems]
+    double *partials;               // [item][block][NSLOT] per-block FP64 partial sums
+    unsigned long long *topk_keys;  // [block][ktop] candidate keys (final pass, single item)
+    int n;
+    int lo;                         // window offset of a high-group pass
+    uint32_t mask;                  // which of the 13 block bits are mixed
+    int nitems, ntables;
+    int init;                       // synthesise |+>^n instead of loading psi
+    int has_pre, has_cost, has_post;
+    int store;                      // write the result back (reverse passes)
+    int precise_phase;              // 1: sincospif, 0: hardware sin/cos
+    int ktop;                       // top-K candidates per block (final pass), 0 = off
+    float amp0;                     // 2^{-n/2}
+};
+
+// Launchers.  grid: persistent CTAs (TMA kernels); status: device word set to
+// a non-zero value if a bounded wait expired.
+cudaError_t launch_fwd_pass(int type, const PassArgs &a, cudaStream_t st);
+cudaError_t launch_final_pass(int type, const PassArgs &a, int grid, unsigned int *status, cudaStream_t st);
+cudaError_t launch_rev_pass(int type, const PassArgs &a, int grid, unsigned int *status, cudaStream_t st);
+cudaError_t launch_reduce_partials(const double *partials, int nitems, int nblocks, double *out,
                                    cudaStream_t st);
 cudaError_t launch_topk_merge(const unsigned long long *in, int nlists, int k,
                               unsigned long long *out, int *nout, int *nlaunch, cudaStream_t st);

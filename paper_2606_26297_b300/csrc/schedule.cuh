@@ -1,0 +1,369 @@
+// Layer-pass schedule and the angle-dependent scalars of every pass.
+//
+// The n qubits are split into G groups of <= 10 (the mixer of Eq.
+// qaoa_mixer_unitary factorises over qubits).  Group 0 owns the low bits
+// (blocks of 13 contiguous bits); every other group owns a 10-bit window
+// lo..lo+9 and carries global bits 0..2 for coalescing.  Layers visit the
+// groups in alternating order (A,B,C | C,B,A | ...), so the pass that ends
+// layer l also applies U_C(gamma_{l+1}) (diagonal, Eq. qaoa_cost_unitary) and
+// the same group's mixer of layer l+1: 1 + p(G-1) forward passes in all.
+//
+// pass_scalars() is __host__ __device__: the host uses it for single
+// evaluations, and a device kernel (batch.cu) recomputes it from
+// device-resident angles inside a captured CUDA graph.
+#pragma once
+
+#include <cmath>
+#include <cstdint>
+#include <vector>
+
+#include "qaoa_internal.h"
+
+namespace qaoa {
+
+struct Group {
+    int type;       // 0: low group (block = global bits 0..12), 1: high group
+    int lo;         // window offset (type 1)
+    uint32_t mask;  // mixed local bits
+    int kX, kY;     // mixed bits in the register rounds of arrangements X and Y
+};
+
+// One pass as executed.  kind 0: forward; 1: final forward pass of a gradient
+// evaluation; 2: reverse pass undoing forward pass `fwd`.
+struct PassPlan {
+    int kind;
+    int type, lo;
+    uint32_t mask;
+    int kX, kY;
+    int init;
+    int la, lc, lb;            // layers (0-based) of pre mixer, cost, post mixer; -1 none
+    int slot_param[NSLOT];     // -1 none, -2 expectation sums, l: dE/dbeta_l, p+l: dE/dgamma_l
+    int sum_index;             // row of this pass in the partial-sum table, -1 none
+};
+
+// register bits of arrangements X and Y (see pass_common.cuh)
+constexpr uint32_t REGS_X[2] = {0x0F8u, 0x1C18u};  // type 0: bits 3..7; type 1: {3,4,10,11,12}
+constexpr uint32_t REGS_Y[2] = {0x307u, 0x3E0u};   // type 0: {0,1,2,8,9}; type 1: bits 5..9
+
+inline std::vector<Group> make_groups(int n, int maxq) {
+    const int G = (n + maxq - 1) / maxq;
+    std::vector<Group> gs;
+    int q0 = 0;
+    for (int g = 0; g < G; ++g) {
+        const int k = n / G + (g < n % G ? 1 : 0);
+        Group gr{};
+        if (g == 0) {
+            gr.type = 0;
+            gr.lo = 0;
+            gr.mask = (1u << k) - 1u;
+        } else {
+            gr.type = 1;
+            gr.lo = q0 < n - 10 ? q0 : n - 10;
+            gr.mask = 0;
+            for (int q = q0; q < q0 + k; ++q) gr.mask |= 1u << (3 + q - gr.lo);
+        }
+        gr.kX = __builtin_popcount(gr.mask & REGS_X[gr.type]);
+        gr.kY = __builtin_popcount(gr.mask & REGS_Y[gr.type]);
+        gs.push_back(gr);
+        q0 += k;
+    }
+    return gs;
+}
+
+// Forward schedule, then (grad) the reverse passes in reverse order; the
+// reverse of the final pass is fused into it.
+inline std::vector<PassPlan> make_plan(int n, int p, bool grad, int maxq) {
+    const std::vector<Group> gs = make_groups(n, maxq);
+    const int G = (int)gs.size();
+    struct D {
+        int group, init, epi, la, lc, lb;
+    };
+    std::vector<D> f;
+    auto order = [&](int l, int i) { return (l % 2 == 0) ? i : G - 1 - i; };
+    if (p == 0) {
+        f.push_back({0, 1, 0, -1, -1, -1});
+    } else {
+        f.push_back({order(0, 0), 1, 0, -1, 0, 0});
+        for (int l = 0; l < p; ++l) {
+            for (int i = 1; i < G - 1; ++i) f.push_back({order(l, i), 0, 0, -1, -1, l});
+            const int last = order(l, G - 1);
+            if (l + 1 < p) f.push_back({last, 0, 0, l, l + 1, l + 1});
+            else if (grad) f.push_back({last, 0, 1, l, -1, -1});
+            else f.push_back({last, 0, 0, -1, -1, l});
+        }
+    }
+    std::vector<PassPlan> plan;
+    int rows = 0;
+    auto base = [&](const D &d, int kind) {
+        PassPlan pl{};
+        const Group &g = gs[d.group];
+        pl.kind = kind;
+        pl.type = g.type;
+        pl.lo = g.lo;
+        pl.mask = g.mask;
+        pl.kX = g.kX;
+        pl.kY = g.kY;
+        pl.init = d.init;
+        pl.la = d.la;
+        pl.lc = d.lc;
+        pl.lb = d.lb;
+        for (int s = 0; s < NSLOT; ++s) pl.slot_param[s] = -1;
+        pl.sum_index = -1;
+        return pl;
+    };
+    for (const D &d : f) {
+        PassPlan pl = base(d, d.epi ? 1 : 0);
+        if (d.epi) {
+            pl.slot_param[0] = pl.slot_param[1] = -2;
+            pl.slot_param[2] = pl.slot_param[3] = d.la;
+            pl.sum_index = rows++;
+        }
+        plan.push_back(pl);
+    }
+    if (grad)
+        for (int i = (int)f.size() - 2; i >= 0; --i) {
+            PassPlan pl = base(f[i], 2);
+            if (f[i].lb >= 0) pl.slot_param[0] = pl.slot_param[1] = f[i].lb;
+            if (f[i].lc >= 0) pl.slot_param[2] = p + f[i].lc;
+            if (f[i].la >= 0) pl.slot_param[3] = pl.slot_param[4] = f[i].la;
+            pl.sum_index = rows++;
+            plan.push_back(pl);
+        }
+    return plan;
+}
+
+inline int plan_rows(const std::vector<PassPlan> &plan) {
+    int r = 0;
+    for (const auto &pl : plan) r += pl.sum_index >= 0;
+    return r;
+}
+
+// ---- host/device scalar arithmetic ---------------------------------------------
+
+struct HdCx {
+    double re, im;
+};
+__host__ __device__ inline HdCx hc_mul(HdCx a, HdCx b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+__host__ __device__ inline HdCx hc_conj(HdCx a) { return {a.re, -a.im}; }
+__host__ __device__ inline double hc_norm(HdCx a) { return a.re * a.re + a.im * a.im; }
+__host__ __device__ inline HdCx hc_inv(HdCx a) {
+    const double d = hc_norm(a);
+    return {a.re / d, -a.im / d};
+}
+__host__ __device__ inline HdCx hc_div(HdCx a, HdCx b) { return hc_mul(a, hc_inv(b)); }
+__host__ __device__ inline HdCx hc_pow(HdCx f, int k) {
+    HdCx r{1.0, 0.0};
+    for (int i = 0; i < k; ++i) r = hc_mul(r, f);
+    return r;
+}
+__host__ __device__ inline float2 hc_f2(HdCx z) { return make_float2((float)z.re, (float)z.im); }
+
+// 64 x 64 -> 128-bit product
+__host__ __device__ inline void mul64(unsigned long long a, unsigned long long b, unsigned long long *hi,
+                                      unsigned long long *lo) {
+#ifdef __CUDA_ARCH__
+    *lo = a * b;
+    *hi = __umul64hi(a, b);
+#else
+    const unsigned __int128 t = (unsigned __int128)a * b;
+    *lo = (unsigned long long)t;
+    *hi = (unsigned long long)(t >> 64);
+#endif
+}
+
+// Phase multiplier for U_C(gamma): a table entry T contributes (T + k_c) * phi
+// turns (units of 2^-64 turn, modulo 2^64), with
+//   phi = round(gamma 2^-s / (2 pi) 2^64) mod 2^64.
+// |gamma| = M 2^E exactly (M < 2^53); phi = round(M * K * 2^(E - s + 64 - 256))
+// with K = floor(2^256 / (2 pi)), evaluated on 64-bit limbs.
+__host__ __device__ inline unsigned long long phase_multiplier(double gamma, int s) {
+    // floor(2^256 / (2 pi)), little-endian 64-bit limbs
+    const unsigned long long K[4] = {0x7f9458eaf7aef158ull, 0x36d8a5664f10e410ull, 0x7f09d5f47d4d3770ull,
+                                     0x28be60db9391054aull};
+    if (gamma == 0.0 || !isfinite(gamma)) return 0ull;
+    int e2;
+    const double m = frexp(fabs(gamma), &e2);                   // |gamma| = m 2^e2, m in [0.5, 1)
+    const unsigned long long M = (unsigned long long)ldexp(m, 53);  // exact 53-bit integer
+    const int E = e2 - 53;
+    unsigned long long P[5] = {0, 0, 0, 0, 0};
+    unsigned long long carry = 0;
+    for (int i = 0; i < 4; ++i) {
+        unsigned long long hi, lo;
+        mul64(M, K[i], &hi, &lo);
+        const unsigned long long t = lo + carry;
+        P[i] = t;
+        carry = hi + (t < lo ? 1ull : 0ull);
+    }
+    P[4] = carry;
+    const int sh = E - s + 64 - 256;
+    unsigned long long phi = 0;
+    if (sh >= 0) {
+        phi = sh < 64 ? (P[0] << sh) : 0ull;
+    } else {
+        const int r = -sh;
+        if (r > 320) return 0ull;
+        // round: add 2^(r-1), then shift right by r
+        const int wb = (r - 1) / 64, bb = (r - 1) % 64;
+        unsigned long long c2 = 0;
+        for (int i = 0; i < 5; ++i) {
+            const unsigned long long add = (i == wb) ? (1ull << bb) : 0ull;
+            const unsigned long long t = P[i] + add;
+            const unsigned long long t2 = t + c2;
+            c2 = (t < P[i] ? 1ull : 0ull) + (t2 < t ? 1ull : 0ull);
+            P[i] = t2;
+        }
+        const int w = r / 64, b = r % 64;
+        const unsigned long long lo = w < 5 ? P[w] : 0ull, hi = (w + 1) < 5 ? P[w + 1] : 0ull;
+        phi = b == 0 ? lo : ((lo >> b) | (hi << (64 - b)));
+    }
+    return gamma < 0 ? (0ull - phi) : phi;
+}
+
+// turns offset (units of 2^-64 turn) that multiplies the phase by e^{i arg z}
+__host__ __device__ inline unsigned long long turns_of_arg(HdCx z) {
+    double x = -atan2(z.im, z.re) / (2.0 * 3.14159265358979323846) * 18446744073709551616.0;
+    if (x >= 9.2233720368547758e18) x -= 18446744073709551616.0;
+    return (unsigned long long)(long long)llrint(x);
+}
+
+struct HdMix {
+    float t;
+    int flip;
+    HdCx f;  // common factor of one level: true = f * computed
+};
+
+// RX(2 beta) = cos(beta) (1 - i tan(beta) X) if |cos| >= |sin|,
+// else (-i X) RX(2 beta - pi) = -i sin(beta) X (1 - i tan(beta - pi/2) X).
+__host__ __device__ inline HdMix mix_of(double beta) {
+    HdMix m;
+    const double c = cos(beta), s = sin(beta);
+    if (fabs(c) >= fabs(s)) {
+        m.flip = 0;
+        m.t = (float)(s / c);
+        m.f = {c, 0.0};
+    } else {
+        m.flip = 1;
+        m.t = (float)(-c / s);
+        m.f = {0.0, -s};
+    }
+    return m;
+}
+
+// Scalars of pass `pl` for one parameter set (gamma, beta: p entries each) on
+// a table with fixed-point parameters (s, k_c).  The computed amplitudes are
+// tracked as true * S: each forward mixer level divides by f, each inverse
+// level by conj(f); the phase multiplier absorbs the accumulated scalars so
+// that every stored state is at true scale, and slot_scale[s] converts each
+// partial sum back to true scale.
+__host__ __device__ inline void pass_scalars(const PassPlan &pl, const double *gamma, const double *beta, int s,
+                                             long long k_c, PassScal *sc, double *slot_scale) {
+    const int k = pl.kX + pl.kY;
+    sc->pre_t = sc->post_t = 0.f;
+    sc->pre_flip = sc->post_flip = 0;
+    sc->phi = sc->off = 0ull;
+    sc->kmag = 1.f;
+    sc->cscale = (float)ldexp(1.0, -s);
+    sc->kend = make_float2(1.f, 0.f);
+    sc->kend2 = make_float2(1.f, 0.f);
+    for (int q = 0; q < NSLOT; ++q) slot_scale[q] = 0.0;
+    HdMix ma{}, mb{};
+    if (pl.la >= 0) {
+        ma = mix_of(beta[pl.la]);
+        sc->pre_t = ma.t;
+        sc->pre_flip = ma.flip;
+    }
+    if (pl.lb >= 0) {
+        mb = mix_of(beta[pl.lb]);
+        sc->post_t = mb.t;
+        sc->post_flip = mb.flip;
+    }
+    const HdCx one{1.0, 0.0};
+    HdCx S = one;
+    if (pl.kind != 2) {
+        if (pl.la >= 0) S = hc_div(S, hc_pow(ma.f, k));
+        if (pl.lc >= 0) {
+            const unsigned long long phi = phase_multiplier(gamma[pl.lc], s);
+            const HdCx post = pl.lb >= 0 ? hc_pow(mb.f, k) : one;
+            const HdCx Kf = hc_div(post, S);
+            sc->phi = phi;
+            sc->off = (unsigned long long)k_c * phi + turns_of_arg(Kf);
+            sc->kmag = (float)sqrt(hc_norm(Kf));
+            S = post;
+        }
+        if (pl.lb >= 0) S = hc_div(S, hc_pow(mb.f, k));
+        if (pl.kind == 0) {
+            if (pl.lc < 0) sc->kend = hc_f2(hc_inv(S));
+        } else {
+            sc->kend = hc_f2(hc_inv(S));  // psi_p = kend * computed
+            HdCx Sl = one;
+            slot_scale[0] = slot_scale[1] = 1.0;
+            slot_scale[2] = 1.0;
+            Sl = hc_div(Sl, hc_pow(hc_conj(ma.f), pl.kY));
+            slot_scale[3] = 1.0 / hc_norm(Sl);
+            Sl = hc_div(Sl, hc_pow(hc_conj(ma.f), pl.kX));
+            sc->kend2 = hc_f2(hc_inv(Sl));
+        }
+    } else {
+        if (pl.lb >= 0) {
+            slot_scale[0] = 1.0 / hc_norm(S);
+            S = hc_div(S, hc_pow(hc_conj(mb.f), pl.kX));
+            slot_scale[1] = 1.0 / hc_norm(S);
+            S = hc_div(S, hc_pow(hc_conj(mb.f), pl.kY));
+        }
+        if (pl.lc >= 0) {
+            slot_scale[2] = 1.0 / hc_norm(S);
+            const unsigned long long phi = phase_multiplier(gamma[pl.lc], s);
+            const HdCx pre = pl.la >= 0 ? hc_pow(hc_conj(ma.f), k) : one;
+            const HdCx Kf = hc_div(pre, S);
+            sc->phi = 0ull - phi;
+            sc->off = (0ull - (unsigned long long)k_c * phi) + turns_of_arg(Kf);
+            sc->kmag = (float)sqrt(hc_norm(Kf));
+            S = hc_mul(S, Kf);
+        }
+        if (pl.la >= 0) {
+            slot_scale[3] = 1.0 / hc_norm(S);
+            S = hc_div(S, hc_pow(hc_conj(ma.f), pl.kY));
+            slot_scale[4] = 1.0 / hc_norm(S);
+            S = hc_div(S, hc_pow(hc_conj(ma.f), pl.kX));
+        }
+        if (pl.lc < 0) sc->kend = hc_f2(hc_inv(S));
+    }
+}
+
+// Algorithmic bytes per amplitude of a pass (what the method must move).
+inline double pass_bytes_per_amp(const PassPlan &pl) {
+    if (pl.kind == 0) return (pl.init ? 0.0 : 8.0) + 8.0 + (pl.lc >= 0 ? 4.0 : 0.0);
+    if (pl.kind == 1) return 8.0 + 4.0 + 16.0;
+    return 16.0 + (pl.init ? 0.0 : 16.0) + (pl.lc >= 0 ? 4.0 : 0.0);
+}
+
+// Device side (batch.cu): recompute every pass's scalars from device angles,
+// assemble E and the gradient from the partial sums, and the Adam update.
+struct DevPlan {
+    const PassPlan *plan;  // [npasses]
+    int npasses, p, nitems;
+    const double *gamma, *beta;        // [nitems][p]
+    const int *item_s;                 // [nitems] fixed-point shift of the item's table
+    const long long *item_kc;          // [nitems]
+    PassScal *scal;                    // [npasses][nitems]
+    double *slot_scale;                // [npasses][nitems][NSLOT]
+};
+cudaError_t launch_prep_scalars(const DevPlan &d, cudaStream_t st);
+cudaError_t launch_assemble(const DevPlan &d, const double *sums /*[rows][nitems][NSLOT]*/, double *E,
+                            double *dgamma, double *dbeta, cudaStream_t st);
+
+struct AdamArgs {
+    double *gamma, *beta;        // [nitems][p], updated in place
+    const double *dgamma, *dbeta;  // gradient of item i, parameter l at [i * gstride + l]
+    int gstride;
+    double *m, *v;               // [2][nitems][p] moments
+    int *step;                   // device step counter
+    const double *E;             // objective of item i at E[i * estride]
+    int estride;
+    double *history;             // [max_steps][nitems] or null
+    int max_steps, nitems, p;
+    double lr, beta1, beta2, eps;
+};
+cudaError_t launch_adam(const AdamArgs &a, cudaStream_t st);
+
+}  // namespace qaoa

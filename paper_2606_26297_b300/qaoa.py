@@ -40,8 +40,13 @@ class qaoa_qubo(ctypes.Structure):
 class qaoa_options(ctypes.Structure):
     _fields_ = [("adjoint_mode", ctypes.c_int32), ("profile", ctypes.c_int32),
                 ("memory_budget", ctypes.c_int64), ("max_fused_qubits", ctypes.c_int32),
-                ("state_fp64", ctypes.c_int32), ("pass_variant", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("state_fp64", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+
+
+class qaoa_adam_options(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_double), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
+                ("eps", ctypes.c_double), ("iterations", ctypes.c_int32), ("disable_graph", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
 
 
 _P = ctypes.c_void_p
@@ -69,6 +74,8 @@ _SIGS = {
     "qaoa_topk": ([_P, _P, _P, _I, _PU64, _PF, _PD, _PU64, _PD, _PF], _I),
     "qaoa_grad": ([_P, _P, _I, _PD, _PD, _PD, _PD, _PD, _I, _PU64, _PF], _I),
     "qaoa_grad_batch": ([_P, _I, ctypes.POINTER(_P), _PI32, _I, _I, _PD, _PD, _PD, _PD, _PD], _I),
+    "qaoa_optimize_adam": ([_P, _I, ctypes.POINTER(_P), _PI32, _I, _I, _PD, _PD,
+                            ctypes.POINTER(qaoa_adam_options), _PD, _PD], _I),
     "qaoa_partition": ([_I, _I, _PI32, _PI32, _PI32], _I),
     "qaoa_classify": ([_P, _PI32, _I, _PI64, _PI64, _PI64, _PI64], _I),
     "qaoa_check_factorisation": ([_P, _P, _PI32, _D, _PI64, _PD], _I),
@@ -101,8 +108,7 @@ def qaoa_last_error() -> str:
 # ---- context ---------------------------------------------------------------------
 
 def qaoa_ctx_create(device: int = 0, stream: int | None = None, profile: bool = False,
-                    memory_budget: int = 0, max_fused_qubits: int = 0, state_fp64: bool = False,
-                    pass_variant: int = 0):
+                    memory_budget: int = 0, max_fused_qubits: int = 0, state_fp64: bool = False):
     """Create a context; `stream` is a raw cudaStream_t (e.g. torch's
     `torch.cuda.current_stream().cuda_stream`), None for the default stream."""
     opt = qaoa_options()
@@ -110,7 +116,6 @@ def qaoa_ctx_create(device: int = 0, stream: int | None = None, profile: bool = 
     opt.memory_budget = int(memory_budget)
     opt.max_fused_qubits = int(max_fused_qubits)
     opt.state_fp64 = int(state_fp64)
-    opt.pass_variant = int(pass_variant)
     out = _P()
     _check(_lib.qaoa_ctx_create(int(device), _P(stream or 0), ctypes.byref(opt), ctypes.byref(out)))
     return out
@@ -239,6 +244,26 @@ def qaoa_grad_batch(ctx, costs, gamma, beta, item_cost=None, grad: bool = True):
                                 _dptr(g), _dptr(b), _dptr(E), None if dg is None else _dptr(dg),
                                 None if db is None else _dptr(db)))
     return (E, dg, db) if grad else E
+
+
+def qaoa_optimize_adam(ctx, costs, gamma, beta, iterations: int, item_cost=None, lr: float = 0.0,
+                       beta1: float = 0.0, beta2: float = 0.0, eps: float = 0.0, use_graph: bool = True):
+    """Adam on the exact gradient for B parameter sets (gamma, beta: (B, p)).
+    Returns (gamma, beta, history (iterations, B), final E (B,))."""
+    g = np.array(np.asarray(gamma, dtype=np.float64), order="C", copy=True)
+    b = np.array(np.asarray(beta, dtype=np.float64), order="C", copy=True)
+    B, p = g.shape
+    arr = (_P * len(costs))(*[c.value if isinstance(c, _P) else c for c in costs])
+    ic = None if item_cost is None else np.ascontiguousarray(np.asarray(item_cost, dtype=np.int32))
+    opt = qaoa_adam_options()
+    opt.lr, opt.beta1, opt.beta2, opt.eps = float(lr), float(beta1), float(beta2), float(eps)
+    opt.iterations = int(iterations)
+    opt.disable_graph = 0 if use_graph else 1
+    hist = np.zeros((int(iterations), B))
+    E = np.zeros(B)
+    _check(_lib.qaoa_optimize_adam(ctx, len(costs), arr, None if ic is None else ic.ctypes.data_as(_PI32), B, p,
+                                   _dptr(g), _dptr(b), ctypes.byref(opt), _dptr(hist), _dptr(E)))
+    return g, b, hist, E
 
 
 # ---- DQAOA ----------------------------------------------------------------------------------

@@ -1,0 +1,154 @@
+"""GPU parity of the batched forms: many parameter sets and ragged QUBO sizes
+in one request (qaoa_grad_batch), and the Adam loop on the exact gradient
+replayed as a CUDA graph (qaoa_optimize_adam), against the FP64 oracle.
+
+Tolerances as in test_gpu_parity: |dE| / max|F| <= 1e-5, gradient
+max-abs error / max|gradient| <= 1e-4.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2606_26297_b300 import instances as inst
+
+pytestmark = pytest.mark.gpu
+
+E_TOL = 1e-5
+G_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def q():
+    from paper_2606_26297_b300 import build_lib
+    build_lib.build()
+    from paper_2606_26297_b300 import qaoa
+    return qaoa
+
+
+@pytest.fixture(scope="module")
+def ctx(q):
+    c = q.qaoa_ctx_create(0)
+    yield c
+    q.qaoa_ctx_destroy(c)
+
+
+def _cost(q, ctx, Q):
+    return q.qaoa_build_cost(ctx, Q.H, Q.f, Q.c0, "i32" if Q.dtype == "i32" else "f32")
+
+
+def _check_item(F, g, b, E, dg, db):
+    Eo, dgo, dbo = oracle.grad_adjoint(F, g, b)
+    assert abs(E - Eo) / np.max(np.abs(F)) <= E_TOL
+    sc = max(np.max(np.abs(dgo)), np.max(np.abs(dbo)), 1e-12)
+    err = max(np.max(np.abs(dg - dgo)), np.max(np.abs(db - dbo))) / sc
+    assert err <= G_TOL, err
+
+
+def test_multistart_batch_vs_oracle_and_single(q, ctx):
+    """Many (gamma, beta) sets on one n=16 table: every item against the oracle
+    and against the single-item call."""
+    n, p, B = 16, 3, 6
+    Q = inst.upper_int_qubo(n, 4100)
+    g, b = inst.random_angles(p, B, 4101, gamma_scale=1.0 / math.sqrt(n))
+    cost = _cost(q, ctx, Q)
+    E, dg, db = q.qaoa_grad_batch(ctx, [cost], g, b)
+    F = oracle.cost_table(oracle.canonical_of(Q))
+    for i in range(B):
+        _check_item(F, g[i], b[i], E[i], dg[i], db[i])
+        Es, dgs, dbs = q.qaoa_grad(ctx, cost, g[i], b[i])
+        assert abs(Es - E[i]) <= 1e-6 * np.max(np.abs(F))
+        sc = max(np.abs(dgs).max(), np.abs(dbs).max())
+        assert max(np.abs(dgs - dg[i]).max(), np.abs(dbs - db[i]).max()) <= 1e-5 * sc
+    q.qaoa_cost_destroy(cost)
+
+
+def test_ragged_batch_vs_oracle(q, ctx):
+    """Uneven sizes in one request: n <= 12 items on the shared-memory kernel,
+    two different tables of the same n in one launch, a real-valued table."""
+    Qs = [inst.upper_int_qubo(10, 4200), inst.upper_int_qubo(13, 4201), inst.normal_qubo(15, 4202),
+          inst.upper_int_qubo(15, 4203), inst.regular_maxcut_qubo(18, 4204)]
+    costs = [_cost(q, ctx, Q) for Q in Qs]
+    item_cost = [0, 1, 2, 3, 4, 2, 3, 0, 1]
+    p = 2
+    g, b = inst.random_angles(p, len(item_cost), 4205, gamma_scale=0.3)
+    E, dg, db = q.qaoa_grad_batch(ctx, costs, g, b, item_cost=item_cost)
+    Fs = [oracle.cost_table(oracle.canonical_of(Q)) for Q in Qs]
+    for i, ci in enumerate(item_cost):
+        _check_item(Fs[ci], g[i], b[i], E[i], dg[i], db[i])
+    Ef = q.qaoa_grad_batch(ctx, costs, g, b, item_cost=item_cost, grad=False)
+    for i, ci in enumerate(item_cost):
+        Eo = oracle.expectation(Fs[ci], oracle.evolve(Fs[ci], g[i], b[i]))
+        assert abs(Ef[i] - Eo) / np.max(np.abs(Fs[ci])) <= E_TOL
+    for c in costs:
+        q.qaoa_cost_destroy(c)
+
+
+def test_batch_deterministic(q, ctx):
+    Q = inst.upper_int_qubo(17, 4300)
+    cost = _cost(q, ctx, Q)
+    g, b = inst.random_angles(3, 4, 4301, gamma_scale=0.2)
+    r1 = q.qaoa_grad_batch(ctx, [cost], g, b)
+    r2 = q.qaoa_grad_batch(ctx, [cost], g, b)
+    for a1, a2 in zip(r1, r2):
+        assert np.array_equal(a1, a2)
+    q.qaoa_cost_destroy(cost)
+
+
+def _adam_reference(Fs, item_cost, g0, b0, iters, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """Adam (bias-corrected moments) on the oracle's exact gradient."""
+    g, b = g0.copy(), b0.copy()
+    B, p = g.shape
+    m = np.zeros((B, 2 * p))
+    v = np.zeros((B, 2 * p))
+    hist = np.zeros((iters, B))
+    for t in range(1, iters + 1):
+        for i in range(B):
+            E, dg, db = oracle.grad_adjoint(Fs[item_cost[i]], g[i], b[i])
+            hist[t - 1, i] = E
+            gr = np.concatenate([dg, db])
+            m[i] = b1 * m[i] + (1 - b1) * gr
+            v[i] = b2 * v[i] + (1 - b2) * gr * gr
+            mh = m[i] / (1 - b1 ** t)
+            vh = v[i] / (1 - b2 ** t)
+            step = lr * mh / (np.sqrt(vh) + eps)
+            g[i] -= step[:p]
+            b[i] -= step[p:]
+    return g, b, hist
+
+
+def test_adam_graph_vs_eager_vs_oracle(q, ctx):
+    Qs = [inst.upper_int_qubo(14, 4400), inst.upper_int_qubo(11, 4401), inst.regular_maxcut_qubo(14, 4402)]
+    costs = [_cost(q, ctx, Q) for Q in Qs]
+    item_cost = [0, 1, 2, 0]
+    p, iters, lr = 2, 6, 0.02
+    g0, b0 = inst.random_angles(p, len(item_cost), 4403, gamma_scale=0.2)
+    gg, bg, hg, Eg = q.qaoa_optimize_adam(ctx, costs, g0, b0, iters, item_cost=item_cost, lr=lr)
+    ge, be, he, Ee = q.qaoa_optimize_adam(ctx, costs, g0, b0, iters, item_cost=item_cost, lr=lr, use_graph=False)
+    # the graph replays exactly the eager step's kernels
+    assert np.array_equal(gg, ge) and np.array_equal(bg, be)
+    assert np.array_equal(hg, he) and np.array_equal(Eg, Ee)
+    # the first history entry is the batch evaluation at the starting point
+    E0 = q.qaoa_grad_batch(ctx, costs, g0, b0, item_cost=item_cost)[0]
+    assert np.array_equal(hg[0], E0)
+    Fs = [oracle.cost_table(oracle.canonical_of(Q)) for Q in Qs]
+    gr, br, hr = _adam_reference(Fs, item_cost, g0, b0, iters, lr)
+    assert np.max(np.abs(gg - gr)) <= 1e-5 and np.max(np.abs(bg - br)) <= 1e-5
+    for i, ci in enumerate(item_cost):
+        scale = np.max(np.abs(Fs[ci]))
+        assert np.max(np.abs(hg[:, i] - hr[:, i])) / scale <= E_TOL
+        Ef = oracle.expectation(Fs[ci], oracle.evolve(Fs[ci], gg[i], bg[i]))
+        assert abs(Eg[i] - Ef) / scale <= E_TOL
+    for c in costs:
+        q.qaoa_cost_destroy(c)
+
+
+def test_adam_decreases_objective(q, ctx):
+    Q = inst.regular_maxcut_qubo(16, 4500)
+    cost = _cost(q, ctx, Q)
+    g0, b0 = inst.ramp_angles(3, amp=0.4)
+    g, b, hist, E = q.qaoa_optimize_adam(ctx, [cost], g0[None, :], b0[None, :], 40, lr=0.03)
+    assert E[0] < hist[0, 0] - 0.5
+    assert hist[-1, 0] < hist[0, 0]
+    q.qaoa_cost_destroy(cost)
