@@ -105,7 +105,8 @@ class ClockSampler:
 
 def _kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for name in ("kernels_pass.cu", "pass_common.cuh"):
+    for name in ("kernels_pass.cu", "kernels_adjoint.cu", "pass_common.cuh", "pass_body.cuh", "tma_util.cuh",
+                 "schedule.cuh"):
         with open(os.path.join(ROOT, "paper_2606_26297_b300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -191,14 +192,14 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
     ctx = q.qaoa_ctx_create(local, stream.cuda_stream, profile=True)
 
-    Q, gamma, beta = inst.workload_dense30(N_QUBITS, DEPTH)
-    n, p = Q.n, DEPTH
+    Q, gamma, beta = inst.workload_dense30(args.n, args.p)
+    n, p = Q.n, args.p
     # pinned host inputs and outputs
     H = torch.from_numpy(Q.H.astype(np.float32)).pin_memory()
     f = torch.from_numpy(Q.f.astype(np.float32)).pin_memory()
     g_h = torch.from_numpy(np.asarray(gamma, dtype=np.float64)).pin_memory()
     b_h = torch.from_numpy(np.asarray(beta, dtype=np.float64)).pin_memory()
-    caps = [10, 10, 10]
+    caps = [n // 3 + (1 if m < n % 3 else 0) for m in range(3)]
 
     def step():
         cost = q.qaoa_build_cost(ctx, H.numpy(), f.numpy(), Q.c0, "f32")
@@ -272,9 +273,10 @@ def run_gpu(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "c64 (f32 arithmetic; f64 reductions)",
             "data": "synthetic",
             "config": {"workload": f"dense N(0,1) float32 QUBO n={n}, p={p}, forward+adjoint+top-{KTOP}, "
-                                   "3 QPUs x 10 contiguous + factorisation check",
+                                   f"3 QPUs of capacity {caps} contiguous + factorisation check",
                        "n": n, "p": p, "parallelism": f"replicas x{ws}",
-                       "l2": "inputs larger than L2 (8 GiB state + 4 GiB table per pass)"},
+                       "l2": f"inputs larger than L2 ({8 * 2 ** n / 2 ** 30:g} GiB state + "
+                             f"{4 * 2 ** n / 2 ** 30:g} GiB table per pass)"},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                          "peak_source": f"{peak_src} hbm_gbs", "unit": "GB/s", "frac": achieved / peak,
                          "alg_bytes_per_launch": per_launch,
@@ -301,6 +303,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--n", type=int, default=N_QUBITS, help="qubits (default: the n=30 workload)")
+    ap.add_argument("--p", type=int, default=DEPTH, help="depth (default 8)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
