@@ -295,6 +295,136 @@ def run_gpu(args):
         dist.destroy_process_group()
     return 0
 
+# ---- secondary workloads (not the headline line) ------------------------------------------
+
+def _event_time(torch, stream, fn, reps):
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        out = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1000.0 / reps, out
+
+
+def run_workload(args):
+    """Secondary measurements, one JSON line each:
+      fd       adjoint gradient vs central finite differences from forward-only
+               evaluations (one parameter set: MaxCut n=26 p=4; a batch: 256
+               sets on the n=20 integer QUBO, p=4), time and error vs adjoint;
+      batch20  256 multi-start sets, n=20, p=4: batched fwd+adjoint, and Adam
+               steps replayed from a CUDA graph;
+      ragged   64 integer QUBOs with n in [10, 22], p=4, one request;
+      uc32     unit-commitment QUBO n=32, p=6: `--iters` Adam steps on the
+               exact gradient (CUDA graph)."""
+    import torch
+    from paper_2606_26297_b300 import build_lib
+    build_lib.build()
+    from paper_2606_26297_b300 import instances as inst
+    from paper_2606_26297_b300 import qaoa as q
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    ctx = q.qaoa_ctx_create(0, stream.cuda_stream)
+    res = {"workload": args.workload}
+    if args.workload == "fd":
+        Q, g, b = inst.workload_maxcut26()
+        cost = q.qaoa_build_cost(ctx, Q.H, Q.f, Q.c0, "i32")
+        p = len(g)
+        q.qaoa_grad(ctx, cost, g, b)
+        t_adj, (E, dg, db) = _event_time(torch, stream, lambda: q.qaoa_grad(ctx, cost, g, b), args.steps)
+        ref = np.concatenate([dg, db])
+        sc = np.max(np.abs(ref))
+        sweep = {}
+        t_fd = None
+        for h in (1e-2, 3e-3, 1e-3, 3e-4, 1e-4):
+            G, B = [], []
+            for k in range(2 * p):
+                for sgn in (1, -1):
+                    gg, bb = np.array(g, float), np.array(b, float)
+                    (gg if k < p else bb)[k % p] += sgn * h
+                    G.append(gg)
+                    B.append(bb)
+            G, B = np.array(G), np.array(B)
+            t, Ef = _event_time(torch, stream, lambda: q.qaoa_grad_batch(ctx, [cost], G, B, grad=False), args.steps)
+            d = (Ef[0::2] - Ef[1::2]) / (2 * h)
+            sweep[f"{h:g}"] = float(np.max(np.abs(d - ref)) / sc)
+            t_fd = t
+        res.update({"single": {"n": 26, "p": p, "adjoint_ms": 1e3 * t_adj, "fd_ms": 1e3 * t_fd,
+                               "fd_evals": 4 * p, "speedup": t_fd / t_adj,
+                               "fd_rel_err_vs_adjoint_by_h": sweep}})
+        q.qaoa_cost_destroy(cost)
+        # batched: 256 sets on n=20
+        Q, G0, B0 = inst.workload_batch20()
+        cost = q.qaoa_build_cost(ctx, Q.H, Q.f, Q.c0, "i32")
+        nb, p = G0.shape
+        q.qaoa_grad_batch(ctx, [cost], G0, B0)
+        t_adj, (E, dg, db) = _event_time(torch, stream, lambda: q.qaoa_grad_batch(ctx, [cost], G0, B0), args.steps)
+        h = 1e-3
+        G, B = [], []
+        for i in range(nb):
+            for k in range(2 * p):
+                for sgn in (1, -1):
+                    gg, bb = G0[i].copy(), B0[i].copy()
+                    (gg if k < p else bb)[k % p] += sgn * h
+                    G.append(gg)
+                    B.append(bb)
+        G, B = np.array(G), np.array(B)
+        t_fd, Ef = _event_time(torch, stream, lambda: q.qaoa_grad_batch(ctx, [cost], G, B, grad=False), 1)
+        d = ((Ef[0::2] - Ef[1::2]) / (2 * h)).reshape(nb, 2 * p)
+        refb = np.concatenate([dg, db], axis=1)
+        err = float(np.max(np.abs(d - refb)) / np.max(np.abs(refb)))
+        res.update({"batched": {"n": 20, "p": p, "sets": nb, "adjoint_ms": 1e3 * t_adj, "fd_ms": 1e3 * t_fd,
+                                "fd_evals": 4 * p * nb, "speedup": t_fd / t_adj, "h": h,
+                                "fd_rel_err_vs_adjoint": err}})
+        q.qaoa_cost_destroy(cost)
+    elif args.workload == "batch20":
+        Q, G0, B0 = inst.workload_batch20()
+        cost = q.qaoa_build_cost(ctx, Q.H, Q.f, Q.c0, "i32")
+        nb, p = G0.shape
+        q.qaoa_grad_batch(ctx, [cost], G0, B0)
+        t, _ = _event_time(torch, stream, lambda: q.qaoa_grad_batch(ctx, [cost], G0, B0), args.steps)
+        iters = args.iters
+        q.qaoa_optimize_adam(ctx, [cost], G0, B0, 2, lr=0.01)
+        t0 = time.perf_counter()
+        g1, b1, hist, Ef = q.qaoa_optimize_adam(ctx, [cost], G0, B0, iters, lr=0.01)
+        t_adam = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        q.qaoa_optimize_adam(ctx, [cost], G0, B0, iters, lr=0.01, use_graph=False)
+        t_eager = time.perf_counter() - t0
+        res.update({"n": 20, "p": p, "sets": nb, "grad_batch_ms": 1e3 * t,
+                    "layer_evals_per_s": nb * p / t, "amplitudes_per_pass": nb * 2 ** 20,
+                    "adam_iters": iters, "adam_graph_ms_per_step": 1e3 * t_adam / iters,
+                    "adam_eager_ms_per_step": 1e3 * t_eager / iters,
+                    "mean_E_start": float(hist[0].mean()), "mean_E_end": float(Ef.mean())})
+        q.qaoa_cost_destroy(cost)
+    elif args.workload == "ragged":
+        qs, G0, B0 = inst.workload_ragged()
+        costs = [q.qaoa_build_cost(ctx, Qi.H, Qi.f, Qi.c0, "i32") for Qi in qs]
+        ic = list(range(len(qs)))
+        q.qaoa_grad_batch(ctx, costs, G0, B0, item_cost=ic)
+        t, _ = _event_time(torch, stream, lambda: q.qaoa_grad_batch(ctx, costs, G0, B0, item_cost=ic), args.steps)
+        ns = [Qi.n for Qi in qs]
+        res.update({"qubos": len(qs), "n_min": min(ns), "n_max": max(ns), "p": G0.shape[1],
+                    "grad_batch_ms": 1e3 * t, "layer_evals_per_s": len(qs) * G0.shape[1] / t,
+                    "amplitudes": int(sum(2 ** n for n in ns))})
+        for c in costs:
+            q.qaoa_cost_destroy(c)
+    elif args.workload == "uc32":
+        Q, g, b = inst.workload_uc32()
+        cost = q.qaoa_build_cost(ctx, Q.H, Q.f, Q.c0, "f32")
+        p = len(g)
+        t0 = time.perf_counter()
+        g1, b1, hist, Ef = q.qaoa_optimize_adam(ctx, [cost], g[None, :], b[None, :], args.iters, lr=0.01)
+        dt = time.perf_counter() - t0
+        res.update({"n": 32, "p": p, "adam_iters": args.iters, "seconds": dt, "s_per_step": dt / args.iters,
+                    "layer_evals_per_s": args.iters * p / dt, "E_start": float(hist[0, 0]),
+                    "E_end": float(Ef[0]), "E_min_history": float(hist[:, 0].min())})
+        q.qaoa_cost_destroy(cost)
+    print(json.dumps(res), flush=True)
+    q.qaoa_ctx_destroy(ctx)
+    return 0
+
 
 def main():
     ap = argparse.ArgumentParser()
@@ -305,7 +435,12 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--n", type=int, default=N_QUBITS, help="qubits (default: the n=30 workload)")
     ap.add_argument("--p", type=int, default=DEPTH, help="depth (default 8)")
+    ap.add_argument("--workload", default="", choices=["", "fd", "batch20", "ragged", "uc32"],
+                    help="a secondary measurement instead of the headline step")
+    ap.add_argument("--iters", type=int, default=200, help="Adam steps for --workload batch20/uc32")
     args = ap.parse_args()
+    if args.workload:
+        return run_workload(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

@@ -143,6 +143,12 @@ qaoa_status qaoa_state_copy_to_host(qaoa_ctx ctx, qaoa_state state, float *amps)
  * pointer stays owned by the state. */
 qaoa_status qaoa_state_device_ptr(qaoa_state state, void **amps, int64_t *count);
 
+/* Amplitudes at `count` basis indices: idx is a host array of count indices
+ * (each < 2^n, else QAOA_ERR_INVALID_ARG); out is a host array of count
+ * complex values (2 floats each, or 2 doubles for a complex128 state).  For
+ * reading a few entries of a state too large to copy to the host. */
+qaoa_status qaoa_state_gather(qaoa_ctx ctx, qaoa_state state, const uint64_t *idx, int count, void *out);
+
 /* <H_C> = sum_x |psi_x|^2 F(x) (Eq. qaoa_expectation_expanded), reduced
  * deterministically in FP64 (same inputs give the same bits). */
 qaoa_status qaoa_expect(qaoa_ctx ctx, qaoa_cost cost, qaoa_state state, double *out_expect);

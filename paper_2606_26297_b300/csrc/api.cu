@@ -772,6 +772,31 @@ qaoa_status qaoa_state_device_ptr(qaoa_state s, void **amps, int64_t *count) {
     return QAOA_OK;
 }
 
+qaoa_status qaoa_state_gather(qaoa_ctx c, qaoa_state s, const uint64_t *idx, int count, void *out) {
+    if (!c || !s || !idx || !out || count < 0) return fail(QAOA_ERR_INVALID_ARG, "null argument or count < 0");
+    if (count == 0) return QAOA_OK;
+    const uint64_t N = (uint64_t)1 << s->n;
+    for (int i = 0; i < count; ++i)
+        if (idx[i] >= N) return fail(QAOA_ERR_INVALID_ARG, "index %llu outside the 2^%d amplitudes", (unsigned long long)idx[i], s->n);
+    QAOA_TRY(set_device(c->device));
+    const int es = s->fp64 ? 16 : 8;
+    const size_t ib = (size_t)count * 8, ob = (size_t)count * es;
+    QAOA_TRY(c->misc.ensure(ib + ob + 64, &c->held, c->opt.memory_budget));
+    char *m = c->misc.as<char>();
+    unsigned int *bad = reinterpret_cast<unsigned int *>(m + ib + ob);
+    CUDA_TRY(cudaMemcpyAsync(m, idx, ib, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(cudaMemsetAsync(bad, 0, 4, c->stream));
+    CUDA_TRY(launch_gather(s->amps, es, s->n, reinterpret_cast<const unsigned long long *>(m), count, m + ib, bad,
+                           c->stream));
+    c->launches_total += 1;
+    unsigned int hb = 0;
+    CUDA_TRY(cudaMemcpyAsync(out, m + ib, ob, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(&hb, bad, 4, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (hb) return fail(QAOA_ERR_INVALID_ARG, "gather index outside the state");
+    return QAOA_OK;
+}
+
 qaoa_status qaoa_expect(qaoa_ctx c, qaoa_cost cost, qaoa_state s, double *out) {
     if (!c || !cost || !s || !out) return fail(QAOA_ERR_INVALID_ARG, "null argument");
     if (s->n != cost->n) return fail(QAOA_ERR_INVALID_ARG, "state and cost differ in n");

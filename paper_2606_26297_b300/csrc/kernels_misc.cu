@@ -255,6 +255,32 @@ cudaError_t launch_expect(const float2 *psi, const int32_t *T, int n, double *pa
     return cudaGetLastError();
 }
 
+// out[i] = amps[idx[i]] (element size esize = 8 or 16 bytes); an index
+// outside the state sets *bad and leaves out[i] untouched.
+__global__ void gather_kernel(const unsigned char *__restrict__ amps, int esize, unsigned long long N,
+                              const unsigned long long *__restrict__ idx, int count, unsigned char *out,
+                              unsigned int *bad) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const unsigned long long x = idx[i];
+    if (x >= N) {
+        atomicOr(bad, 1u);
+        return;
+    }
+    if (esize == 16)
+        reinterpret_cast<double2 *>(out)[i] = reinterpret_cast<const double2 *>(amps)[x];
+    else
+        reinterpret_cast<float2 *>(out)[i] = reinterpret_cast<const float2 *>(amps)[x];
+}
+
+cudaError_t launch_gather(const void *amps, int esize, int n, const unsigned long long *idx, int count, void *out,
+                          unsigned int *bad, cudaStream_t st) {
+    gather_kernel<<<(count + 255) / 256, 256, 0, st>>>(static_cast<const unsigned char *>(amps), esize,
+                                                        1ull << n, idx, count, static_cast<unsigned char *>(out),
+                                                        bad);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_topk_chunks(const float2 *psi, int n, int K, unsigned long long *out, cudaStream_t st) {
     const long long N = 1ll << n;
     const unsigned grid = (unsigned)((N + 8191) / 8192);

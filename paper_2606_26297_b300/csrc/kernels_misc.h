@@ -22,6 +22,8 @@ cudaError_t launch_cost_build(CostBuildArgs a, int *nblocks_out, cudaStream_t st
 int cost_build_blocks(int n);
 
 cudaError_t launch_expect(const float2 *psi, const int32_t *T, int n, double *partials, cudaStream_t st);
+cudaError_t launch_gather(const void *amps, int esize, int n, const unsigned long long *idx, int count, void *out,
+                          unsigned int *bad, cudaStream_t st);
 cudaError_t launch_topk_chunks(const float2 *psi, int n, int K, unsigned long long *out, cudaStream_t st);
 
 constexpr int SMALL_MAXP = 64;

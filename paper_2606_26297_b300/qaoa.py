@@ -70,6 +70,7 @@ _SIGS = {
     "qaoa_state_destroy": ([_P], None),
     "qaoa_state_copy_to_host": ([_P, _P, _P], _I),
     "qaoa_state_device_ptr": ([_P, ctypes.POINTER(_P), _PI64], _I),
+    "qaoa_state_gather": ([_P, _P, _PU64, _I, _P], _I),
     "qaoa_expect": ([_P, _P, _P, _PD], _I),
     "qaoa_topk": ([_P, _P, _P, _I, _PU64, _PF, _PD, _PU64, _PD, _PF], _I),
     "qaoa_grad": ([_P, _P, _I, _PD, _PD, _PD, _PD, _PD, _I, _PU64, _PF], _I),
@@ -191,6 +192,14 @@ def qaoa_state_device_ptr(state):
     cnt = ctypes.c_int64()
     _check(_lib.qaoa_state_device_ptr(state, ctypes.byref(p), ctypes.byref(cnt)))
     return p.value, cnt.value
+
+
+def qaoa_state_gather(ctx, state, idx, fp64: bool = False) -> np.ndarray:
+    """Amplitudes at the given basis indices (complex64, or complex128)."""
+    ix = np.ascontiguousarray(np.asarray(idx, dtype=np.uint64).reshape(-1))
+    out = np.zeros(ix.size, dtype=np.complex128 if fp64 else np.complex64)
+    _check(_lib.qaoa_state_gather(ctx, state, ix.ctypes.data_as(_PU64), int(ix.size), out.ctypes.data))
+    return out
 
 
 def qaoa_expect(ctx, cost, state) -> float:

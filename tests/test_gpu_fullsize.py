@@ -1,0 +1,243 @@
+"""GPU parity at the full sizes of the named workloads, in the launch
+configuration the benchmark times.
+
+  * MaxCut on a random 3-regular graph, n=26, p=4: the whole state, E and the
+    8-parameter gradient against the FP64 oracle (which still finishes in
+    seconds at n=26), the gradient against central finite differences taken
+    on the GPU, and E at p=1 against the published closed form.
+  * n=30, p=8: the oracle cannot hold 2^30 amplitudes, so the check uses a
+    QUBO made of three uncoupled dense N(0,1) blocks of 10 variables: its
+    state is the tensor product of the blocks' states, E and the gradient are
+    sums over blocks, and each block is small enough for the oracle.  The
+    dense n=30 workload itself is checked through properties that hold at any
+    size.
+  * n=32 (unit-commitment shape, p=6): the same block construction (4 blocks
+    of 8) pins amplitudes, E and the gradient; the unit-commitment instance is
+    checked through its table entries (sampled against the oracle's F(x)),
+    E consistency and finite differences.
+"""
+import gc
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from closed_forms import maxcut_p1_closed_form
+from paper_2606_26297_b300 import instances as inst
+
+pytestmark = pytest.mark.gpu
+
+E_TOL = 1e-5
+G_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def q():
+    from paper_2606_26297_b300 import build_lib
+    build_lib.build()
+    from paper_2606_26297_b300 import qaoa
+    return qaoa
+
+
+def _cost(q, ctx, Q):
+    return q.qaoa_build_cost(ctx, Q.H, Q.f, Q.c0, "i32" if Q.dtype == "i32" else "f32")
+
+
+def _grad_err(dg, db, dgo, dbo):
+    sc = max(np.max(np.abs(dgo)), np.max(np.abs(dbo)), 1e-12)
+    return max(np.max(np.abs(dg - dgo)), np.max(np.abs(db - dbo))) / sc
+
+
+def _fd_grad(q, ctx, cost, g, b, h):
+    """Central differences of E from forward-only batched evaluations on the GPU."""
+    p = len(g)
+    G, B = [], []
+    for k in range(2 * p):
+        for s in (+1, -1):
+            gg, bb = np.array(g, float), np.array(b, float)
+            if k < p:
+                gg[k] += s * h
+            else:
+                bb[k - p] += s * h
+            G.append(gg)
+            B.append(bb)
+    E = q.qaoa_grad_batch(ctx, [cost], np.array(G), np.array(B), grad=False)
+    d = (E[0::2] - E[1::2]) / (2 * h)
+    return d[:p], d[p:]
+
+
+# ---- MaxCut n=26, p=4 ------------------------------------------------------------------
+
+def test_maxcut26_full_state_and_gradient(q):
+    ctx = q.qaoa_ctx_create(0)
+    Q, g, b = inst.workload_maxcut26()
+    n = Q.n
+    cost = _cost(q, ctx, Q)
+    F = oracle.cost_table(oracle.canonical_of(Q))
+    info = q.qaoa_cost_info(cost)
+    T = q.qaoa_cost_copy_to_host(ctx, cost, n).astype(np.int64)
+    assert np.array_equal(T + info["k_c"], F.astype(np.int64))
+    st = q.qaoa_forward(ctx, cost, g, b)
+    psi = q.qaoa_state_copy_to_host(ctx, st, n).astype(np.complex128)
+    ref = oracle.evolve(F, g, b)
+    assert np.linalg.norm(psi - ref) <= 1e-5
+    E, dg, db, ti, tp = q.qaoa_grad(ctx, cost, g, b, k_top=10)
+    Eo, dgo, dbo = oracle.grad_adjoint(F, g, b)
+    assert abs(E - Eo) / np.max(np.abs(F)) <= E_TOL
+    assert _grad_err(dg, db, dgo, dbo) <= G_TOL
+    # top-10: probabilities descending, and each returned index is a valid
+    # member of the exact top-10 (MaxCut states come in complement pairs of
+    # equal probability, so ties are broken by rounding)
+    Po = np.abs(ref) ** 2
+    kth = np.sort(Po)[-10]
+    assert np.all(np.diff(tp) <= 0) and len(set(ti.tolist())) == 10
+    assert np.all(Po[ti.astype(np.int64)] >= kth - 1e-6 * Po.max())
+    # finite differences on the GPU (c64 forward evaluations): h = 1e-3 balances
+    # truncation (h^2 |E'''|/6) and rounding (~1e-6 max|F| / h); tolerance 1e-3
+    fg, fb = _fd_grad(q, ctx, cost, g, b, 1e-3)
+    assert _grad_err(fg, fb, dgo, dbo) <= 1e-3
+    # p=1: the published closed form for 3-regular MaxCut
+    edges = Q.meta["edges"]
+    for gamma, beta in [(0.45, 0.3), (-0.8, 1.1)]:
+        s1 = q.qaoa_forward(ctx, cost, [gamma], [beta])
+        E1 = q.qaoa_expect(ctx, cost, s1)
+        assert abs(E1 - maxcut_p1_closed_form(n, edges, gamma, beta)) / np.max(np.abs(F)) <= E_TOL
+        q.qaoa_state_destroy(s1)
+    q.qaoa_state_destroy(st)
+    q.qaoa_cost_destroy(cost)
+    q.qaoa_ctx_destroy(ctx)
+
+
+# ---- block-separable pins at n=30 and n=32 -----------------------------------------------
+
+def _block_check(q, ctx, blocks, g, b, nsample, seed):
+    """State, E and gradient of an uncoupled block QUBO against the oracle on
+    each block: psi(x) = prod_b psi_b(x_b), E = sum_b E_b, grad = sum_b grad_b."""
+    Qb = inst.block_diagonal_qubo(blocks)
+    n = Qb.n
+    cost = _cost(q, ctx, Qb)
+    Fs = [oracle.cost_table(oracle.canonical_of(B)) for B in blocks]
+    psis = [oracle.evolve(Fb, g, b) for Fb in Fs]
+    grads = [oracle.grad_adjoint(Fb, g, b) for Fb in Fs]
+    Eo = sum(r[0] for r in grads)
+    dgo = sum(r[1] for r in grads)
+    dbo = sum(r[2] for r in grads)
+    fmax = sum(np.max(np.abs(Fb)) for Fb in Fs)
+    E, dg, db = q.qaoa_grad(ctx, cost, g, b)
+    assert abs(E - Eo) / fmax <= E_TOL
+    assert _grad_err(dg, db, dgo, dbo) <= G_TOL
+    st = q.qaoa_forward(ctx, cost, g, b)
+    assert abs(q.qaoa_expect(ctx, cost, st) - Eo) / fmax <= E_TOL
+    rng = inst.SplitMix64(seed)
+    xs = np.array([rng.next_u64() >> (64 - n) for _ in range(nsample)], dtype=np.uint64)
+    got = q.qaoa_state_gather(ctx, st, xs).astype(np.complex128)
+    ref = np.ones(nsample, dtype=np.complex128)
+    off = 0
+    for B, pb in zip(blocks, psis):
+        ref *= pb[(xs >> np.uint64(off)) & np.uint64((1 << B.n) - 1)]
+        off += B.n
+    # amplitudes are ~2^-n/2: compare the sampled L2 error scaled to the whole state
+    err = np.linalg.norm(got - ref) * math.sqrt(2.0 ** n / nsample)
+    assert err <= 1e-5, err
+    q.qaoa_state_destroy(st)
+    q.qaoa_cost_destroy(cost)
+
+
+def test_block_separable_n30_p8(q):
+    ctx = q.qaoa_ctx_create(0)
+    blocks = [inst.normal_qubo(10, 1003 + k) for k in range(3)]
+    Qd, g, b = inst.workload_dense30()
+    _block_check(q, ctx, blocks, g, b, 4096, 31)
+    q.qaoa_ctx_destroy(ctx)
+    gc.collect()
+
+
+def test_block_separable_n32_p6(q):
+    ctx = q.qaoa_ctx_create(0)
+    blocks = [inst.unit_commitment_qubo(8, 1005 + k) for k in range(4)]
+    g, b = inst.ramp_angles(6, gamma_scale=math.sqrt(32) / sum(inst.coefficient_norm(B) for B in blocks))
+    _block_check(q, ctx, blocks, g, b, 4096, 32)
+    q.qaoa_ctx_destroy(ctx)
+    gc.collect()
+
+
+# ---- the dense workloads themselves: properties at full size --------------------------
+
+def test_dense30_properties(q):
+    ctx = q.qaoa_ctx_create(0)
+    Q, g, b = inst.workload_dense30()
+    n = Q.n
+    cost = _cost(q, ctx, Q)
+    info = q.qaoa_cost_info(cost)
+    cq = oracle.canonical_of(Q)
+    rng = inst.SplitMix64(300)
+    xs = np.array([rng.next_u64() >> (64 - n) for _ in range(256)] + [info["argmin"]], dtype=np.uint64)
+    # table entries against the oracle's F(x), within the fixed-point rounding bound
+    s = info["shift_bits"]
+    bound = (1 + n + n * (n - 1) / 2) * 2.0 ** (-(s + 1))
+    E, dg, db, ti, tp = q.qaoa_grad(ctx, cost, g, b, k_top=10)
+    st = q.qaoa_forward(ctx, cost, g, b)
+    E2 = q.qaoa_expect(ctx, cost, st)
+    assert abs(E - E2) <= 1e-6 * max(1.0, abs(E))
+    # the top-10 of the gradient call's final state and of the forward state
+    # agree up to rounding (the two paths apply the last mixer's bit rounds in
+    # opposite order)
+    tk = q.qaoa_topk(ctx, cost, st, 10)
+    amps = q.qaoa_state_gather(ctx, st, np.asarray(ti, dtype=np.uint64))
+    P = amps.real.astype(np.float64) ** 2 + amps.imag.astype(np.float64) ** 2
+    assert np.max(np.abs(P - tp)) <= 1e-4 * tp[0]
+    assert np.min(P) >= tk["prob"][-1] * (1 - 1e-4)
+    assert np.max(np.abs(tk["cost"] - oracle.cost_at(cq, [int(x) for x in tk["idx"]]))) <= bound
+    Fx = oracle.cost_at(cq, [int(x) for x in xs])
+    # the brute-force minimum is the oracle's F at the recorded argmin, and no sample is lower
+    assert abs(info["min_cost"] - Fx[-1]) <= bound
+    assert np.min(Fx) >= info["min_cost"] - bound
+    # E cannot lie below the minimum of F; the gradient is finite
+    assert info["min_cost"] - bound <= E
+    assert np.all(np.isfinite(dg)) and np.all(np.isfinite(db))
+    q.qaoa_state_destroy(st)
+    q.qaoa_cost_destroy(cost)
+    q.qaoa_ctx_destroy(ctx)
+    gc.collect()
+
+
+def test_uc32_properties_and_fd(q):
+    ctx = q.qaoa_ctx_create(0)
+    Q, g, b = inst.workload_uc32()
+    n = Q.n
+    cost = _cost(q, ctx, Q)
+    info = q.qaoa_cost_info(cost)
+    cq = oracle.canonical_of(Q)
+    s = info["shift_bits"]
+    bound = (1 + n + n * (n - 1) / 2) * 2.0 ** (-(s + 1))
+    E, dg, db = q.qaoa_grad(ctx, cost, g, b)
+    # two parameters by central differences of GPU forward evaluations; the
+    # step is relative to the parameter's scale (gamma ~ 1e-6 here, since the
+    # objective reaches 1e6)
+    for k in (0, 7):
+        gp, bp = np.array(g, float), np.array(b, float)
+        gm, bm = gp.copy(), bp.copy()
+        if k < 6:
+            h = 1e-3 * np.max(np.abs(g))
+            gp[k] += h
+            gm[k] -= h
+            ref, scale = dg[k], np.max(np.abs(dg))
+        else:
+            h = 1e-3
+            bp[k - 6] += h
+            bm[k - 6] -= h
+            ref, scale = db[k - 6], np.max(np.abs(db))
+        Ep = q.qaoa_grad_batch(ctx, [cost], gp[None, :], bp[None, :], grad=False)[0]
+        Em = q.qaoa_grad_batch(ctx, [cost], gm[None, :], bm[None, :], grad=False)[0]
+        assert abs((Ep - Em) / (2 * h) - ref) <= 1e-3 * scale, (k, (Ep - Em) / (2 * h), ref)
+    st = q.qaoa_forward(ctx, cost, g, b)
+    assert abs(q.qaoa_expect(ctx, cost, st) - E) <= 1e-6 * max(1.0, abs(E))
+    tk = q.qaoa_topk(ctx, cost, st, 8)
+    Fx = oracle.cost_at(cq, [int(x) for x in tk["idx"]] + [int(tk["argmin"])])
+    assert np.max(np.abs(tk["cost"] - Fx[:-1])) <= bound
+    assert abs(tk["min_cost"] - Fx[-1]) <= bound
+    q.qaoa_state_destroy(st)
+    q.qaoa_cost_destroy(cost)
+    q.qaoa_ctx_destroy(ctx)
+    gc.collect()

@@ -11,6 +11,7 @@ from itertools import product
 import numpy as np
 import pytest
 
+from closed_forms import maxcut_p1_closed_form
 import oracle
 from paper_2606_26297_b300 import instances as inst
 
@@ -185,29 +186,6 @@ def test_block_diagonal_tensor_product():
 
 # ---- published p=1 MaxCut expectation -----------------------------------------
 
-def _maxcut_p1_closed_form(n, edges, gamma, beta):
-    """Wang, Hadfield, Jiang, Rieffel, PRA 97, 022304 (2018), Thm. 1: for the
-    cut operator C = sum (1 - Z_u Z_v)/2 and |g,b> = e^{-ibB}e^{-igC}|+>,
-      <C_uv> = 1/2 + 1/4 sin4b sing (cos^du g + cos^dv g)
-               - 1/4 sin^2 2b cos^{du+dv-2t} g (1 - cos^t 2g),
-    du = deg(u)-1, dv = deg(v)-1, t = #triangles on (u,v).
-    The QUBO here has F = -cut, so exp(-i g F) = exp(-i (-g) C) and
-    E_F(g, b) = -E_cut(-g, b)."""
-    adj = [set() for _ in range(n)]
-    for u, v in edges:
-        adj[u].add(v)
-        adj[v].add(u)
-    g = -gamma
-    tot = 0.0
-    for u, v in edges:
-        du, dv = len(adj[u]) - 1, len(adj[v]) - 1
-        t = len(adj[u] & adj[v])
-        val = 0.5 + 0.25 * math.sin(4 * beta) * math.sin(g) * (math.cos(g) ** du + math.cos(g) ** dv)
-        val -= 0.25 * math.sin(2 * beta) ** 2 * math.cos(g) ** (du + dv - 2 * t) * (1 - math.cos(2 * g) ** t)
-        tot += val
-    return -tot
-
-
 def _prism():
     return [(0, 1), (1, 2), (0, 2), (3, 4), (4, 5), (3, 5), (0, 3), (1, 4), (2, 5)]
 
@@ -236,7 +214,7 @@ def test_maxcut_p1_analytic(name, n, edges):
     F = oracle.cost_table(oracle.canonical_of(q))
     for gamma, beta in [(0.3, 0.2), (0.61, 1.17), (-1.4, 0.35), (2.2, -0.9)]:
         E = oracle.expectation(F, oracle.evolve(F, [gamma], [beta]))
-        assert abs(E - _maxcut_p1_closed_form(n, edges, gamma, beta)) < 1e-11
+        assert abs(E - maxcut_p1_closed_form(n, edges, gamma, beta)) < 1e-11
 
 
 # ---- gradients ---------------------------------------------------------------
@@ -270,7 +248,7 @@ def test_adjoint_matches_analytic_p1_derivative():
     F = oracle.cost_table(oracle.canonical_of(inst.maxcut_qubo(n, edges)))
     gamma, beta, h = 0.47, 0.33, 1e-6
     _, dg, db = oracle.grad_adjoint(F, [gamma], [beta])
-    cf = lambda g_, b_: _maxcut_p1_closed_form(n, edges, g_, b_)
+    cf = lambda g_, b_: maxcut_p1_closed_form(n, edges, g_, b_)
     ag = (cf(gamma + h, beta) - cf(gamma - h, beta)) / (2 * h)
     ab = (cf(gamma, beta + h) - cf(gamma, beta - h)) / (2 * h)
     assert abs(dg[0] - ag) < 1e-7 * max(1, abs(ag))
