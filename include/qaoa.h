@@ -85,7 +85,9 @@ typedef struct {
     int64_t memory_budget;  /* bytes of device memory the context may hold; 0 = free memory */
     int32_t max_fused_qubits; /* qubits per mixer pass: 0 = default (10), else 3..10 */
     int32_t state_fp64;     /* 1: complex128 states and arithmetic (n <= 12 only) */
-    int32_t reserved[6];    /* must be zero */
+    int32_t table_build;    /* objective table: 0 = tensor cores (tcgen05) for n >= 14 and the
+                               SIMT Gray-code kernel below that; 1 = the SIMT kernel for every n */
+    int32_t reserved[5];    /* must be zero */
 } qaoa_options;
 
 typedef struct qaoa_ctx_s *qaoa_ctx;     /* device, stream, options, scratch, plan cache */

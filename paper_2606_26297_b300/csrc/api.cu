@@ -604,7 +604,8 @@ qaoa_status qaoa_ctx_create(int device, void *cuda_stream, const qaoa_options *o
     if (opt) o = *opt;
     if (o.max_fused_qubits != 0 && (o.max_fused_qubits < 3 || o.max_fused_qubits > 10))
         return fail(QAOA_ERR_INVALID_ARG, "max_fused_qubits must be 0 or in [3, 10]");
-    for (int k = 0; k < 6; ++k)
+    if (o.table_build < 0 || o.table_build > 1) return fail(QAOA_ERR_INVALID_ARG, "table_build must be 0 or 1");
+    for (int k = 0; k < 5; ++k)
         if (o.reserved[k]) return fail(QAOA_ERR_INVALID_ARG, "options.reserved[%d] must be zero", k);
     auto *c = new qaoa_ctx_s();
     c->device = device;
@@ -647,34 +648,91 @@ qaoa_status qaoa_build_cost(qaoa_ctx c, const qaoa_qubo *q, qaoa_cost *out) {
             return fail(QAOA_ERR_OUT_OF_MEMORY, "objective table (%zu bytes): %s", N * 4, cudaGetErrorString(e));
         }
     }
-    const int nblk = cost_build_blocks(n);
     const size_t coef_bytes = (size_t)(n + n * n) * 8;
-    QAOA_TRY(c->misc.ensure(coef_bytes + (size_t)nblk * 16 + 64, &c->held, c->opt.memory_budget));
     std::vector<long long> coef(n + n * n);
     for (int i = 0; i < n; ++i) coef[i] = h->fp.ell_q[i];
     for (int k = 0; k < n * n; ++k) coef[n + k] = h->fp.b_q[k];
-    char *m = c->misc.as<char>();
-    CUDA_TRY(cudaMemcpyAsync(m, coef.data(), coef_bytes, cudaMemcpyHostToDevice, c->stream));
-    CostBuildArgs a{};
-    a.n = n;
-    a.ell = reinterpret_cast<long long *>(m);
-    a.b = reinterpret_cast<long long *>(m) + n;
-    a.c_off = h->fp.c0_q - h->fp.k_c;
-    a.T = h->T;
-    a.blk_val = reinterpret_cast<long long *>(m + coef_bytes);
-    a.blk_idx = reinterpret_cast<unsigned long long *>(m + coef_bytes + (size_t)nblk * 8);
-    a.min_val = reinterpret_cast<long long *>(m + coef_bytes + (size_t)nblk * 16);
-    a.min_idx = reinterpret_cast<unsigned long long *>(m + coef_bytes + (size_t)nblk * 16 + 8);
-    int nb = 0;
-    {
-        ProfScope ps(c, 2, (double)N * 4.0);
-        CUDA_TRY(launch_cost_build(a, &nb, c->stream));
-        c->launches_total += 2;
+    // tensor-core build for n >= 14 unless disabled: the cross couplings between
+    // the low n - n_hi and the high n_hi = min(16, n - 7) variables must fit
+    // four base-2^11 digits (always true for tables that fit int32)
+    int digits = -1;
+    const int nhi = n - 7 < 16 ? n - 7 : 16, nlo = n - nhi;
+    if (n >= 14 && c->opt.table_build == 0) {
+        long long wmax = 0;
+        for (int j = 0; j < nhi; ++j) {
+            long long w = 0;
+            for (int i = 0; i < nlo; ++i) w += std::llabs(h->fp.b_q[(size_t)i * n + nlo + j]);
+            wmax = std::max(wmax, w);
+        }
+        digits = table_mma_digits(wmax);
+    }
+    long long *min_val = nullptr;
+    unsigned long long *min_idx = nullptr;
+    if (digits > 0) {
+        const int grid = c->num_sms;
+        const size_t alo_b = ((size_t)8 << nlo), ahi_b = ((size_t)8 << nhi), w_b = (size_t)digits * 32 << nlo;
+        const size_t tot = coef_bytes + (size_t)grid * 16 + 64 + alo_b + ahi_b + w_b + 1024;
+        QAOA_TRY(c->misc.ensure(tot, &c->held, c->opt.memory_budget));
+        QAOA_TRY(c->status.ensure(16, &c->held, c->opt.memory_budget));
+        char *m = c->misc.as<char>();
+        CUDA_TRY(cudaMemcpyAsync(m, coef.data(), coef_bytes, cudaMemcpyHostToDevice, c->stream));
+        CUDA_TRY(cudaMemsetAsync(c->status.p, 0, 16, c->stream));
+        size_t o = (coef_bytes + 255) & ~size_t(255);
+        TableMmaArgs a{};
+        a.n = n;
+        a.digits = digits;
+        a.ell = reinterpret_cast<long long *>(m);
+        a.b = reinterpret_cast<long long *>(m) + n;
+        a.c_off = h->fp.c0_q - h->fp.k_c;
+        a.T = h->T;
+        a.blk_val = reinterpret_cast<long long *>(m + o);
+        a.blk_idx = reinterpret_cast<unsigned long long *>(m + o + (size_t)grid * 8);
+        o += (size_t)grid * 16;
+        a.min_val = reinterpret_cast<long long *>(m + o);
+        a.min_idx = reinterpret_cast<unsigned long long *>(m + o + 8);
+        o = (o + 16 + 255) & ~size_t(255);
+        a.alo = reinterpret_cast<long long *>(m + o);
+        o += alo_b;
+        a.ahi = reinterpret_cast<long long *>(m + o);
+        o += ahi_b;
+        a.wdig = reinterpret_cast<__half *>(m + o);
+        a.status = c->status.as<unsigned int>();
+        {
+            ProfScope ps(c, 2, (double)N * 4.0);
+            CUDA_TRY(launch_table_mma(a, grid, c->stream));
+            c->launches_total += 3;
+        }
+        min_val = a.min_val;
+        min_idx = a.min_idx;
+        QAOA_TRY(status_check(c));
+    } else {
+        const int nblk = cost_build_blocks(n);
+        QAOA_TRY(c->misc.ensure(coef_bytes + (size_t)nblk * 16 + 64, &c->held, c->opt.memory_budget));
+        char *m = c->misc.as<char>();
+        CUDA_TRY(cudaMemcpyAsync(m, coef.data(), coef_bytes, cudaMemcpyHostToDevice, c->stream));
+        CostBuildArgs a{};
+        a.n = n;
+        a.ell = reinterpret_cast<long long *>(m);
+        a.b = reinterpret_cast<long long *>(m) + n;
+        a.c_off = h->fp.c0_q - h->fp.k_c;
+        a.T = h->T;
+        a.blk_val = reinterpret_cast<long long *>(m + coef_bytes);
+        a.blk_idx = reinterpret_cast<unsigned long long *>(m + coef_bytes + (size_t)nblk * 8);
+        a.min_val = reinterpret_cast<long long *>(m + coef_bytes + (size_t)nblk * 16);
+        a.min_idx = reinterpret_cast<unsigned long long *>(m + coef_bytes + (size_t)nblk * 16 + 8);
+        int nb = 0;
+        {
+            ProfScope ps(c, 2, (double)N * 4.0);
+            CUDA_TRY(launch_cost_build(a, &nb, c->stream));
+            c->launches_total += 2;
+        }
+        min_val = a.min_val;
+        min_idx = a.min_idx;
     }
     long long mv = 0;
     unsigned long long mi = 0;
-    CUDA_TRY(cudaMemcpyAsync(&mv, a.min_val, 8, cudaMemcpyDeviceToHost, c->stream));
-    CUDA_TRY(cudaMemcpyAsync(&mi, a.min_idx, 8, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(&mv, min_val, 8, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(&mi, min_idx, 8, cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
     h->minval = mv;
     h->argmin = mi;

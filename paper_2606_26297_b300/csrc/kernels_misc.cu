@@ -153,6 +153,12 @@ cudaError_t launch_cost_build(CostBuildArgs a, int *nblocks_out, cudaStream_t st
     return cudaGetLastError();
 }
 
+cudaError_t launch_argmin_reduce(const long long *val, const unsigned long long *idx, int m, long long *oval,
+                                 unsigned long long *oidx, cudaStream_t st) {
+    argmin_reduce_kernel<<<1, 256, 0, st>>>(val, idx, m, oval, oidx);
+    return cudaGetLastError();
+}
+
 int cost_build_blocks(int n) {
     const int nlo = n < 12 ? n : 12;
     const int t = (n - nlo) < MAXT ? (n - nlo) : MAXT;

@@ -1,6 +1,7 @@
 // Argument blocks and launchers of kernels_misc.cu.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "qaoa_internal.h"
@@ -20,6 +21,27 @@ struct CostBuildArgs {
 };
 cudaError_t launch_cost_build(CostBuildArgs a, int *nblocks_out, cudaStream_t st);
 int cost_build_blocks(int n);
+cudaError_t launch_argmin_reduce(const long long *val, const unsigned long long *idx, int m, long long *oval,
+                                 unsigned long long *oidx, cudaStream_t st);
+
+// Tensor-core table build (kernels_table_mma.cu), n >= 14.
+struct TableMmaArgs {
+    int n, nlo, nhi, digits;
+    const long long *ell;      // [n]    fixed-point linear coefficients (device)
+    const long long *b;        // [n*n]  fixed-point couplings, upper triangle (device)
+    long long c_off;           // c0_q - k_c
+    long long *alo;            // [2^nlo] objective of the low variables (+ c_off)
+    long long *ahi;            // [2^nhi] objective of the high variables
+    __half *wdig;              // [digits][2^nlo][16] base-2^11 digits of W
+    int32_t *T;                // [2^n] table out
+    long long *blk_val;        // [grid] per-CTA minimum
+    unsigned long long *blk_idx;
+    long long *min_val;        // final minimum (device scalar)
+    unsigned long long *min_idx;
+    unsigned int *status;      // set if a bounded wait expired
+};
+int table_mma_digits(long long wmax);  // -1 if W does not fit 4 digits
+cudaError_t launch_table_mma(TableMmaArgs a, int grid, cudaStream_t st);
 
 cudaError_t launch_expect(const float2 *psi, const int32_t *T, int n, double *partials, cudaStream_t st);
 cudaError_t launch_gather(const void *amps, int esize, int n, const unsigned long long *idx, int count, void *out,

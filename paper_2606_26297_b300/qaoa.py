@@ -40,7 +40,8 @@ class qaoa_qubo(ctypes.Structure):
 class qaoa_options(ctypes.Structure):
     _fields_ = [("adjoint_mode", ctypes.c_int32), ("profile", ctypes.c_int32),
                 ("memory_budget", ctypes.c_int64), ("max_fused_qubits", ctypes.c_int32),
-                ("state_fp64", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("state_fp64", ctypes.c_int32), ("table_build", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 class qaoa_adam_options(ctypes.Structure):
@@ -109,7 +110,8 @@ def qaoa_last_error() -> str:
 # ---- context ---------------------------------------------------------------------
 
 def qaoa_ctx_create(device: int = 0, stream: int | None = None, profile: bool = False,
-                    memory_budget: int = 0, max_fused_qubits: int = 0, state_fp64: bool = False):
+                    memory_budget: int = 0, max_fused_qubits: int = 0, state_fp64: bool = False,
+                    table_build: int = 0):
     """Create a context; `stream` is a raw cudaStream_t (e.g. torch's
     `torch.cuda.current_stream().cuda_stream`), None for the default stream."""
     opt = qaoa_options()
@@ -117,6 +119,7 @@ def qaoa_ctx_create(device: int = 0, stream: int | None = None, profile: bool = 
     opt.memory_budget = int(memory_budget)
     opt.max_fused_qubits = int(max_fused_qubits)
     opt.state_fp64 = int(state_fp64)
+    opt.table_build = int(table_build)
     out = _P()
     _check(_lib.qaoa_ctx_create(int(device), _P(stream or 0), ctypes.byref(opt), ctypes.byref(out)))
     return out

@@ -86,6 +86,44 @@ def test_cost_table_real_within_bound(q, ctx, maker, n):
     q.qaoa_cost_destroy(cost)
 
 
+@pytest.mark.parametrize("n,kind", [(14, "int"), (15, "big"), (18, "normal"), (22, "int"), (24, "uc"),
+                                    (26, "big"), (29, "normal")])
+def test_table_tensor_core_matches_simt(q, n, kind):
+    """The tcgen05 build (digit-split f16 products, exact FP32 accumulation)
+    against the integer SIMT build of the same fixed-point table: bit-exact
+    tables, argmin and minimum.  'big' has couplings up to 5e4, which need two
+    base-2^11 digits."""
+    if kind == "int":
+        Q = inst.upper_int_qubo(n, 900 + n)
+    elif kind == "big":
+        Q = inst.upper_int_qubo(n, 900 + n, lo=-50000, hi=50000)
+    elif kind == "normal":
+        Q = inst.normal_qubo(n, 900 + n)
+    else:
+        Q = inst.unit_commitment_qubo(n, 900 + n)
+    dt = "i32" if Q.dtype == "i32" else "f32"
+    c_tc = q.qaoa_ctx_create(0)
+    c_si = q.qaoa_ctx_create(0, table_build=1)
+    k_tc = q.qaoa_build_cost(c_tc, Q.H, Q.f, Q.c0, dt)
+    k_si = q.qaoa_build_cost(c_si, Q.H, Q.f, Q.c0, dt)
+    assert q.qaoa_cost_info(k_tc) == q.qaoa_cost_info(k_si)
+    T_tc = q.qaoa_cost_copy_to_host(c_tc, k_tc, n)
+    T_si = q.qaoa_cost_copy_to_host(c_si, k_si, n)
+    assert np.array_equal(T_tc, T_si)
+    if n <= 22:
+        info = q.qaoa_cost_info(k_tc)
+        F = oracle.cost_table(oracle.canonical_of(Q))
+        if Q.dtype == "i32":
+            assert np.array_equal(T_tc.astype(np.int64) + info["k_c"], F.astype(np.int64))
+        else:
+            s = info["shift_bits"]
+            got = (T_tc.astype(np.float64) + info["k_c"]) * 2.0 ** (-s)
+            assert np.max(np.abs(got - F)) <= _table_error_bound(n, s)
+    for k, c in ((k_tc, c_tc), (k_si, c_si)):
+        q.qaoa_cost_destroy(k)
+        q.qaoa_ctx_destroy(c)
+
+
 # ---- forward state -------------------------------------------------------------------
 
 FWD_CASES = [
