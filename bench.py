@@ -317,7 +317,8 @@ def run_workload(args):
                steps replayed from a CUDA graph;
       ragged   64 integer QUBOs with n in [10, 22], p=4, one request;
       uc32     unit-commitment QUBO n=32, p=6: `--iters` Adam steps on the
-               exact gradient (CUDA graph)."""
+               exact gradient (CUDA graph);
+      autotune fusion widths 10..5 timed on the dense workload (--n, depth 2)."""
     import torch
     from paper_2606_26297_b300 import build_lib
     build_lib.build()
@@ -410,6 +411,13 @@ def run_workload(args):
                     "amplitudes": int(sum(2 ** n for n in ns))})
         for c in costs:
             q.qaoa_cost_destroy(c)
+    elif args.workload == "autotune":
+        Q, g, b = inst.workload_dense30(args.n, args.p)
+        cost = q.qaoa_build_cost(ctx, Q.H, Q.f, Q.c0, "f32")
+        best, ms = q.qaoa_autotune(ctx, cost, 2)
+        res.update({"n": args.n, "p_timed": 2, "best_fusion_width": best,
+                    "ms_fwd_adjoint_by_width": {str(k): v for k, v in sorted(ms.items(), reverse=True)}})
+        q.qaoa_cost_destroy(cost)
     elif args.workload == "uc32":
         Q, g, b = inst.workload_uc32()
         cost = q.qaoa_build_cost(ctx, Q.H, Q.f, Q.c0, "f32")
@@ -435,7 +443,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--n", type=int, default=N_QUBITS, help="qubits (default: the n=30 workload)")
     ap.add_argument("--p", type=int, default=DEPTH, help="depth (default 8)")
-    ap.add_argument("--workload", default="", choices=["", "fd", "batch20", "ragged", "uc32"],
+    ap.add_argument("--workload", default="", choices=["", "fd", "batch20", "ragged", "uc32", "autotune"],
                     help="a secondary measurement instead of the headline step")
     ap.add_argument("--iters", type=int, default=200, help="Adam steps for --workload batch20/uc32")
     args = ap.parse_args()

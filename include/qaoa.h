@@ -87,7 +87,10 @@ typedef struct {
     int32_t state_fp64;     /* 1: complex128 states and arithmetic (n <= 12 only) */
     int32_t table_build;    /* objective table: 0 = tensor cores (tcgen05) for n >= 14 and the
                                SIMT Gray-code kernel below that; 1 = the SIMT kernel for every n */
-    int32_t reserved[5];    /* must be zero */
+    int32_t autotune;       /* 1: the first evaluation of each state size n >= 13 times every
+                               fusion width (qaoa_autotune) and the context keeps the fastest;
+                               ignored when max_fused_qubits is set */
+    int32_t reserved[4];    /* must be zero */
 } qaoa_options;
 
 typedef struct qaoa_ctx_s *qaoa_ctx;     /* device, stream, options, scratch, plan cache */
@@ -216,6 +219,19 @@ typedef struct {
 qaoa_status qaoa_optimize_adam(qaoa_ctx ctx, int nq, const qaoa_cost *costs, const int32_t *item_cost,
                                int B, int p, double *gamma, double *beta,
                                const qaoa_adam_options *opt, double *history, double *final_expect);
+
+/* ---- autotuning ---------------------------------------------------------- */
+
+/* Pick the fusion width (qubits per mixer pass) for states of cost's n by
+ * timing one forward + adjoint evaluation at depth p (linear-ramp angles) for
+ * each width in {10, 9, 8, 7, 6, 5} (<= n) with CUDA events on the context
+ * stream.  The fastest width is returned in *best_k and kept by the context
+ * for that n (used when options.autotune = 1 and max_fused_qubits = 0).
+ * ms_by_k (host, 8 doubles, may be NULL): ms_by_k[k - 3] = time for width k,
+ * NaN where not timed.  n <= 12 is rejected (the shared-memory kernel has no
+ * passes).  Sec. 4.1 compiles a circuit once and reuses it; this is the
+ * counterpart for the pass plan. */
+qaoa_status qaoa_autotune(qaoa_ctx ctx, qaoa_cost cost, int p, int32_t *best_k, double *ms_by_k);
 
 /* ---- DQAOA bookkeeping (host) and the GPU factorisation invariant ------- */
 

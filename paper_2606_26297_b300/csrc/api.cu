@@ -98,6 +98,7 @@ struct qaoa_ctx_s {
     double prof_bytes[5] = {0, 0, 0, 0, 0};
     int64_t launches_total = 0;  // every kernel launched by this context
     cudaStream_t aux_stream = nullptr;  // owned; runs captured optimisation loops
+    std::map<int, int> tuned_k;         // fusion width picked by the autotuner, by n
 };
 
 struct qaoa_cost_s {
@@ -188,7 +189,16 @@ qaoa_status check_angles(int p, const double *gamma, const double *beta) {
     return QAOA_OK;
 }
 
-int maxq_of(qaoa_ctx c) { return c->opt.max_fused_qubits ? c->opt.max_fused_qubits : 10; }
+// Fusion width (qubits per mixer pass) for states of n qubits: the explicit
+// option, else the autotuner's pick for n (options.autotune), else 10.
+int maxq_for(qaoa_ctx c, int n) {
+    if (c->opt.max_fused_qubits) return c->opt.max_fused_qubits;
+    if (c->opt.autotune) {
+        auto it = c->tuned_k.find(n);
+        if (it != c->tuned_k.end()) return it->second;
+    }
+    return 10;
+}
 
 // Decode top-K keys: x = 2^33-1 - low33, P = float bits of the high part.
 void decode_keys(const unsigned long long *keys, int k, uint64_t *idx, float *prob) {
@@ -357,7 +367,7 @@ qaoa_status run_single(qaoa_ctx c, const qaoa_cost_s *cost, int p, const double 
     r.ntables = 1;
     r.grad = grad;
     r.ktop = grad ? ktop : 0;
-    r.plan = make_plan(cost->n, p, grad, maxq_of(c));
+    r.plan = make_plan(cost->n, p, grad, maxq_for(c, cost->n));
     r.rows = plan_rows(r.plan);
     r.psi_ext = grad ? nullptr : psi_out;
     PlanBufs &b = c->single;
@@ -405,6 +415,66 @@ qaoa_status run_single(qaoa_ctx c, const qaoa_cost_s *cost, int p, const double 
 namespace {
 
 // ---- batches -------------------------------------------------------------------------
+
+// ---- autotuner -----------------------------------------------------------------------
+// Candidate fusion widths, largest first (fewer passes, more work per pass).
+constexpr int TUNE_K[] = {10, 9, 8, 7, 6, 5};
+
+// Time one forward + adjoint evaluation (depth p, linear-ramp angles) of
+// `cost` for every candidate width; the fastest is kept for cost->n.
+// ms_by_k[k - 3] receives the time of width k (NaN where not timed).
+qaoa_status tune_width(qaoa_ctx c, const qaoa_cost_s *cost, int p, int *best_k, double *ms_by_k) {
+    const int n = cost->n;
+    std::vector<double> g(p), b(p), dg(p), db(p);
+    for (int l = 0; l < p; ++l) {
+        const double t = (l + 0.5) / p;
+        g[l] = 0.4 * t;
+        b[l] = 0.4 * (1.0 - t);
+    }
+    for (int k = 0; k < 8; ++k)
+        if (ms_by_k) ms_by_k[k] = std::nan("");
+    const int saved = c->opt.max_fused_qubits, saved_prof = c->opt.profile;
+    c->opt.profile = 0;
+    double best = 1e300;
+    int bk = 10;
+    qaoa_status st = QAOA_OK;
+    for (int k : TUNE_K) {
+        if (k > n) continue;
+        c->opt.max_fused_qubits = k;
+        double E = 0.0;
+        st = run_single(c, cost, p, g.data(), b.data(), true, nullptr, &E, dg.data(), db.data(), 0, nullptr, nullptr);
+        if (st != QAOA_OK) break;
+        cudaEvent_t e0 = get_event(c), e1 = get_event(c);
+        cudaEventRecord(e0, c->stream);
+        st = run_single(c, cost, p, g.data(), b.data(), true, nullptr, &E, dg.data(), db.data(), 0, nullptr, nullptr);
+        cudaEventRecord(e1, c->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        c->ev_free.push_back(e0);
+        c->ev_free.push_back(e1);
+        if (st != QAOA_OK) break;
+        if (ms_by_k) ms_by_k[k - 3] = ms;
+        if (ms < best) {
+            best = ms;
+            bk = k;
+        }
+    }
+    c->opt.max_fused_qubits = saved;
+    c->opt.profile = saved_prof;
+    QAOA_TRY(st);
+    c->tuned_k[n] = bk;
+    if (best_k) *best_k = bk;
+    return QAOA_OK;
+}
+
+// With options.autotune, tune each n >= 13 on first use (depth 2 is enough:
+// every candidate's time is a sum of per-pass times).
+qaoa_status maybe_tune(qaoa_ctx c, const qaoa_cost_s *cost) {
+    if (!c->opt.autotune || c->opt.max_fused_qubits || cost->n <= SMALL_MAXN || c->tuned_k.count(cost->n))
+        return QAOA_OK;
+    return tune_width(c, cost, 2, nullptr, nullptr);
+}
 
 // Items of one n evaluated together on the pass path.
 struct BatchGroup {
@@ -464,7 +534,7 @@ qaoa_status build_groups(qaoa_ctx c, int nq, const qaoa_cost *costs, const int32
         g.r.ntables = (int)g.tabs.size();
         g.r.grad = grad;
         g.r.ktop = 0;
-        g.r.plan = make_plan(g.n, p, grad, maxq_of(c));
+        g.r.plan = make_plan(g.n, p, grad, maxq_for(c, g.n));
         g.r.rows = plan_rows(g.r.plan);
         auto &slot = c->groups[g.n];
         if (!slot) slot.reset(new PlanBufs());
@@ -605,7 +675,8 @@ qaoa_status qaoa_ctx_create(int device, void *cuda_stream, const qaoa_options *o
     if (o.max_fused_qubits != 0 && (o.max_fused_qubits < 3 || o.max_fused_qubits > 10))
         return fail(QAOA_ERR_INVALID_ARG, "max_fused_qubits must be 0 or in [3, 10]");
     if (o.table_build < 0 || o.table_build > 1) return fail(QAOA_ERR_INVALID_ARG, "table_build must be 0 or 1");
-    for (int k = 0; k < 5; ++k)
+    if (o.autotune < 0 || o.autotune > 1) return fail(QAOA_ERR_INVALID_ARG, "autotune must be 0 or 1");
+    for (int k = 0; k < 4; ++k)
         if (o.reserved[k]) return fail(QAOA_ERR_INVALID_ARG, "options.reserved[%d] must be zero", k);
     auto *c = new qaoa_ctx_s();
     c->device = device;
@@ -801,6 +872,7 @@ qaoa_status qaoa_forward(qaoa_ctx c, qaoa_cost cost, int p, const double *gamma,
         QAOA_TRY(run_small(c, c->small_items, items, fp64, false, n));
         CUDA_TRY(cudaStreamSynchronize(c->stream));
     } else {
+        QAOA_TRY(maybe_tune(c, cost));
         QAOA_TRY(run_single(c, cost, p, gamma, beta, false, static_cast<float2 *>(st->amps), nullptr, nullptr,
                             nullptr, 0, nullptr, nullptr));
     }
@@ -949,6 +1021,7 @@ qaoa_status qaoa_grad(qaoa_ctx c, qaoa_cost cost, int p, const double *gamma, co
         return QAOA_OK;
     }
     if (fp64) return fail(QAOA_ERR_INVALID_ARG, "complex128 states are limited to n <= 12");
+    QAOA_TRY(maybe_tune(c, cost));
     return run_single(c, cost, p, gamma, beta, true, nullptr, out_expect, dgamma, dbeta, k_top, top_idx, top_prob);
 }
 
@@ -963,6 +1036,8 @@ qaoa_status qaoa_grad_batch(qaoa_ctx c, int nq, const qaoa_cost *costs, const in
     QAOA_TRY(check_angles(p * B, gamma, beta));
     QAOA_TRY(set_device(c->device));
     const bool grad = dgamma != nullptr;
+    for (int k = 0; k < nq; ++k)
+        if (costs[k]) QAOA_TRY(maybe_tune(c, costs[k]));
     std::vector<BatchGroup> groups;
     SmallSet small;
     QAOA_TRY(build_groups(c, nq, costs, item_cost, B, p, grad, groups, small));
@@ -1049,6 +1124,8 @@ qaoa_status qaoa_optimize_adam(qaoa_ctx c, int nq, const qaoa_cost *costs, const
     const int iters = aopt->iterations;
     QAOA_TRY(set_device(c->device));
     if (!c->aux_stream) CUDA_TRY(cudaStreamCreateWithFlags(&c->aux_stream, cudaStreamNonBlocking));
+    for (int k = 0; k < nq; ++k)
+        if (costs[k]) QAOA_TRY(maybe_tune(c, costs[k]));
     std::vector<BatchGroup> groups;
     SmallSet small;
     QAOA_TRY(build_groups(c, nq, costs, item_cost, B, p, true, groups, small));
@@ -1186,6 +1263,19 @@ qaoa_status qaoa_optimize_adam(qaoa_ctx c, int nq, const qaoa_cost *costs, const
     CUDA_TRY(cudaEventRecord(done, c->aux_stream));
     CUDA_TRY(cudaStreamWaitEvent(user, done, 0));
     c->ev_free.push_back(done);
+    return QAOA_OK;
+}
+
+qaoa_status qaoa_autotune(qaoa_ctx c, qaoa_cost cost, int p, int32_t *best_k, double *ms_by_k) {
+    if (!c || !cost || !best_k) return fail(QAOA_ERR_INVALID_ARG, "null argument");
+    if (p < 1 || p > 64) return fail(QAOA_ERR_INVALID_ARG, "p=%d not in [1, 64]", p);
+    if (cost->n <= SMALL_MAXN)
+        return fail(QAOA_ERR_INVALID_ARG, "n=%d is evaluated by the shared-memory kernel; nothing to tune", cost->n);
+    if (c->opt.state_fp64) return fail(QAOA_ERR_INVALID_ARG, "the layer-pass path runs in complex64 only");
+    QAOA_TRY(set_device(c->device));
+    int k = 10;
+    QAOA_TRY(tune_width(c, cost, p, &k, ms_by_k));
+    *best_k = k;
     return QAOA_OK;
 }
 

@@ -41,7 +41,7 @@ class qaoa_options(ctypes.Structure):
     _fields_ = [("adjoint_mode", ctypes.c_int32), ("profile", ctypes.c_int32),
                 ("memory_budget", ctypes.c_int64), ("max_fused_qubits", ctypes.c_int32),
                 ("state_fp64", ctypes.c_int32), ("table_build", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("autotune", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class qaoa_adam_options(ctypes.Structure):
@@ -78,6 +78,7 @@ _SIGS = {
     "qaoa_grad_batch": ([_P, _I, ctypes.POINTER(_P), _PI32, _I, _I, _PD, _PD, _PD, _PD, _PD], _I),
     "qaoa_optimize_adam": ([_P, _I, ctypes.POINTER(_P), _PI32, _I, _I, _PD, _PD,
                             ctypes.POINTER(qaoa_adam_options), _PD, _PD], _I),
+    "qaoa_autotune": ([_P, _P, _I, _PI32, _PD], _I),
     "qaoa_partition": ([_I, _I, _PI32, _PI32, _PI32], _I),
     "qaoa_classify": ([_P, _PI32, _I, _PI64, _PI64, _PI64, _PI64], _I),
     "qaoa_check_factorisation": ([_P, _P, _PI32, _D, _PI64, _PD], _I),
@@ -111,7 +112,7 @@ def qaoa_last_error() -> str:
 
 def qaoa_ctx_create(device: int = 0, stream: int | None = None, profile: bool = False,
                     memory_budget: int = 0, max_fused_qubits: int = 0, state_fp64: bool = False,
-                    table_build: int = 0):
+                    table_build: int = 0, autotune: bool = False):
     """Create a context; `stream` is a raw cudaStream_t (e.g. torch's
     `torch.cuda.current_stream().cuda_stream`), None for the default stream."""
     opt = qaoa_options()
@@ -120,6 +121,7 @@ def qaoa_ctx_create(device: int = 0, stream: int | None = None, profile: bool = 
     opt.max_fused_qubits = int(max_fused_qubits)
     opt.state_fp64 = int(state_fp64)
     opt.table_build = int(table_build)
+    opt.autotune = int(autotune)
     out = _P()
     _check(_lib.qaoa_ctx_create(int(device), _P(stream or 0), ctypes.byref(opt), ctypes.byref(out)))
     return out
@@ -276,6 +278,14 @@ def qaoa_optimize_adam(ctx, costs, gamma, beta, iterations: int, item_cost=None,
     _check(_lib.qaoa_optimize_adam(ctx, len(costs), arr, None if ic is None else ic.ctypes.data_as(_PI32), B, p,
                                    _dptr(g), _dptr(b), ctypes.byref(opt), _dptr(hist), _dptr(E)))
     return g, b, hist, E
+
+
+def qaoa_autotune(ctx, cost, p: int = 2):
+    """Time every fusion width; returns (best width, {width: ms})."""
+    k = ctypes.c_int32()
+    ms = np.zeros(8)
+    _check(_lib.qaoa_autotune(ctx, cost, int(p), ctypes.byref(k), _dptr(ms)))
+    return k.value, {w: float(ms[w - 3]) for w in range(3, 11) if not np.isnan(ms[w - 3])}
 
 
 # ---- DQAOA ----------------------------------------------------------------------------------

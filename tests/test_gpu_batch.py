@@ -152,3 +152,34 @@ def test_adam_decreases_objective(q, ctx):
     assert E[0] < hist[0, 0] - 0.5
     assert hist[-1, 0] < hist[0, 0]
     q.qaoa_cost_destroy(cost)
+
+
+def test_autotune_fusion_width(q, ctx):
+    """The tuner times every width and keeps the fastest; a context with
+    autotune on evaluates exactly as one fixed to that width, and both match
+    the oracle."""
+    Q = inst.upper_int_qubo(18, 4600)
+    g, b = inst.ramp_angles(3, gamma_scale=0.2)
+    cost = _cost(q, ctx, Q)
+    best, ms = q.qaoa_autotune(ctx, cost, 2)
+    assert set(ms) == {10, 9, 8, 7, 6, 5} and best in ms
+    assert ms[best] == min(ms.values()) and all(v > 0 for v in ms.values())
+    q.qaoa_cost_destroy(cost)
+    ca = q.qaoa_ctx_create(0, autotune=True)
+    ck = q.qaoa_ctx_create(0, max_fused_qubits=best)
+    ka, kk = _cost(q, ca, Q), _cost(q, ck, Q)
+    ra = q.qaoa_grad(ca, ka, g, b)
+    rk = q.qaoa_grad(ck, kk, g, b)
+    F = oracle.cost_table(oracle.canonical_of(Q))
+    _check_item(F, g, b, *ra)
+    # the autotuned context may pick a different width on its own timing run;
+    # whichever it picked, the result equals a fixed-width run of that width
+    cw = q.qaoa_ctx_create(0, max_fused_qubits=q.qaoa_autotune(ca, ka, 2)[0])
+    kw = _cost(q, cw, Q)
+    rw = q.qaoa_grad(cw, kw, g, b)
+    ra2 = q.qaoa_grad(ca, ka, g, b)
+    assert ra2[0] == rw[0] and np.array_equal(ra2[1], rw[1]) and np.array_equal(ra2[2], rw[2])
+    _check_item(F, g, b, *rk)
+    for c, k in ((ca, ka), (ck, kk), (cw, kw)):
+        q.qaoa_cost_destroy(k)
+        q.qaoa_ctx_destroy(c)
