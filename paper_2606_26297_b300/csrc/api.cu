@@ -272,7 +272,8 @@ qaoa_status enqueue_plan(qaoa_ctx c, PlanBufs &b, const PlanRun &r, const int32_
         a.partials = b.partials.as<double>();
         a.topk_keys = b.topk_a.as<unsigned long long>();
         a.n = n;
-        a.lo = pl.lo;
+        a.loA = pl.loA;
+        a.loB = pl.loB;
         a.mask = pl.mask;
         a.nitems = r.nitems;
         a.ntables = r.ntables;
@@ -368,6 +369,7 @@ qaoa_status run_single(qaoa_ctx c, const qaoa_cost_s *cost, int p, const double 
     r.grad = grad;
     r.ktop = grad ? ktop : 0;
     r.plan = make_plan(cost->n, p, grad, maxq_for(c, cost->n));
+    if (r.plan.empty()) return fail(QAOA_ERR_INVALID_ARG, "no pass layout for n=%d", cost->n);
     r.rows = plan_rows(r.plan);
     r.psi_ext = grad ? nullptr : psi_out;
     PlanBufs &b = c->single;
@@ -535,6 +537,7 @@ qaoa_status build_groups(qaoa_ctx c, int nq, const qaoa_cost *costs, const int32
         g.r.grad = grad;
         g.r.ktop = 0;
         g.r.plan = make_plan(g.n, p, grad, maxq_for(c, g.n));
+        if (g.r.plan.empty()) return fail(QAOA_ERR_INVALID_ARG, "no pass layout for n=%d", g.n);
         g.r.rows = plan_rows(g.r.plan);
         auto &slot = c->groups[g.n];
         if (!slot) slot.reset(new PlanBufs());
@@ -1354,7 +1357,15 @@ qaoa_status qaoa_check_factorisation(qaoa_ctx c, qaoa_cost cost, const int32_t *
     std::vector<int> qs(M + 1, 0);
     for (int m = 0; m < M; ++m) qs[m + 1] = qs[m] + (int)vars[m].size();
     QAOA_TRY(set_device(c->device));
-    const size_t bytes = n * 4 * 2 + (M + 1) * 4 + L.size() * 8 + Loff.size() * 8 + V.size() * 8 + Voff.size() * 8 + 64 * 8;
+    // contiguous: QPU indices start at 0 and never decrease, stepping by 0 or 1
+    bool contiguous = qpu_of[0] == 0;
+    for (int i = 1; i < n; ++i)
+        if (qpu_of[i] != qpu_of[i - 1] && qpu_of[i] != qpu_of[i - 1] + 1) contiguous = false;
+    const int c0 = (int)vars[0].size();
+    if (c0 > 16 || n - c0 > 31 || n - c0 < 1) contiguous = false;
+    const size_t hhi_bytes = contiguous ? ((size_t)8 << (n - c0)) : 0;
+    const size_t bytes = n * 4 * 2 + (M + 1) * 4 + L.size() * 8 + Loff.size() * 8 + V.size() * 8 + Voff.size() * 8 +
+                         64 * 8 + hhi_bytes;
     QAOA_TRY(c->misc.ensure(bytes + 1024, &c->held, c->opt.memory_budget));
     char *d = c->misc.as<char>();
     size_t o = 0;
@@ -1383,17 +1394,17 @@ qaoa_status qaoa_check_factorisation(qaoa_ctx c, qaoa_cost cost, const int32_t *
     a.c_off = fp.c0_q - fp.k_c;
     a.k_c = fp.k_c;
     a.phi = phase_multiplier(gamma_probe, fp.s);
-    // contiguous: QPU indices start at 0 and never decrease, stepping by 0 or 1
-    a.contiguous = qpu_of[0] == 0 ? 1 : 0;
-    for (int i = 1; i < n; ++i)
-        if (qpu_of[i] != qpu_of[i - 1] && qpu_of[i] != qpu_of[i - 1] + 1) a.contiguous = 0;
-    a.c0 = (int)vars[0].size();
-    if (a.c0 > 12 || n - a.c0 > 31) a.contiguous = 0;
+    a.contiguous = contiguous ? 1 : 0;
+    a.c0 = c0;
+    if (contiguous) {
+        a.hhi = reinterpret_cast<long long *>(d + ((o + 255) & ~size_t(255)));
+        o = ((o + 255) & ~size_t(255)) + hhi_bytes;
+    }
     CUDA_TRY(cudaGetLastError());
     {
         ProfScope ps(c, 4, std::ldexp(4.0, n));
         CUDA_TRY(launch_fact_check(a, c->stream));
-        c->launches_total += 1;
+        c->launches_total += contiguous ? 2 : 1;
     }
     unsigned long long hres[2];
     CUDA_TRY(cudaMemcpyAsync(hres, res, 16, cudaMemcpyDeviceToHost, c->stream));

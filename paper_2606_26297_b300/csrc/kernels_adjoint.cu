@@ -93,10 +93,11 @@ __device__ __forceinline__ void read_stage_pq(float2 (&P)[32], float2 (&Q)[32], 
 
 template <int T, int A>
 __device__ __forceinline__ void store_pq(const float2 (&P)[32], const float2 (&Q)[32], float4 *__restrict__ p,
-                                         uint32_t l, uint32_t w, int lo) {
-    float4 *q = p + goff<T>(local_idx<T, A>(l, 0u, w), lo);
+                                         uint32_t l, uint32_t w, int loA, int loB) {
+    float4 *q = p + goff<T>(local_idx<T, A>(l, 0u, w), loA, loB);
 #pragma unroll
-    for (int m = 0; m < 32; ++m) __stcs(q + roff<T, A>(m, lo), make_float4(P[m].x, P[m].y, Q[m].x, Q[m].y));
+    for (int m = 0; m < 32; ++m)
+        __stcs(q + roff<T, A>(m, loA, loB), make_float4(P[m].x, P[m].y, Q[m].x, Q[m].y));
 }
 
 // unit u of a launch: item u >> nbits, block u & (2^nbits - 1)
@@ -104,6 +105,18 @@ struct Unit {
     uint32_t item, b;
 };
 __device__ __forceinline__ Unit unit_of(uint32_t u, int nbits) { return {u >> nbits, u & ((1u << nbits) - 1u)}; }
+
+// Tensor-map coordinates of high-group block b of array `arr` (item or table
+// index): dims (bits 0..2) x (bits 3..loA-1) x (window A) x (bits
+// loA+5..loB-1) x (window B and above, arrays stacked); the box covers bits
+// 0..2 and both windows.
+__device__ __forceinline__ void tile_coords(uint32_t b, uint32_t arr, const PassArgs &a, int *c1, int *c3,
+                                            int *c4) {
+    const int n1 = a.loA - 3, n2 = a.loB - a.loA - 5;
+    *c1 = (int)(b & ((1u << n1) - 1u));
+    *c3 = (int)((b >> n1) & ((1u << n2) - 1u));
+    *c4 = (int)(((b >> (n1 + n2)) << 5) + (arr << (a.n - a.loB)));
+}
 
 // Issue the copy of a unit's amplitudes: the psi block (64 KB) or the
 // interleaved (psi, lambda) block (128 KB).  High-group tensor maps stack the
@@ -120,9 +133,9 @@ __device__ __forceinline__ void issue_amps(uint32_t u, const PassArgs &a, const 
         const void *src = PL ? (const void *)(a.pl + off) : (const void *)(a.psi + off);
         bulk_load(stage, src, bytes, mbar);
     } else {
-        const int nlow = a.lo - 3;
-        const int c4 = (int)((un.b >> nlow) + (un.item << (a.n - a.lo - 10)));
-        tma_load_5d(stage, map, (int)(un.b & ((1u << nlow) - 1u)), c4, mbar);
+        int c1, c3, c4;
+        tile_coords(un.b, un.item, a, &c1, &c3, &c4);
+        tma_load_5d(stage, map, c1, c3, c4, mbar);
     }
 }
 
@@ -136,9 +149,9 @@ __device__ __forceinline__ void issue_table(uint32_t u, const PassArgs &a, const
     if (T == 0) {
         bulk_load(cstage, a.C + ((size_t)tab << a.n) + ((size_t)un.b << 13), 32768u, mbar);
     } else {
-        const int nlow = a.lo - 3;
-        const int c4 = (int)((un.b >> nlow) + (tab << (a.n - a.lo - 10)));
-        tma_load_5d(cstage, mcost, (int)(un.b & ((1u << nlow) - 1u)), c4, mbar);
+        int c1, c3, c4;
+        tile_coords(un.b, tab, a, &c1, &c3, &c4);
+        tma_load_5d(cstage, mcost, c1, c3, c4, mbar);
     }
 }
 
@@ -175,7 +188,7 @@ __global__ void __launch_bounds__(PASS_THREADS, 1)
         const Unit un = unit_of(u, nbits);
         const PassScal sc = a.scal[un.item];
         const uint32_t fm = sc.pre_flip ? a.mask : 0u;
-        const size_t base = block_base<T>(un.b, a.lo);
+        const size_t base = block_base<T>(un.b, a.loA, a.loB);
         float2 v[32];
         if (!stage_ready(&mbar, parity, status)) return;
         parity ^= 1u;
@@ -212,8 +225,8 @@ __global__ void __launch_bounds__(PASS_THREADS, 1)
             Q[m] = make_float2(v[m].y, v[m].y * lf);
         }
         if (a.ktop > 0) {
-            const size_t xthread = base + goff<T>(local_idx<T, 1>(l, 0u, w), a.lo);
-            block_topk<T, 1>(v, xthread, a.lo, a.ktop, a.topk_keys + (size_t)un.b * a.ktop, smk);
+            const size_t xthread = base + goff<T>(local_idx<T, 1>(l, 0u, w), a.loA, a.loB);
+            block_topk<T, 1>(v, xthread, a.loA, a.loB, a.ktop, a.topk_keys + (size_t)un.b * a.ktop, smk);
         }
         const float x1 = xterm_pq<T, 1>(P, Q, a.mask);
         round_mix_pq<T, 1>(P, Q, -sc.pre_t, a.mask);
@@ -223,7 +236,7 @@ __global__ void __launch_bounds__(PASS_THREADS, 1)
         round_mix_pq<T, 0>(P, Q, -sc.pre_t, a.mask);
 #pragma unroll
         for (int m = 0; m < 32; ++m) cmul_pq(P[m], Q[m], sc.kend2);
-        store_pq<T, 0>(P, Q, a.pl + ((size_t)un.item << a.n) + base, l, w, a.lo);
+        store_pq<T, 0>(P, Q, a.pl + ((size_t)un.item << a.n) + base, l, w, a.loA, a.loB);
         double vals[NSLOT] = {(double)e0, (double)e1, (double)x1, (double)x0, 0.0, 0.0, 0.0, 0.0};
         block_sum_write(vals, red, a.partials, u);
         __syncthreads();
@@ -262,7 +275,7 @@ __global__ void __launch_bounds__(PASS_THREADS, 1)
         const Unit un = unit_of(u, nbits);
         const PassScal sc = a.scal[un.item];
         const uint32_t fa = sc.pre_flip ? a.mask : 0u, fb = sc.post_flip ? a.mask : 0u;
-        const size_t base = block_base<T>(un.b, a.lo);
+        const size_t base = block_base<T>(un.b, a.loA, a.loB);
         float2 P[32], Q[32];
         float acc[NSLOT] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if (!stage_ready(&mbar, parity, status)) return;
@@ -316,14 +329,14 @@ __global__ void __launch_bounds__(PASS_THREADS, 1)
 #pragma unroll
                     for (int m = 0; m < 32; ++m) cmul_pq(P[m], Q[m], sc.kend);
                 }
-                store_pq<T, 0>(P, Q, dst, l, w, a.lo);
+                store_pq<T, 0>(P, Q, dst, l, w, a.loA, a.loB);
             }
         } else if (a.store) {
             if (!a.has_cost) {
 #pragma unroll
                 for (int m = 0; m < 32; ++m) cmul_pq(P[m], Q[m], sc.kend);
             }
-            store_pq<T, 1>(P, Q, dst, l, w, a.lo);
+            store_pq<T, 1>(P, Q, dst, l, w, a.loA, a.loB);
         }
         double vals[NSLOT];
 #pragma unroll
@@ -349,19 +362,22 @@ static cudaError_t get_encoder() {
     return cudaSuccess;
 }
 
-// 5-D view of high-group blocks: (carried bits 0..2) x (bits 3..lo-1) x
-// (group bits 0..4) x (group bits 5..9) x (bits lo+10..n-1, then `count`
-// consecutive arrays of 2^n elements).  esize: 16 (interleaved psi/lambda,
-// described as pairs of 8-byte elements in dim 0), 8 (complex64) or 4 (int32).
-static cudaError_t make_block_map(CUtensorMap *map, const void *base, int n, int lo, int esize, int count) {
+// 5-D view of high-group blocks: (bits 0..2) x (bits 3..loA-1) x (window A,
+// bits loA..loA+4) x (bits loA+5..loB-1) x (bits loB..n-1, then `count`
+// consecutive arrays of 2^n elements); the box is 8 x 1 x 32 x 1 x 32, i.e.
+// bits 0..2 and both windows.  esize: 16 (interleaved psi/lambda, described as
+// pairs of 8-byte elements in dim 0), 8 (complex64) or 4 (int32).
+static cudaError_t make_block_map(CUtensorMap *map, const void *base, int n, int loA, int loB, int esize,
+                                  int count) {
     std::memset(map, 0, sizeof(*map));
     cudaError_t e = get_encoder();
     if (e) return e;
     const cuuint64_t es = (cuuint64_t)esize;
     const cuuint64_t d0 = esize == 16 ? 16ull : 8ull;
-    cuuint64_t dims[5] = {d0, 1ull << (lo - 3), 32ull, 32ull, (1ull << (n - lo - 10)) * (cuuint64_t)count};
-    cuuint64_t strides[4] = {8ull * es, es << lo, es << (lo + 5), es << (lo + 10)};
-    cuuint32_t box[5] = {(cuuint32_t)d0, 1u, 32u, 32u, 1u};
+    cuuint64_t dims[5] = {d0, 1ull << (loA - 3), 32ull, 1ull << (loB - loA - 5),
+                          (1ull << (n - loB)) * (cuuint64_t)count};
+    cuuint64_t strides[4] = {8ull * es, es << loA, es << (loA + 5), es << loB};
+    cuuint32_t box[5] = {(cuuint32_t)d0, 1u, 32u, 1u, 32u};
     cuuint32_t estr[5] = {1u, 1u, 1u, 1u, 1u};
     CUresult r = g_encode(map, esize == 4 ? CU_TENSOR_MAP_DATA_TYPE_INT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 5,
                           const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -383,8 +399,8 @@ cudaError_t launch_final_pass(int type, const PassArgs &a, int grid, unsigned in
     std::memset(&mc, 0, sizeof mc);
     cudaError_t e;
     if (type == 1) {
-        if ((e = make_block_map(&m, a.psi, a.n, a.lo, 8, a.nitems))) return e;
-        if ((e = make_block_map(&mc, a.C, a.n, a.lo, 4, a.ntables))) return e;
+        if ((e = make_block_map(&m, a.psi, a.n, a.loA, a.loB, 8, a.nitems))) return e;
+        if ((e = make_block_map(&mc, a.C, a.n, a.loA, a.loB, 4, a.ntables))) return e;
     }
     if (grid > nunits) grid = nunits;
     if (type == 0) {
@@ -405,8 +421,8 @@ cudaError_t launch_rev_pass(int type, const PassArgs &a, int grid, unsigned int 
     std::memset(&mc, 0, sizeof mc);
     cudaError_t e;
     if (type == 1) {
-        if ((e = make_block_map(&m, a.pl, a.n, a.lo, 16, a.nitems))) return e;
-        if (a.has_cost && (e = make_block_map(&mc, a.C, a.n, a.lo, 4, a.ntables))) return e;
+        if ((e = make_block_map(&m, a.pl, a.n, a.loA, a.loB, 16, a.nitems))) return e;
+        if (a.has_cost && (e = make_block_map(&mc, a.C, a.n, a.loA, a.loB, 4, a.ntables))) return e;
     }
     if (grid > nunits) grid = nunits;
     if (type == 0) {

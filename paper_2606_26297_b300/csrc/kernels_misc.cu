@@ -589,61 +589,74 @@ __global__ void fact_check_kernel(FactArgs a) {
     }
 }
 
-// Contiguous allocation (QPU m owns bits [s_m, s_m + c_m)): a CTA fixes the
-// fields of QPUs 1..M-1 (its index), its threads walk QPU 0's field.  The
-// CTA-uniform part of the split (their local tables and their mutual cross
-// terms) is formed once; per x only QPU 0's table and its cross sum remain.
-__global__ void fact_check_contig_kernel(FactArgs a) {
+// Contiguous allocation (QPU m owns bits [s_m, s_m + c_m)).  x = u0 + 2^c0 hi
+// with u0 the field of QPU 0.  The part of the split that does not depend on
+// u0 (the local tables of QPUs 1..M-1 and their mutual cross terms) is formed
+// once per hi by fact_hi_kernel; a CTA of the check fixes hi, forms
+// W[q] = sum_{m >= 1} V_{0,m}[u_m][q] (QPU 0 variable q's cross coupling to
+// the other QPUs' set variables) and two subset-sum tables of W over the low
+// and high 8 bits of u0, so that the cross term of x is two table reads.
+__global__ void fact_hi_kernel(FactArgs a, long long *Hhi) {
+    const unsigned long long hi = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int c0 = a.c0;
+    if (hi >= (1ull << (a.n - c0))) return;
+    long long h = a.c_off;
+    for (int m = 1; m < a.M; ++m) {
+        const int sm = a.q_start[m], cm = a.q_start[m + 1] - sm;
+        const unsigned um = (unsigned)((hi >> (sm - c0)) & ((1u << cm) - 1u));
+        h += a.Ltab[a.L_off[m] + um];
+        for (int m2 = m + 1; m2 < a.M; ++m2) {
+            const int s2 = a.q_start[m2], c2 = a.q_start[m2 + 1] - s2;
+            const unsigned u2 = (unsigned)((hi >> (s2 - c0)) & ((1u << c2) - 1u));
+            const long long *Vrow = a.V + a.V_off[m * 16 + m2] + (size_t)u2 * cm;
+            for (int q = 0; q < cm; ++q)
+                if ((um >> q) & 1u) h += Vrow[q];
+        }
+    }
+    Hhi[hi] = h;
+}
+
+__global__ void fact_check_contig_kernel(FactArgs a, const long long *__restrict__ Hhi) {
     __shared__ long long wrow[16];
-    __shared__ long long hi_part;
+    __shared__ long long tlo[256], thi[256];
     __shared__ unsigned long long cnt_sh;
     __shared__ unsigned int err_sh;
-    __shared__ int qs[17];
-    if (threadIdx.x <= (unsigned)a.M) qs[threadIdx.x] = a.q_start[threadIdx.x];
+    const int c0 = a.c0;
+    const unsigned long long hi = blockIdx.x;  // bits c0..n-1 of x
     if (threadIdx.x == 0) {
         cnt_sh = 0;
         err_sh = 0;
     }
+    if (threadIdx.x < (unsigned)c0) {
+        const int q = threadIdx.x;
+        long long w = 0;
+        for (int m2 = 1; m2 < a.M; ++m2) {
+            const int s2 = a.q_start[m2], c2 = a.q_start[m2 + 1] - s2;
+            const unsigned u2 = (unsigned)((hi >> (s2 - c0)) & ((1u << c2) - 1u));
+            w += a.V[a.V_off[m2] + (size_t)u2 * c0 + q];
+        }
+        wrow[q] = w;
+    }
+    const long long H = Hhi[hi];
     __syncthreads();
-    const int c0 = qs[1];
-    const unsigned long long hi = blockIdx.x;  // bits c0..n-1 of x
-    if (threadIdx.x < 32) {
-        // W[a] = sum over QPUs m' >= 1 of V_{0,m'}[u_m'][a]
-        for (int q = threadIdx.x; q < c0; q += 32) {
-            long long w = 0;
-            for (int m2 = 1; m2 < a.M; ++m2) {
-                const unsigned u2 = (unsigned)((hi >> (qs[m2] - c0)) & ((1u << (qs[m2 + 1] - qs[m2])) - 1u));
-                w += a.V[a.V_off[m2] + (size_t)u2 * c0 + q];
-            }
-            wrow[q] = w;
-        }
-        if (threadIdx.x == 0) {
-            long long h = a.c_off;
-            for (int m = 1; m < a.M; ++m) {
-                const int cm = qs[m + 1] - qs[m];
-                const unsigned um = (unsigned)((hi >> (qs[m] - c0)) & ((1u << cm) - 1u));
-                h += a.Ltab[a.L_off[m] + um];
-                for (int m2 = m + 1; m2 < a.M; ++m2) {
-                    const unsigned u2 = (unsigned)((hi >> (qs[m2] - c0)) & ((1u << (qs[m2 + 1] - qs[m2])) - 1u));
-                    const long long *Vrow = a.V + a.V_off[m * 16 + m2] + (size_t)u2 * cm;
-                    for (int q = 0; q < cm; ++q)
-                        if ((um >> q) & 1u) h += Vrow[q];
-                }
-            }
-            hi_part = h;
-        }
+    const int klo = c0 < 8 ? c0 : 8, khi = c0 - klo;
+    for (int k = threadIdx.x; k < 256; k += blockDim.x) {
+        long long sl = 0, sh = 0;
+        for (int q = 0; q < klo; ++q)
+            if ((k >> q) & 1) sl += wrow[q];
+        for (int q = 0; q < khi; ++q)
+            if ((k >> q) & 1) sh += wrow[klo + q];
+        tlo[k] = sl;
+        thi[k] = sh;
     }
     __syncthreads();
-    const long long H = hi_part;
     unsigned long long bad = 0;
     float maxerr = 0.f;
+    const int32_t *Tr = a.T + (hi << c0);
     for (unsigned u0 = threadIdx.x; u0 < (1u << c0); u0 += blockDim.x) {
-        const unsigned long long x = (hi << c0) | u0;
-        long long cross = 0;
-        for (int q = 0; q < c0; ++q)
-            if ((u0 >> q) & 1u) cross += wrow[q];
+        const long long cross = tlo[u0 & ((1u << klo) - 1u)] + thi[u0 >> klo];
         const long long loc = H + a.Ltab[u0];
-        const int32_t tx = a.T[x];
+        const int32_t tx = Tr[u0];
         if ((long long)tx != loc + cross) ++bad;
         const float2 pf = phase_ll((long long)tx + a.k_c, a.phi, 0ull);
         const float2 pl = phase_ll(loc + a.k_c, a.phi, 0ull);
@@ -651,19 +664,28 @@ __global__ void fact_check_contig_kernel(FactArgs a) {
         const float2 pp = cmul(pl, pc);
         maxerr = fmaxf(maxerr, fmaxf(fabsf(pf.x - pp.x), fabsf(pf.y - pp.y)));
     }
-    atomicAdd(&cnt_sh, bad);
-    atomicMax(&err_sh, __float_as_uint(maxerr));
+    // warp then CTA reduction of the counts and the error bound
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        bad += __shfl_xor_sync(0xffffffffu, bad, o);
+        maxerr = fmaxf(maxerr, __shfl_xor_sync(0xffffffffu, maxerr, o));
+    }
+    if ((threadIdx.x & 31u) == 0) {
+        if (bad) atomicAdd(&cnt_sh, bad);
+        atomicMax(&err_sh, __float_as_uint(maxerr));
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        atomicAdd(a.mismatches, cnt_sh);
+        if (cnt_sh) atomicAdd(a.mismatches, cnt_sh);
         atomicMax(a.max_err_bits, err_sh);
     }
 }
 
 cudaError_t launch_fact_check(const FactArgs &a, cudaStream_t st) {
     if (a.contiguous) {
-        const int c0 = a.c0;
-        fact_check_contig_kernel<<<(unsigned)(1ull << (a.n - c0)), 256, 0, st>>>(a);
+        const unsigned long long nhi = 1ull << (a.n - a.c0);
+        fact_hi_kernel<<<(unsigned)((nhi + 255) / 256), 256, 0, st>>>(a, a.hhi);
+        fact_check_contig_kernel<<<(unsigned)nhi, 256, 0, st>>>(a, a.hhi);
     } else {
         fact_check_kernel<<<148 * 8, 256, 0, st>>>(a);
     }

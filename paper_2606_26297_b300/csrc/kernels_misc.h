@@ -87,6 +87,7 @@ struct FactArgs {
     unsigned int *max_err_bits;
     int contiguous;           // QPU m owns the contiguous bit range [q_start[m], q_start[m+1])
     int c0;                   // size of QPU 0 (contiguous case)
+    long long *hhi;           // [2^(n - c0)] scratch of the contiguous case
 };
 cudaError_t launch_fact_check(const FactArgs &a, cudaStream_t st);
 

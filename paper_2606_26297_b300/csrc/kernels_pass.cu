@@ -20,7 +20,7 @@ __global__ void __launch_bounds__(PASS_THREADS, 2) fwd_pass_kernel(const PassArg
     const int nbits = a.n - BLOCK_BITS;
     const uint32_t item = blockIdx.x >> nbits, b = blockIdx.x & ((1u << nbits) - 1u);
     const PassScal sc = a.scal[item];
-    const size_t base = block_base<T>(b, a.lo);
+    const size_t base = block_base<T>(b, a.loA, a.loB);
     float2 *pb = a.psi + ((size_t)item << a.n) + base;
     const int32_t *cb = a.C + ((size_t)(a.item_table ? a.item_table[item] : 0) << a.n) + base;
     float2 v[32];
@@ -28,9 +28,9 @@ __global__ void __launch_bounds__(PASS_THREADS, 2) fwd_pass_kernel(const PassArg
 #pragma unroll
         for (int m = 0; m < 32; ++m) v[m] = make_float2(a.amp0, 0.f);
     } else if (a.has_pre) {
-        load_arr<T, 0>(v, pb, l, w, a.lo);
+        load_arr<T, 0>(v, pb, l, w, a.loA, a.loB);
     } else {
-        load_arr<T, 1>(v, pb, l, w, a.lo);
+        load_arr<T, 1>(v, pb, l, w, a.loA, a.loB);
     }
     if (a.has_pre) {
         round_mix<T, 0>(v, sc.pre_t, a.mask);
@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(PASS_THREADS, 2) fwd_pass_kernel(const PassArg
     // arrangement Y
     if (a.has_cost) {
         int32_t c[32];
-        load_cost<T, 1>(c, cb, l, w, a.lo);
+        load_cost<T, 1>(c, cb, l, w, a.loA, a.loB);
 #pragma unroll
         for (int m = 0; m < 32; ++m) v[m] = cmul(v[m], cost_phase(c[m], sc.phi, sc.off, sc.kmag, a.precise_phase));
     }
@@ -52,13 +52,13 @@ __global__ void __launch_bounds__(PASS_THREADS, 2) fwd_pass_kernel(const PassArg
 #pragma unroll
             for (int m = 0; m < 32; ++m) v[m] = cmul(v[m], sc.kend);
         }
-        store_arr<T, 0>(v, pb, l, w, a.lo);
+        store_arr<T, 0>(v, pb, l, w, a.loA, a.loB);
     } else {
         if (!a.has_cost) {
 #pragma unroll
             for (int m = 0; m < 32; ++m) v[m] = cmul(v[m], sc.kend);
         }
-        store_arr<T, 1>(v, pb, l, w, a.lo);
+        store_arr<T, 1>(v, pb, l, w, a.loA, a.loB);
     }
 }
 

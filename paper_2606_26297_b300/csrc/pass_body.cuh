@@ -1,6 +1,6 @@
 // Register/shared-memory building blocks of a layer pass, shared by the
 // direct-load kernels (kernels_pass.cu) and the TMA-pipelined persistent
-// kernels (kernels_tma.cu).
+// kernels (kernels_adjoint.cu).
 #pragma once
 
 #include "pass_common.cuh"
@@ -8,50 +8,50 @@
 namespace qaoa {
 
 template <int T, int A>
-__device__ __forceinline__ size_t roff(int m, int lo) {
-    return goff<T>(local_idx<T, A>(0u, (uint32_t)m, 0u), lo);
+__device__ __forceinline__ size_t roff(int m, int loA, int loB) {
+    return goff<T>(local_idx<T, A>(0u, (uint32_t)m, 0u), loA, loB);
 }
 
 template <int T, int A>
 __device__ __forceinline__ void load_arr(float2 (&v)[32], const float2 *__restrict__ p, uint32_t l,
-                                         uint32_t w, int lo) {
-    const float2 *q = p + goff<T>(local_idx<T, A>(l, 0u, w), lo);
+                                         uint32_t w, int loA, int loB) {
+    const float2 *q = p + goff<T>(local_idx<T, A>(l, 0u, w), loA, loB);
     if (T == 0 && A == 1) {  // runs of 8 contiguous amplitudes per thread
 #pragma unroll
         for (int m = 0; m < 32; m += 2) {
-            const float4 t = *reinterpret_cast<const float4 *>(q + roff<T, A>(m, lo));
+            const float4 t = *reinterpret_cast<const float4 *>(q + roff<T, A>(m, loA, loB));
             v[m] = make_float2(t.x, t.y);
             v[m + 1] = make_float2(t.z, t.w);
         }
     } else {
 #pragma unroll
-        for (int m = 0; m < 32; ++m) v[m] = q[roff<T, A>(m, lo)];
+        for (int m = 0; m < 32; ++m) v[m] = q[roff<T, A>(m, loA, loB)];
     }
 }
 
 template <int T, int A>
 __device__ __forceinline__ void store_arr(const float2 (&v)[32], float2 *__restrict__ p, uint32_t l,
-                                          uint32_t w, int lo) {
-    float2 *q = p + goff<T>(local_idx<T, A>(l, 0u, w), lo);
+                                          uint32_t w, int loA, int loB) {
+    float2 *q = p + goff<T>(local_idx<T, A>(l, 0u, w), loA, loB);
     if (T == 0 && A == 1) {
 #pragma unroll
         for (int m = 0; m < 32; m += 2)
-            __stcs(reinterpret_cast<float4 *>(q + roff<T, A>(m, lo)),
+            __stcs(reinterpret_cast<float4 *>(q + roff<T, A>(m, loA, loB)),
                    make_float4(v[m].x, v[m].y, v[m + 1].x, v[m + 1].y));
     } else {
 #pragma unroll
-        for (int m = 0; m < 32; ++m) __stcs(q + roff<T, A>(m, lo), v[m]);
+        for (int m = 0; m < 32; ++m) __stcs(q + roff<T, A>(m, loA, loB), v[m]);
     }
 }
 
 template <int T, int A>
 __device__ __forceinline__ void load_cost(int32_t (&c)[32], const int32_t *__restrict__ p, uint32_t l,
-                                          uint32_t w, int lo) {
-    const int32_t *q = p + goff<T>(local_idx<T, A>(l, 0u, w), lo);
+                                          uint32_t w, int loA, int loB) {
+    const int32_t *q = p + goff<T>(local_idx<T, A>(l, 0u, w), loA, loB);
     if (T == 0 && A == 1) {
 #pragma unroll
         for (int m = 0; m < 32; m += 4) {
-            const int4 t = __ldg(reinterpret_cast<const int4 *>(q + roff<T, A>(m, lo)));
+            const int4 t = __ldg(reinterpret_cast<const int4 *>(q + roff<T, A>(m, loA, loB)));
             c[m] = t.x;
             c[m + 1] = t.y;
             c[m + 2] = t.z;
@@ -59,7 +59,7 @@ __device__ __forceinline__ void load_cost(int32_t (&c)[32], const int32_t *__res
         }
     } else {
 #pragma unroll
-        for (int m = 0; m < 32; ++m) c[m] = __ldg(q + roff<T, A>(m, lo));
+        for (int m = 0; m < 32; ++m) c[m] = __ldg(q + roff<T, A>(m, loA, loB));
     }
 }
 
@@ -103,27 +103,39 @@ __device__ __forceinline__ void transpose2(float2 (&v)[32], float2 (&u)[32], flo
 // key = (bits(P) << 33) | (2^33 - 1 - x); keys are unique since x is.
 // Writes K keys to out (global), using smk (shared, >= 8*16 keys).
 template <int T, int A>
-__device__ __forceinline__ void block_topk(const float2 (&v)[32], size_t xthread, int lo, int K,
+__device__ __forceinline__ void block_topk(const float2 (&v)[32], size_t xthread, int loA, int loB, int K,
                                            unsigned long long *out, unsigned long long *smk) {
     const uint32_t l = threadIdx.x & 31, w = threadIdx.x >> 5;
     uint32_t taken = 0;
-    unsigned long long bk = 0;
-    int bm = -1;
+    // this thread's best and second-best remaining keys: a thread rescans its
+    // 32 amplitudes only when it wins a second time after its last scan
+    unsigned long long bk = 0, sk = 0;
+    int bm = -1, sm = -1;
+    // x grows with m inside a thread, so among equal probabilities the first
+    // m seen has the smaller index; P >= 0 orders like its bit pattern
+    auto key_of = [&](uint32_t pbits, int m) {
+        const unsigned long long x = xthread + goff<T>(local_idx<T, A>(0u, (uint32_t)m, 0u), loA, loB);
+        return ((unsigned long long)pbits << 33) | (0x1FFFFFFFFull - x);
+    };
     auto scan = [&]() {
-        bk = 0;
-        bm = -1;
+        uint32_t bp = 0, sp = 0;
+        bm = sm = -1;
 #pragma unroll
         for (int m = 0; m < 32; ++m) {
             if ((taken >> m) & 1u) continue;
-            const float P = fmaf(v[m].x, v[m].x, v[m].y * v[m].y);
-            const unsigned long long x = xthread + roff<T, A>(m, lo);
-            const unsigned long long key =
-                ((unsigned long long)__float_as_uint(P) << 33) | (0x1FFFFFFFFull - x);
-            if (key > bk) {
-                bk = key;
+            const uint32_t pb = __float_as_uint(fmaf(v[m].x, v[m].x, v[m].y * v[m].y));
+            if (bm < 0 || pb > bp) {
+                sp = bp;
+                sm = bm;
+                bp = pb;
                 bm = m;
+            } else if (sm < 0 || pb > sp) {
+                sp = pb;
+                sm = m;
             }
         }
+        bk = bm >= 0 ? key_of(bp, bm) : 0ull;
+        sk = sm >= 0 ? key_of(sp, sm) : 0ull;
     };
     scan();
     for (int r = 0; r < K; ++r) {
@@ -136,7 +148,14 @@ __device__ __forceinline__ void block_topk(const float2 (&v)[32], size_t xthread
         if (l == 0) smk[w * 16 + r] = wb;
         if (bk == wb && bm >= 0) {
             taken |= 1u << bm;
-            scan();
+            if (sm >= 0) {
+                bk = sk;
+                bm = sm;
+                sk = 0;
+                sm = -1;
+            } else {
+                scan();
+            }
         }
     }
     __syncthreads();

@@ -52,17 +52,22 @@ __device__ __forceinline__ constexpr uint32_t swz(uint32_t e) {
     return T == 0 ? (e ^ ((e >> 4) & 7u) ^ (((e >> 8) & 1u) << 3)) : (e ^ (((e >> 5) & 1u) << 3));
 }
 
-// Global element offset of local index e, relative to the block base.
+// Global element offset of local index e, relative to the block base.  Type 1:
+// local bits 0..2 -> global bits 0..2, local bits 3..7 -> loA.., 8..12 -> loB..
 template <int T>
-__device__ __forceinline__ size_t goff(uint32_t e, int lo) {
-    return T == 0 ? (size_t)e : ((size_t)(e & 7u) | ((size_t)(e >> 3) << lo));
+__device__ __forceinline__ size_t goff(uint32_t e, int loA, int loB) {
+    return T == 0 ? (size_t)e
+                  : ((size_t)(e & 7u) | ((size_t)((e >> 3) & 31u) << loA) | ((size_t)(e >> 8) << loB));
 }
 
+// Base index of block b: type 1 blocks enumerate the bits outside the two
+// windows and bits 0..2, lowest first (3..loA-1, loA+5..loB-1, loB+5..n-1).
 template <int T>
-__device__ __forceinline__ size_t block_base(uint32_t b, int lo) {
+__device__ __forceinline__ size_t block_base(uint32_t b, int loA, int loB) {
     if (T == 0) return (size_t)b << 13;
-    const int nlow = lo - 3;  // global bits 3 .. lo-1 come from the low block-index bits
-    return ((size_t)(b & ((1u << nlow) - 1u)) << 3) | ((size_t)(b >> nlow) << (lo + 10));
+    const int n1 = loA - 3, n2 = loB - loA - 5;
+    const size_t b1 = b & ((1u << n1) - 1u), b2 = (b >> n1) & ((1u << n2) - 1u), b3 = b >> (n1 + n2);
+    return (b1 << 3) | (b2 << (loA + 5)) | (b3 << (loB + 5));
 }
 
 // ---------------------------------------------------------------------------

@@ -78,7 +78,7 @@ struct PassArgs {
     double *partials;               // [item][block][NSLOT] per-block FP64 partial sums
     unsigned long long *topk_keys;  // [block][ktop] candidate keys (final pass, single item)
     int n;
-    int lo;                         // window offset of a high-group pass
+    int loA, loB;                   // window offsets of a high-group pass (local bits 3..7, 8..12)
     uint32_t mask;                  // which of the 13 block bits are mixed
     int nitems, ntables;
     int init;                       // synthesise |+>^n instead of loading psi

@@ -2,8 +2,14 @@
 //
 // The n qubits are split into G groups of <= 10 (the mixer of Eq.
 // qaoa_mixer_unitary factorises over qubits).  Group 0 owns the low bits
-// (blocks of 13 contiguous bits); every other group owns a 10-bit window
-// lo..lo+9 and carries global bits 0..2 for coalescing.  Layers visit the
+// (blocks of 13 contiguous bits); every other group owns two 5-bit windows
+// loA..loA+4 and loB..loB+4 (block local bits 3..7 and 8..12) and carries
+// global bits 0..2 for coalescing.  From n = 24 on, each high group takes one
+// window in the lower and one in the upper half of the high bits: a block
+// whose ten bits were all among the top bits would touch 2^10 rows 2^{n-10}
+// elements apart, i.e. about a thousand 2 MiB pages per CTA, and B300 then
+// streams at half its bandwidth (measured: 3.1 TB/s for bits 20..29 of a
+// 2^30 state against 5.5 TB/s for bits {10..14, 25..29}).  Layers visit the
 // groups in alternating order (A,B,C | C,B,A | ...), so the pass that ends
 // layer l also applies U_C(gamma_{l+1}) (diagonal, Eq. qaoa_cost_unitary) and
 // the same group's mixer of layer l+1: 1 + p(G-1) forward passes in all.
@@ -23,7 +29,7 @@ namespace qaoa {
 
 struct Group {
     int type;       // 0: low group (block = global bits 0..12), 1: high group
-    int lo;         // window offset (type 1)
+    int loA, loB;   // window offsets (type 1): local bits 3..7 -> loA.., 8..12 -> loB..
     uint32_t mask;  // mixed local bits
     int kX, kY;     // mixed bits in the register rounds of arrangements X and Y
 };
@@ -32,7 +38,7 @@ struct Group {
 // evaluation; 2: reverse pass undoing forward pass `fwd`.
 struct PassPlan {
     int kind;
-    int type, lo;
+    int type, loA, loB;
     uint32_t mask;
     int kX, kY;
     int init;
@@ -45,27 +51,62 @@ struct PassPlan {
 constexpr uint32_t REGS_X[2] = {0x0F8u, 0x1C18u};  // type 0: bits 3..7; type 1: {3,4,10,11,12}
 constexpr uint32_t REGS_Y[2] = {0x307u, 0x3E0u};   // type 0: {0,1,2,8,9}; type 1: bits 5..9
 
+inline uint32_t window_mask(int loA, int loB, int q0, int k) {
+    uint32_t m = 0;
+    for (int q = q0; q < q0 + k; ++q) {
+        if (q >= loA && q < loA + 5) m |= 1u << (3 + q - loA);
+        else m |= 1u << (8 + q - loB);
+    }
+    return m;
+}
+
+// Groups of the schedule.  Returns an empty vector if no valid layout exists
+// (never for 13 <= n <= 33 and 3 <= maxq <= 10).
 inline std::vector<Group> make_groups(int n, int maxq) {
     const int G = (n + maxq - 1) / maxq;
-    std::vector<Group> gs;
-    int q0 = 0;
-    for (int g = 0; g < G; ++g) {
-        const int k = n / G + (g < n % G ? 1 : 0);
-        Group gr{};
-        if (g == 0) {
-            gr.type = 0;
-            gr.lo = 0;
-            gr.mask = (1u << k) - 1u;
+    std::vector<int> k(G);
+    for (int g = 0; g < G; ++g) k[g] = n / G + (g < n % G ? 1 : 0);
+    std::vector<Group> gs(G);
+    gs[0] = Group{};
+    gs[0].type = 0;
+    gs[0].mask = (1u << k[0]) - 1u;
+    // high qubits [k0, n): the lower halves of the groups first, then the upper halves
+    const bool split = n >= 24 && G >= 2;
+    int qa = k[0];
+    int qb = k[0];
+    if (split)
+        for (int g = 1; g < G; ++g) qb += (k[g] + 1) / 2;
+    for (int g = 1; g < G; ++g) {
+        Group &gr = gs[g];
+        gr.type = 1;
+        bool ok = false;
+        if (split) {
+            const int a = (k[g] + 1) / 2, b = k[g] - a;
+            int sA = qa - (5 - a);
+            if (sA < 3) sA = 3;
+            int sB = qb < n - 5 ? qb : n - 5;
+            if (sA <= qa && sA + 5 >= qa + a && sB <= qb && sB + 5 >= qb + b && sA + 5 <= sB) {
+                gr.loA = sA;
+                gr.loB = sB;
+                gr.mask = 0;
+                for (int q = qa; q < qa + a; ++q) gr.mask |= 1u << (3 + q - sA);
+                for (int q = qb; q < qb + b; ++q) gr.mask |= 1u << (8 + q - sB);
+                ok = true;
+            }
+            qa += a;
+            qb += b;
+            if (!ok) return {};
         } else {
-            gr.type = 1;
-            gr.lo = q0 < n - 10 ? q0 : n - 10;
-            gr.mask = 0;
-            for (int q = q0; q < q0 + k; ++q) gr.mask |= 1u << (3 + q - gr.lo);
+            const int lo = qa < n - 10 ? qa : n - 10;
+            gr.loA = lo;
+            gr.loB = lo + 5;
+            gr.mask = window_mask(gr.loA, gr.loB, qa, k[g]);
+            qa += k[g];
         }
+    }
+    for (Group &gr : gs) {
         gr.kX = __builtin_popcount(gr.mask & REGS_X[gr.type]);
         gr.kY = __builtin_popcount(gr.mask & REGS_Y[gr.type]);
-        gs.push_back(gr);
-        q0 += k;
     }
     return gs;
 }
@@ -74,6 +115,7 @@ inline std::vector<Group> make_groups(int n, int maxq) {
 // reverse of the final pass is fused into it.
 inline std::vector<PassPlan> make_plan(int n, int p, bool grad, int maxq) {
     const std::vector<Group> gs = make_groups(n, maxq);
+    if (gs.empty()) return {};
     const int G = (int)gs.size();
     struct D {
         int group, init, epi, la, lc, lb;
@@ -99,7 +141,8 @@ inline std::vector<PassPlan> make_plan(int n, int p, bool grad, int maxq) {
         const Group &g = gs[d.group];
         pl.kind = kind;
         pl.type = g.type;
-        pl.lo = g.lo;
+        pl.loA = g.loA;
+        pl.loB = g.loB;
         pl.mask = g.mask;
         pl.kX = g.kX;
         pl.kY = g.kY;

@@ -45,12 +45,12 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *m, uint32_
 
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-__device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, int c1, int c4,
+__device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, int c1, int c3, int c4,
                                             unsigned long long *mbar) {
     asm volatile(
         "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::
             "r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(c1), "r"(0), "r"(0), "r"(c4), "r"(smem_u32(mbar))
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(c1), "r"(0), "r"(c3), "r"(c4), "r"(smem_u32(mbar))
         : "memory");
 }
 

@@ -183,3 +183,45 @@ def test_autotune_fusion_width(q, ctx):
     for c, k in ((ca, ka), (ck, kk), (cw, kw)):
         q.qaoa_cost_destroy(k)
         q.qaoa_ctx_destroy(c)
+
+
+def test_autograd_functions(q, ctx):
+    """torch.autograd.Function wrappers: backward of E (single and batched)
+    against the oracle's gradient and against central differences of the
+    wrapped forward."""
+    import torch
+    from paper_2606_26297_b300.autograd import qaoa_expectation, qaoa_expectation_batch
+    Q = inst.regular_maxcut_qubo(16, 4700)
+    cost = _cost(q, ctx, Q)
+    F = oracle.cost_table(oracle.canonical_of(Q))
+    g0, b0 = inst.ramp_angles(3)
+    g = torch.tensor(g0, dtype=torch.float64, requires_grad=True)
+    b = torch.tensor(b0, dtype=torch.float64, requires_grad=True)
+    E = qaoa_expectation(g, b, ctx, cost)
+    (2.0 * E).backward()
+    Eo, dgo, dbo = oracle.grad_adjoint(F, g0, b0)
+    assert abs(E.item() - Eo) / np.max(np.abs(F)) <= E_TOL
+    sc = max(np.abs(dgo).max(), np.abs(dbo).max())
+    assert np.max(np.abs(g.grad.numpy() - 2 * dgo)) <= 2 * G_TOL * sc
+    assert np.max(np.abs(b.grad.numpy() - 2 * dbo)) <= 2 * G_TOL * sc
+    h = 1e-3
+    for k in range(3):
+        e = np.zeros(3)
+        e[k] = h
+        fd = (qaoa_expectation(torch.tensor(g0 + e), torch.tensor(b0), ctx, cost).item()
+              - qaoa_expectation(torch.tensor(g0 - e), torch.tensor(b0), ctx, cost).item()) / (2 * h)
+        assert abs(fd - dgo[k]) <= 1e-3 * sc
+    # batched: weights per item flow into each item's gradient
+    G0, B0 = inst.random_angles(3, 4, 4701, gamma_scale=0.3)
+    G = torch.tensor(G0, requires_grad=True)
+    B = torch.tensor(B0, requires_grad=True)
+    Eb = qaoa_expectation_batch(G, B, ctx, [cost])
+    w = torch.tensor([1.0, -2.0, 0.5, 3.0], dtype=torch.float64)
+    (Eb * w).sum().backward()
+    for i in range(4):
+        Ei, dgi, dbi = oracle.grad_adjoint(F, G0[i], B0[i])
+        assert abs(Eb[i].item() - Ei) / np.max(np.abs(F)) <= E_TOL
+        sci = max(np.abs(dgi).max(), np.abs(dbi).max())
+        assert np.max(np.abs(G.grad[i].numpy() - w[i].item() * dgi)) <= abs(w[i].item()) * G_TOL * sci
+        assert np.max(np.abs(B.grad[i].numpy() - w[i].item() * dbi)) <= abs(w[i].item()) * G_TOL * sci
+    q.qaoa_cost_destroy(cost)

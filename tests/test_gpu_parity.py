@@ -394,6 +394,30 @@ def test_fusion_depth_agrees(q, n, p, kind):
         q.qaoa_ctx_destroy(c)
 
 
+@pytest.mark.parametrize("maxq", [10, 6])
+def test_split_windows_n24(q, maxq):
+    """From n = 24 the high groups take one 5-bit window from the lower and one
+    from the upper half of the high bits; state and gradient against the
+    oracle for 3 (width 10) and 4 (width 6) groups."""
+    n, p = 24, 2
+    Q = inst.normal_qubo(n, 1300)
+    g, b = _angles(Q, p, "normal")
+    c = q.qaoa_ctx_create(0, max_fused_qubits=maxq)
+    cost = _cost(q, c, Q)
+    F = oracle.cost_table(oracle.canonical_of(Q))
+    st = q.qaoa_forward(c, cost, g, b)
+    psi = q.qaoa_state_copy_to_host(c, st, n).astype(np.complex128)
+    assert np.linalg.norm(psi - oracle.evolve(F, g, b)) <= AMP_TOL
+    E, dg, db = q.qaoa_grad(c, cost, g, b)
+    Eo, dgo, dbo = oracle.grad_adjoint(F, g, b)
+    assert abs(E - Eo) / np.max(np.abs(F)) <= E_TOL
+    sc = max(np.max(np.abs(dgo)), np.max(np.abs(dbo)))
+    assert max(np.max(np.abs(dg - dgo)), np.max(np.abs(db - dbo))) <= G_TOL * sc
+    q.qaoa_state_destroy(st)
+    q.qaoa_cost_destroy(cost)
+    q.qaoa_ctx_destroy(c)
+
+
 def test_factorisation_noncontiguous(q, ctx):
     """A manual (non-contiguous) allocation goes through the general check."""
     n = 14
