@@ -173,6 +173,24 @@ def run_reference(args):
     return 0
 
 
+# ---- multi-rank aggregation (replicas) -------------------------------------------------
+
+def max_over_ranks(values, dist, device):
+    """Element-wise maximum of `values` over all ranks (identity without a
+    process group)."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def job_throughput(units_per_rank: float, world_size: int, seconds: float) -> float:
+    """Whole-job rate: the units every rank processed over the slowest rank's time."""
+    return units_per_rank * world_size / seconds
+
+
 # ---- the GPU arm ----------------------------------------------------------------------------
 
 def run_gpu(args):
@@ -244,15 +262,9 @@ def run_gpu(args):
     barrier()
     e2e_s = time.perf_counter() - t0
 
-    # max over ranks
-    t_max, e_max = ms / 1000.0, e2e_s
-    if dist is not None:
-        tt = torch.tensor([t_max, e_max], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max, e_max = float(tt[0]), float(tt[1])
-    units = p * args.steps * ws
-    value = units / t_max
-    e2e_value = units / e_max
+    # max over ranks; every rank evaluated the same number of layers
+    t_max, e_max = max_over_ranks([ms / 1000.0, e2e_s], dist, "cuda")
+    value, e2e_value = job_throughput(p * args.steps, ws, t_max), job_throughput(p * args.steps, ws, e_max)
 
     if rank == 0:
         peak, peak_src = _peaks()
