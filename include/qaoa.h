@@ -30,9 +30,9 @@
  *     synchronise that stream.
  *   - Handles are owned by the library and released with qaoa_*_destroy;
  *     every other buffer belongs to the caller.
- *   - Sizes: 1 <= n <= 33 (the state of n=33 is 64 GiB).  Functions that
- *     keep a second state (gradients) need 2 states + the 4-byte cost table
- *     in device memory.
+ *   - Sizes: 1 <= n <= 33 (the state of n=33 is 64 GiB).  Gradients need 3
+ *     states + the 4-byte cost table in device memory, or about p + 2 states
+ *     with stored forward states (options.adjoint_mode).
  */
 #ifndef QAOA_H
 #define QAOA_H
@@ -74,8 +74,13 @@ typedef struct {
 
 /* Adjoint (gradient) strategy. */
 typedef enum {
-    QAOA_ADJ_AUTO = 0,      /* uncompute unless the memory budget forbids it */
-    QAOA_ADJ_UNCOMPUTE = 1  /* reverse sweep recomputes earlier states by U^dagger */
+    QAOA_ADJ_AUTO = 0,      /* stored states when they fit in free device memory (and the
+                               memory budget) with a 4 GiB margin, else uncompute */
+    QAOA_ADJ_UNCOMPUTE = 1, /* the reverse sweep recomputes earlier states by U^dagger on an
+                               interleaved (psi, lambda) buffer: 3 states of memory */
+    QAOA_ADJ_STORE = 2      /* the forward sweep keeps the states the reverse sweep needs (about
+                               p + 2 states for 3 qubit groups); the reverse passes of mixer-only
+                               passes then carry lambda alone */
 } qaoa_adjoint_mode;
 
 /* Options of a context.  Zero-initialised means "defaults". */

@@ -62,6 +62,12 @@ struct DevBuf {
         *held += (int64_t)bytes;
         return QAOA_OK;
     }
+    void release(int64_t *held) {
+        if (p) cudaFree(p);
+        p = nullptr;
+        *held -= (int64_t)cap;
+        cap = 0;
+    }
     template <typename T>
     T *as() const {
         return reinterpret_cast<T *>(p);
@@ -76,7 +82,7 @@ struct ProfRec {
 
 // Device buffers of one plan execution (one n, a batch of items).
 struct PlanBufs {
-    DevBuf psi, pl, partials, sums, scal, slot_scale, plan, gamma, beta, item_s, item_kc, item_table, tables,
+    DevBuf psi, pl, states, lam, partials, sums, scal, slot_scale, plan, gamma, beta, item_s, item_kc, item_table, tables,
         out_E, out_dg, out_db, topk_a, topk_b, adam_m, adam_v, adam_step, history, small_items, small_out;
 };
 
@@ -223,7 +229,42 @@ struct PlanRun {
     std::vector<PassPlan> plan;
     int rows;
     float2 *psi_ext = nullptr;  // forward-only: evolve in this caller buffer instead of b.psi
+    bool stored = false;        // adjoint with stored forward states (else uncompute)
+    int nslots = 0;             // stored states per item
 };
+
+// Build the pass plan of r (r.n, r.p, r.grad, r.nitems set): the adjoint
+// keeps the forward states it needs when options.adjoint_mode asks for it, or
+// (auto) when they fit in free device memory with a margin; else it
+// uncomputes psi on the interleaved buffer.
+qaoa_status make_run_plan(qaoa_ctx c, PlanRun &r, const PlanBufs &b) {
+    const int maxq = maxq_for(c, r.n);
+    r.stored = false;
+    r.nslots = 0;
+    if (r.grad && c->opt.adjoint_mode != QAOA_ADJ_UNCOMPUTE) {
+        int ns = 0;
+        std::vector<PassPlan> sp = make_plan(r.n, r.p, true, maxq, true, &ns);
+        const double N8 = std::ldexp(8.0 * r.nitems, r.n);
+        // stored: psi + interleaved + lambda + ns states; uncompute: psi + interleaved
+        const double extra = (ns + 1) * N8 - (double)(b.states.cap + b.lam.cap);
+        size_t freeb = 0, total = 0;
+        cudaMemGetInfo(&freeb, &total);
+        const double margin = 4.0 * (1ull << 30);
+        bool fits = extra <= (double)freeb - margin;
+        if (c->opt.memory_budget > 0 &&
+            (double)c->held + extra > (double)c->opt.memory_budget)
+            fits = false;
+        if (ns > 0 && (c->opt.adjoint_mode == QAOA_ADJ_STORE || fits)) {
+            r.plan = std::move(sp);
+            r.stored = true;
+            r.nslots = ns;
+        }
+    }
+    if (!r.stored) r.plan = make_plan(r.n, r.p, r.grad, maxq);
+    if (r.plan.empty()) return fail(QAOA_ERR_INVALID_ARG, "no pass layout for n=%d", r.n);
+    r.rows = plan_rows(r.plan);
+    return QAOA_OK;
+}
 
 // Allocate the working set of a plan for `nitems` items of size n.
 qaoa_status ensure_plan_bufs(qaoa_ctx c, PlanBufs &b, const PlanRun &r) {
@@ -234,6 +275,13 @@ qaoa_status ensure_plan_bufs(qaoa_ctx c, PlanBufs &b, const PlanRun &r) {
     int64_t *h = &c->held;
     if (!r.psi_ext) QAOA_TRY(b.psi.ensure(B * N * sizeof(float2), h, bud));
     if (r.grad) QAOA_TRY(b.pl.ensure(B * N * sizeof(float4), h, bud));
+    if (r.grad && r.stored) {
+        QAOA_TRY(b.states.ensure((size_t)r.nslots * B * N * sizeof(float2), h, bud));
+        QAOA_TRY(b.lam.ensure(B * N * sizeof(float2), h, bud));
+    } else if (r.grad) {
+        b.states.release(h);
+        b.lam.release(h);
+    }
     QAOA_TRY(b.partials.ensure(B * nb * NSLOT * sizeof(double), h, bud));
     QAOA_TRY(b.sums.ensure((size_t)std::max(r.rows, 1) * B * NSLOT * sizeof(double), h, bud));
     QAOA_TRY(b.scal.ensure(r.plan.size() * B * sizeof(PassScal), h, bud));
@@ -264,8 +312,26 @@ qaoa_status enqueue_plan(qaoa_ctx c, PlanBufs &b, const PlanRun &r, const int32_
     for (size_t i = 0; i < r.plan.size(); ++i) {
         const PassPlan &pl = r.plan[i];
         PassArgs a{};
-        a.psi = r.psi_ext ? r.psi_ext : b.psi.as<float2>();
+        float2 *W = r.psi_ext ? r.psi_ext : b.psi.as<float2>();
+        const size_t stride = (size_t)r.nitems << n;  // elements of one stored state (all items)
+        auto slot_ptr = [&](int sl) -> float2 * {
+            return sl >= 0 ? b.states.as<float2>() + (size_t)sl * stride : W;
+        };
+        a.psi = W;
         a.pl = b.pl.as<float4>();
+        if (r.stored) {
+            a.split = pl.kind == 1 || pl.kind == 2;  // write lambda alone
+            a.lam = b.lam.as<float2>();
+            if (pl.kind == 0) {
+                a.psi = slot_ptr(pl.in_slot);
+                a.psi_out = slot_ptr(pl.out_slot);
+            } else if (pl.kind == 1) {
+                a.psi = slot_ptr(pl.in_slot);
+            } else if (pl.kind == 3) {
+                a.psi_src = slot_ptr(pl.psi_slot);
+                a.pl_out = pl.pl_out;
+            }
+        }
         a.C = tables;
         a.item_table = item_table;
         a.scal = scal + i * r.nitems;
@@ -281,16 +347,17 @@ qaoa_status enqueue_plan(qaoa_ctx c, PlanBufs &b, const PlanRun &r, const int32_
         a.has_pre = pl.la >= 0;
         a.has_cost = pl.lc >= 0;
         a.has_post = pl.lb >= 0;
-        a.store = pl.kind == 2 ? !pl.init : 1;
+        a.store = pl.kind >= 2 ? !pl.init : 1;
         a.precise_phase = 0;
         a.ktop = pl.kind == 1 ? r.ktop : 0;
         a.amp0 = (float)std::pow(2.0, -0.5 * n);
         const double bytes = pass_bytes_per_amp(pl) * std::ldexp((double)r.nitems, n);
         {
-            ProfScope ps(c, pl.kind == 2 ? 1 : 0, bytes, profile);
+            ProfScope ps(c, pl.kind >= 2 ? 1 : 0, bytes, profile);
             cudaError_t e = pl.kind == 0   ? launch_fwd_pass(pl.type, a, c->stream)
                             : pl.kind == 1 ? launch_final_pass(pl.type, a, c->num_sms, stw, c->stream)
-                                           : launch_rev_pass(pl.type, a, c->num_sms, stw, c->stream);
+                            : pl.kind == 2 ? launch_rev_pass(pl.type, a, c->num_sms, stw, c->stream)
+                                           : launch_rev_mid(pl.type, a, c->stream);
             if (e) return fail(QAOA_ERR_CUDA, "layer-pass launch failed: %s", cudaGetErrorString(e));
             c->launches_total += 1;
         }
@@ -368,11 +435,9 @@ qaoa_status run_single(qaoa_ctx c, const qaoa_cost_s *cost, int p, const double 
     r.ntables = 1;
     r.grad = grad;
     r.ktop = grad ? ktop : 0;
-    r.plan = make_plan(cost->n, p, grad, maxq_for(c, cost->n));
-    if (r.plan.empty()) return fail(QAOA_ERR_INVALID_ARG, "no pass layout for n=%d", cost->n);
-    r.rows = plan_rows(r.plan);
     r.psi_ext = grad ? nullptr : psi_out;
     PlanBufs &b = c->single;
+    QAOA_TRY(make_run_plan(c, r, b));
     QAOA_TRY(ensure_plan_bufs(c, b, r));
     // scalars on the host (one item)
     std::vector<PassScal> sc(r.plan.size());
@@ -536,12 +601,10 @@ qaoa_status build_groups(qaoa_ctx c, int nq, const qaoa_cost *costs, const int32
         g.r.ntables = (int)g.tabs.size();
         g.r.grad = grad;
         g.r.ktop = 0;
-        g.r.plan = make_plan(g.n, p, grad, maxq_for(c, g.n));
-        if (g.r.plan.empty()) return fail(QAOA_ERR_INVALID_ARG, "no pass layout for n=%d", g.n);
-        g.r.rows = plan_rows(g.r.plan);
         auto &slot = c->groups[g.n];
         if (!slot) slot.reset(new PlanBufs());
         g.b = slot.get();
+        QAOA_TRY(make_run_plan(c, g.r, *g.b));
         QAOA_TRY(ensure_plan_bufs(c, *g.b, g.r));
         const size_t N = (size_t)1 << g.n;
         if (g.tabs.size() == 1) {
@@ -679,6 +742,7 @@ qaoa_status qaoa_ctx_create(int device, void *cuda_stream, const qaoa_options *o
         return fail(QAOA_ERR_INVALID_ARG, "max_fused_qubits must be 0 or in [3, 10]");
     if (o.table_build < 0 || o.table_build > 1) return fail(QAOA_ERR_INVALID_ARG, "table_build must be 0 or 1");
     if (o.autotune < 0 || o.autotune > 1) return fail(QAOA_ERR_INVALID_ARG, "autotune must be 0 or 1");
+    if (o.adjoint_mode < 0 || o.adjoint_mode > 2) return fail(QAOA_ERR_INVALID_ARG, "adjoint_mode must be 0, 1 or 2");
     for (int k = 0; k < 4; ++k)
         if (o.reserved[k]) return fail(QAOA_ERR_INVALID_ARG, "options.reserved[%d] must be zero", k);
     auto *c = new qaoa_ctx_s();

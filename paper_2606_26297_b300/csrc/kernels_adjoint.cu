@@ -100,6 +100,15 @@ __device__ __forceinline__ void store_pq(const float2 (&P)[32], const float2 (&Q
         __stcs(q + roff<T, A>(m, loA, loB), make_float4(P[m].x, P[m].y, Q[m].x, Q[m].y));
 }
 
+// store lambda alone from the packed pair (P, Q)
+template <int T, int A>
+__device__ __forceinline__ void store_lam(const float2 (&P)[32], const float2 (&Q)[32], float2 *__restrict__ p,
+                                          uint32_t l, uint32_t w, int loA, int loB) {
+    float2 *q = p + goff<T>(local_idx<T, A>(l, 0u, w), loA, loB);
+#pragma unroll
+    for (int m = 0; m < 32; ++m) __stcs(q + roff<T, A>(m, loA, loB), make_float2(P[m].y, Q[m].y));
+}
+
 // unit u of a launch: item u >> nbits, block u & (2^nbits - 1)
 struct Unit {
     uint32_t item, b;
@@ -236,7 +245,10 @@ __global__ void __launch_bounds__(PASS_THREADS, 1)
         round_mix_pq<T, 0>(P, Q, -sc.pre_t, a.mask);
 #pragma unroll
         for (int m = 0; m < 32; ++m) cmul_pq(P[m], Q[m], sc.kend2);
-        store_pq<T, 0>(P, Q, a.pl + ((size_t)un.item << a.n) + base, l, w, a.loA, a.loB);
+        if (a.split)
+            store_lam<T, 0>(P, Q, a.lam + ((size_t)un.item << a.n) + base, l, w, a.loA, a.loB);
+        else
+            store_pq<T, 0>(P, Q, a.pl + ((size_t)un.item << a.n) + base, l, w, a.loA, a.loB);
         double vals[NSLOT] = {(double)e0, (double)e1, (double)x1, (double)x0, 0.0, 0.0, 0.0, 0.0};
         block_sum_write(vals, red, a.partials, u);
         __syncthreads();
@@ -248,7 +260,7 @@ __global__ void __launch_bounds__(PASS_THREADS, 1)
 // (psi, lambda).  slots: 0,1 = X-terms of the post mixer (arrangements X, Y);
 // 2 = cost term; 3,4 = X-terms of the pre mixer (Y, X).
 // ---------------------------------------------------------------------------
-template <int T>
+template <int T, bool SPLIT>
 __global__ void __launch_bounds__(PASS_THREADS, 1)
     rev_pass_kernel(const PassArgs a, const __grid_constant__ CUtensorMap mpl,
                     const __grid_constant__ CUtensorMap mcost, int nunits, unsigned int *status) {
@@ -329,14 +341,16 @@ __global__ void __launch_bounds__(PASS_THREADS, 1)
 #pragma unroll
                     for (int m = 0; m < 32; ++m) cmul_pq(P[m], Q[m], sc.kend);
                 }
-                store_pq<T, 0>(P, Q, dst, l, w, a.loA, a.loB);
+                if (SPLIT) store_lam<T, 0>(P, Q, a.lam + ((size_t)un.item << a.n) + base, l, w, a.loA, a.loB);
+                else store_pq<T, 0>(P, Q, dst, l, w, a.loA, a.loB);
             }
         } else if (a.store) {
             if (!a.has_cost) {
 #pragma unroll
                 for (int m = 0; m < 32; ++m) cmul_pq(P[m], Q[m], sc.kend);
             }
-            store_pq<T, 1>(P, Q, dst, l, w, a.loA, a.loB);
+            if (SPLIT) store_lam<T, 1>(P, Q, a.lam + ((size_t)un.item << a.n) + base, l, w, a.loA, a.loB);
+            else store_pq<T, 1>(P, Q, dst, l, w, a.loA, a.loB);
         }
         double vals[NSLOT];
 #pragma unroll
@@ -344,6 +358,74 @@ __global__ void __launch_bounds__(PASS_THREADS, 1)
         block_sum_write(vals, red, a.partials, u);
         __syncthreads();
     }
+}
+
+// ---------------------------------------------------------------------------
+// reverse pass of a middle forward pass (mixer only) with stored states:
+// lambda alone is carried back through the mixer (undo the group's RX,
+// return to true scale) and written, alone or interleaved with the stored
+// input state psi_in; the X-terms of the mixer are taken at the pass input
+// against psi_in, once with lambda in arrangement Y and once, after a
+// transpose, in arrangement X.  Direct loads, two CTAs per SM.  slots: 0 =
+// X-term (Y bits), 1 = X-term (X bits).
+// ---------------------------------------------------------------------------
+
+// sum over the mixed register bits j of sum_m Im(conj(lambda_{m ^ e_j}) psi_m),
+// psi streamed from global memory in arrangement A; PL: also write the
+// interleaved element (psi_m, lambda_m) to pl
+template <int T, int A, bool PL>
+__device__ __forceinline__ float xterm_stream(const float2 (&v)[32], const float2 *__restrict__ pp,
+                                              float4 *__restrict__ pl, uint32_t l, uint32_t w, int loA, int loB,
+                                              uint32_t mask) {
+    const size_t t = goff<T>(local_idx<T, A>(l, 0u, w), loA, loB);
+    const float2 *q = pp + t;
+    bool on[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) on[i] = (mask >> regbit<T, A>(i)) & 1u;
+    float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+    for (int m = 0; m < 32; ++m) {
+        const float2 ps = __ldg(q + roff<T, A>(m, loA, loB));
+        if (PL) __stcs(pl + t + roff<T, A>(m, loA, loB), make_float4(ps.x, v[m].x, ps.y, v[m].y));
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            if (!on[i]) continue;
+            const float2 la = v[m ^ (1 << i)];
+            s0 = fmaf(la.x, ps.y, s0);
+            s1 = fmaf(-la.y, ps.x, s1);
+        }
+    }
+    return s0 + s1;
+}
+
+template <int T, bool PLOUT>
+__global__ void __launch_bounds__(PASS_THREADS, 2) rev_mid_kernel(const PassArgs a) {
+    extern __shared__ __align__(16) float2 sm[];
+    __shared__ double red[PASS_THREADS / 32][NSLOT];
+    const uint32_t l = threadIdx.x & 31u, w = threadIdx.x >> 5;
+    const int nbits = a.n - BLOCK_BITS;
+    const uint32_t item = blockIdx.x >> nbits, b = blockIdx.x & ((1u << nbits) - 1u);
+    const PassScal sc = a.scal[item];
+    const uint32_t fb = sc.post_flip ? a.mask : 0u;
+    const size_t base = block_base<T>(b, a.loA, a.loB);
+    float2 *lp = a.lam + ((size_t)item << a.n) + base;
+    const float2 *pp = a.psi_src + ((size_t)item << a.n) + base;
+    float2 v[32];
+    load_arr<T, 0>(v, lp, l, w, a.loA, a.loB);
+    round_mix<T, 0>(v, -sc.post_t, a.mask);
+    transpose1<T, 0, 1>(v, sm, l, w, fb);
+    round_mix<T, 1>(v, -sc.post_t, a.mask);
+#pragma unroll
+    for (int m = 0; m < 32; ++m) v[m] = cmul(v[m], sc.kend);
+    // lambda_in: interleaved with psi_in for a following reverse pass that
+    // undoes a cost layer (it uncomputes psi), else alone
+    float4 *plo = a.pl + ((size_t)item << a.n) + base;
+    const float xy = xterm_stream<T, 1, false>(v, pp, plo, l, w, a.loA, a.loB, a.mask);
+    if (!PLOUT) store_arr<T, 1>(v, lp, l, w, a.loA, a.loB);
+    transpose1<T, 1, 0>(v, sm, l, w, 0u);
+    const float xx = xterm_stream<T, 0, PLOUT>(v, pp, plo, l, w, a.loA, a.loB, a.mask);
+    double vals[NSLOT] = {(double)xy, (double)xx, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    block_sum_write(vals, red, a.partials, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -425,12 +507,38 @@ cudaError_t launch_rev_pass(int type, const PassArgs &a, int grid, unsigned int 
         if (a.has_cost && (e = make_block_map(&mc, a.C, a.n, a.loA, a.loB, 4, a.ntables))) return e;
     }
     if (grid > nunits) grid = nunits;
-    if (type == 0) {
-        if ((e = set_smem(rev_pass_kernel<0>, smem))) return e;
-        rev_pass_kernel<0><<<grid, PASS_THREADS, smem, st>>>(a, m, mc, nunits, status);
+    if (type == 0 && !a.split) {
+        if ((e = set_smem(rev_pass_kernel<0, false>, smem))) return e;
+        rev_pass_kernel<0, false><<<grid, PASS_THREADS, smem, st>>>(a, m, mc, nunits, status);
+    } else if (type == 0) {
+        if ((e = set_smem(rev_pass_kernel<0, true>, smem))) return e;
+        rev_pass_kernel<0, true><<<grid, PASS_THREADS, smem, st>>>(a, m, mc, nunits, status);
+    } else if (!a.split) {
+        if ((e = set_smem(rev_pass_kernel<1, false>, smem))) return e;
+        rev_pass_kernel<1, false><<<grid, PASS_THREADS, smem, st>>>(a, m, mc, nunits, status);
     } else {
-        if ((e = set_smem(rev_pass_kernel<1>, smem))) return e;
-        rev_pass_kernel<1><<<grid, PASS_THREADS, smem, st>>>(a, m, mc, nunits, status);
+        if ((e = set_smem(rev_pass_kernel<1, true>, smem))) return e;
+        rev_pass_kernel<1, true><<<grid, PASS_THREADS, smem, st>>>(a, m, mc, nunits, status);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rev_mid(int type, const PassArgs &a, cudaStream_t st) {
+    const unsigned grid = (unsigned)a.nitems << (a.n - BLOCK_BITS);
+    const int smem = 8192 * (int)sizeof(float2);
+    cudaError_t e;
+    if (type == 0 && a.pl_out) {
+        if ((e = set_smem(rev_mid_kernel<0, true>, smem))) return e;
+        rev_mid_kernel<0, true><<<grid, PASS_THREADS, smem, st>>>(a);
+    } else if (type == 0) {
+        if ((e = set_smem(rev_mid_kernel<0, false>, smem))) return e;
+        rev_mid_kernel<0, false><<<grid, PASS_THREADS, smem, st>>>(a);
+    } else if (a.pl_out) {
+        if ((e = set_smem(rev_mid_kernel<1, true>, smem))) return e;
+        rev_mid_kernel<1, true><<<grid, PASS_THREADS, smem, st>>>(a);
+    } else {
+        if ((e = set_smem(rev_mid_kernel<1, false>, smem))) return e;
+        rev_mid_kernel<1, false><<<grid, PASS_THREADS, smem, st>>>(a);
     }
     return cudaGetLastError();
 }

@@ -21,7 +21,8 @@ __global__ void __launch_bounds__(PASS_THREADS, 2) fwd_pass_kernel(const PassArg
     const uint32_t item = blockIdx.x >> nbits, b = blockIdx.x & ((1u << nbits) - 1u);
     const PassScal sc = a.scal[item];
     const size_t base = block_base<T>(b, a.loA, a.loB);
-    float2 *pb = a.psi + ((size_t)item << a.n) + base;
+    const float2 *pb = a.psi + ((size_t)item << a.n) + base;
+    float2 *po = (a.psi_out ? a.psi_out : a.psi) + ((size_t)item << a.n) + base;
     const int32_t *cb = a.C + ((size_t)(a.item_table ? a.item_table[item] : 0) << a.n) + base;
     float2 v[32];
     if (a.init) {
@@ -52,13 +53,13 @@ __global__ void __launch_bounds__(PASS_THREADS, 2) fwd_pass_kernel(const PassArg
 #pragma unroll
             for (int m = 0; m < 32; ++m) v[m] = cmul(v[m], sc.kend);
         }
-        store_arr<T, 0>(v, pb, l, w, a.loA, a.loB);
+        store_arr<T, 0>(v, po, l, w, a.loA, a.loB);
     } else {
         if (!a.has_cost) {
 #pragma unroll
             for (int m = 0; m < 32; ++m) v[m] = cmul(v[m], sc.kend);
         }
-        store_arr<T, 1>(v, pb, l, w, a.loA, a.loB);
+        store_arr<T, 1>(v, po, l, w, a.loA, a.loB);
     }
 }
 

@@ -70,8 +70,13 @@ struct PassScal {
 // Item i's state is psi + i * 2^n (pl likewise); its table is
 // C + item_table[i] * 2^n (item_table null: table 0 for all).
 struct PassArgs {
-    float2 *psi;
+    float2 *psi;                    // forward: input state (in place unless psi_out is set)
+    float2 *psi_out;                // forward: output state, or null for in place
     float4 *pl;                     // interleaved (psi.re, lambda.re, psi.im, lambda.im) per index
+    const float2 *psi_src;          // stored forward state read by a reverse pass (split mode)
+    float2 *lam;                    // lambda alone (stored-state adjoint)
+    int split;                      // final / reverse pass: write lambda alone to lam
+    int pl_out;                     // mixer-only reverse pass: write (psi_in, lambda) interleaved to pl
     const int32_t *C;
     const int *item_table;
     const PassScal *scal;           // [nitems]
@@ -94,6 +99,7 @@ struct PassArgs {
 cudaError_t launch_fwd_pass(int type, const PassArgs &a, cudaStream_t st);
 cudaError_t launch_final_pass(int type, const PassArgs &a, int grid, unsigned int *status, cudaStream_t st);
 cudaError_t launch_rev_pass(int type, const PassArgs &a, int grid, unsigned int *status, cudaStream_t st);
+cudaError_t launch_rev_mid(int type, const PassArgs &a, cudaStream_t st);
 cudaError_t launch_reduce_partials(const double *partials, int nitems, int nblocks, double *out,
                                    cudaStream_t st);
 cudaError_t launch_topk_merge(const unsigned long long *in, int nlists, int k,

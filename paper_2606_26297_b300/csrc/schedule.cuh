@@ -35,9 +35,25 @@ struct Group {
 };
 
 // One pass as executed.  kind 0: forward; 1: final forward pass of a gradient
-// evaluation; 2: reverse pass undoing forward pass `fwd`.
+// evaluation; 2: reverse pass undoing a forward pass on (psi, lambda); 3:
+// reverse pass of a middle (mixer-only) forward pass that advances lambda
+// alone, reading psi from a stored forward state.
+//
+// State buffers: slot >= 0 is a stored forward state, SLOT_W the working
+// state, SLOT_NONE no buffer.  Without stored states every pass works in place
+// and the reverse sweep uncomputes psi on the interleaved (psi, lambda)
+// buffer.  With them (stored = 1, three or more qubit groups) the forward pass
+// f reads in_slot and writes out_slot, keeping the input of every mixer-only
+// pass; the reverse of a mixer-only pass (kind 3) reads psi from psi_slot and
+// carries lambda alone, writing it interleaved with psi (pl_out) when the next
+// reverse pass undoes a cost layer, which then runs on the interleaved buffer
+// as before and writes lambda alone.
+constexpr int SLOT_W = -1, SLOT_NONE = -2;
 struct PassPlan {
     int kind;
+    int stored;
+    int in_slot, out_slot, psi_slot;
+    int pl_out;
     int type, loA, loB;
     uint32_t mask;
     int kX, kY;
@@ -112,8 +128,11 @@ inline std::vector<Group> make_groups(int n, int maxq) {
 }
 
 // Forward schedule, then (grad) the reverse passes in reverse order; the
-// reverse of the final pass is fused into it.
-inline std::vector<PassPlan> make_plan(int n, int p, bool grad, int maxq) {
+// reverse of the final pass is fused into it.  stored: keep the forward states
+// the reverse sweep needs (outputs of the first and of boundary passes, and
+// inputs of middle passes); *nslots receives their count.
+inline std::vector<PassPlan> make_plan(int n, int p, bool grad, int maxq, bool stored = false,
+                                       int *nslots = nullptr) {
     const std::vector<Group> gs = make_groups(n, maxq);
     if (gs.empty()) return {};
     const int G = (int)gs.size();
@@ -134,12 +153,28 @@ inline std::vector<PassPlan> make_plan(int n, int p, bool grad, int maxq) {
             else f.push_back({last, 0, 0, -1, -1, l});
         }
     }
+    const int F = (int)f.size();
+    stored = stored && grad && G >= 3;
+    auto is_middle = [&](int i) { return !f[i].init && !f[i].epi && f[i].la < 0 && f[i].lc < 0 && f[i].lb >= 0; };
+    std::vector<int> in_slot(F, SLOT_NONE), out_slot(F, SLOT_W);
+    int ns = 0;
+    for (int i = 0; i < F; ++i) {
+        in_slot[i] = i == 0 ? SLOT_NONE : out_slot[i - 1];
+        if (f[i].epi) {
+            out_slot[i] = SLOT_NONE;
+        } else if (stored && i + 1 < F && is_middle(i + 1)) {
+            out_slot[i] = ns++;
+        }
+    }
+    if (nslots) *nslots = ns;
     std::vector<PassPlan> plan;
     int rows = 0;
     auto base = [&](const D &d, int kind) {
         PassPlan pl{};
         const Group &g = gs[d.group];
         pl.kind = kind;
+        pl.stored = stored ? 1 : 0;
+        pl.in_slot = pl.out_slot = pl.psi_slot = SLOT_W;
         pl.type = g.type;
         pl.loA = g.loA;
         pl.loB = g.loB;
@@ -154,8 +189,11 @@ inline std::vector<PassPlan> make_plan(int n, int p, bool grad, int maxq) {
         pl.sum_index = -1;
         return pl;
     };
-    for (const D &d : f) {
+    for (int i = 0; i < F; ++i) {
+        const D &d = f[i];
         PassPlan pl = base(d, d.epi ? 1 : 0);
+        pl.in_slot = in_slot[i];
+        pl.out_slot = out_slot[i];
         if (d.epi) {
             pl.slot_param[0] = pl.slot_param[1] = -2;
             pl.slot_param[2] = pl.slot_param[3] = d.la;
@@ -165,7 +203,10 @@ inline std::vector<PassPlan> make_plan(int n, int p, bool grad, int maxq) {
     }
     if (grad)
         for (int i = (int)f.size() - 2; i >= 0; --i) {
-            PassPlan pl = base(f[i], 2);
+            const bool mid = stored && is_middle(i);
+            PassPlan pl = base(f[i], mid ? 3 : 2);
+            pl.psi_slot = mid ? in_slot[i] : SLOT_NONE;
+            pl.pl_out = mid && i >= 1 && !is_middle(i - 1);
             if (f[i].lb >= 0) pl.slot_param[0] = pl.slot_param[1] = f[i].lb;
             if (f[i].lc >= 0) pl.slot_param[2] = p + f[i].lc;
             if (f[i].la >= 0) pl.slot_param[3] = pl.slot_param[4] = f[i].la;
@@ -322,7 +363,7 @@ __host__ __device__ inline void pass_scalars(const PassPlan &pl, const double *g
     }
     const HdCx one{1.0, 0.0};
     HdCx S = one;
-    if (pl.kind != 2) {
+    if (pl.kind == 0 || pl.kind == 1) {
         if (pl.la >= 0) S = hc_div(S, hc_pow(ma.f, k));
         if (pl.lc >= 0) {
             const unsigned long long phi = phase_multiplier(gamma[pl.lc], s);
@@ -346,6 +387,12 @@ __host__ __device__ inline void pass_scalars(const PassPlan &pl, const double *g
             Sl = hc_div(Sl, hc_pow(hc_conj(ma.f), pl.kX));
             sc->kend2 = hc_f2(hc_inv(Sl));
         }
+    } else if (pl.kind == 3) {
+        // lambda alone: undo the mixer, return to true scale, then both
+        // X-term halves at the pass input against the stored psi
+        S = hc_div(S, hc_pow(hc_conj(mb.f), k));
+        sc->kend = hc_f2(hc_inv(S));
+        slot_scale[0] = slot_scale[1] = 1.0;
     } else {
         if (pl.lb >= 0) {
             slot_scale[0] = 1.0 / hc_norm(S);
@@ -376,8 +423,9 @@ __host__ __device__ inline void pass_scalars(const PassPlan &pl, const double *g
 // Algorithmic bytes per amplitude of a pass (what the method must move).
 inline double pass_bytes_per_amp(const PassPlan &pl) {
     if (pl.kind == 0) return (pl.init ? 0.0 : 8.0) + 8.0 + (pl.lc >= 0 ? 4.0 : 0.0);
-    if (pl.kind == 1) return 8.0 + 4.0 + 16.0;
-    return 16.0 + (pl.init ? 0.0 : 16.0) + (pl.lc >= 0 ? 4.0 : 0.0);
+    if (pl.kind == 1) return 8.0 + 4.0 + (pl.stored ? 8.0 : 16.0);
+    if (pl.kind == 3) return 8.0 + 8.0 + (pl.pl_out ? 16.0 : 8.0);  // psi_in, lambda in, lambda (+psi) out
+    return 16.0 + (pl.init ? 0.0 : (pl.stored ? 8.0 : 16.0)) + (pl.lc >= 0 ? 4.0 : 0.0);
 }
 
 // Device side (batch.cu): recompute every pass's scalars from device angles,

@@ -23,6 +23,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 QAOA_OK, QAOA_ERR_INVALID_ARG, QAOA_ERR_OUT_OF_MEMORY, QAOA_ERR_RANGE, QAOA_ERR_CUDA, \
     QAOA_ERR_TIMEOUT, QAOA_ERR_ALLOCATION = range(7)
 QAOA_I32, QAOA_F32, QAOA_F64 = 0, 1, 2
+QAOA_ADJ_AUTO, QAOA_ADJ_UNCOMPUTE, QAOA_ADJ_STORE = 0, 1, 2
 _DTYPES = {"i32": (QAOA_I32, np.int32), "f32": (QAOA_F32, np.float32), "f64": (QAOA_F64, np.float64)}
 
 
@@ -112,7 +113,7 @@ def qaoa_last_error() -> str:
 
 def qaoa_ctx_create(device: int = 0, stream: int | None = None, profile: bool = False,
                     memory_budget: int = 0, max_fused_qubits: int = 0, state_fp64: bool = False,
-                    table_build: int = 0, autotune: bool = False):
+                    table_build: int = 0, autotune: bool = False, adjoint_mode: int = 0):
     """Create a context; `stream` is a raw cudaStream_t (e.g. torch's
     `torch.cuda.current_stream().cuda_stream`), None for the default stream."""
     opt = qaoa_options()
@@ -122,6 +123,7 @@ def qaoa_ctx_create(device: int = 0, stream: int | None = None, profile: bool = 
     opt.state_fp64 = int(state_fp64)
     opt.table_build = int(table_build)
     opt.autotune = int(autotune)
+    opt.adjoint_mode = int(adjoint_mode)
     out = _P()
     _check(_lib.qaoa_ctx_create(int(device), _P(stream or 0), ctypes.byref(opt), ctypes.byref(out)))
     return out

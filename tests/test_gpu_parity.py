@@ -418,6 +418,37 @@ def test_split_windows_n24(q, maxq):
     q.qaoa_ctx_destroy(c)
 
 
+@pytest.mark.parametrize("n,p,kind,maxq", [(13, 2, "normal", 10), (18, 3, "int", 10), (22, 3, "maxcut", 10),
+                                          (24, 2, "normal", 10), (20, 2, "int", 6), (17, 4, "normal", 4)])
+def test_adjoint_modes_agree(q, n, p, kind, maxq):
+    """Stored forward states (lambda alone through mixer-only passes) and the
+    uncompute sweep give the same E and gradient, both against the oracle;
+    2 to 5 qubit groups."""
+    Q = _instance(kind, n, 1400 + n)
+    g, b = _angles(Q, p, kind)
+    F = oracle.cost_table(oracle.canonical_of(Q))
+    Eo, dgo, dbo = oracle.grad_adjoint(F, g, b)
+    sc = max(np.max(np.abs(dgo)), np.max(np.abs(dbo)))
+    res = {}
+    for mode in (q.QAOA_ADJ_UNCOMPUTE, q.QAOA_ADJ_STORE):
+        c = q.qaoa_ctx_create(0, adjoint_mode=mode, max_fused_qubits=maxq)
+        cost = _cost(q, c, Q)
+        E, dg, db, ti, tp = q.qaoa_grad(c, cost, g, b, k_top=4)
+        assert abs(E - Eo) / np.max(np.abs(F)) <= E_TOL
+        assert max(np.max(np.abs(dg - dgo)), np.max(np.abs(db - dbo))) <= G_TOL * sc
+        Eb, dgb, dbb = q.qaoa_grad_batch(c, [cost], np.stack([g, g * 0.5]), np.stack([b, b]))
+        assert abs(Eb[0] - Eo) / np.max(np.abs(F)) <= E_TOL
+        assert max(np.max(np.abs(dgb[0] - dgo)), np.max(np.abs(dbb[0] - dbo))) <= G_TOL * sc
+        res[mode] = (E, dg, db, ti, Eb, dgb, dbb)
+        q.qaoa_cost_destroy(cost)
+        q.qaoa_ctx_destroy(c)
+    (E1, dg1, db1, t1, Eb1, dgb1, dbb1), (E2, dg2, db2, t2, Eb2, dgb2, dbb2) = res.values()
+    assert abs(E1 - E2) <= 1e-6 * np.max(np.abs(F))
+    assert max(np.abs(dg1 - dg2).max(), np.abs(db1 - db2).max()) <= 1e-5 * sc
+    assert np.array_equal(t1, t2)
+    assert np.max(np.abs(Eb1 - Eb2)) <= 1e-6 * np.max(np.abs(F))
+
+
 def test_factorisation_noncontiguous(q, ctx):
     """A manual (non-contiguous) allocation goes through the general check."""
     n = 14
