@@ -410,6 +410,12 @@ __global__ void __launch_bounds__(PASS_THREADS, 2) rev_mid_kernel(const PassArgs
     const size_t base = block_base<T>(b, a.loA, a.loB);
     float2 *lp = a.lam + ((size_t)item << a.n) + base;
     const float2 *pp = a.psi_src + ((size_t)item << a.n) + base;
+    {
+        // start the stored state's journey to L1 while lambda is undone
+        const float2 *qy = pp + goff<T>(local_idx<T, 1>(l, 0u, w), a.loA, a.loB);
+#pragma unroll
+        for (int m = 0; m < 32; ++m) asm volatile("prefetch.global.L1 [%0];" ::"l"(qy + roff<T, 1>(m, a.loA, a.loB)));
+    }
     float2 v[32];
     load_arr<T, 0>(v, lp, l, w, a.loA, a.loB);
     round_mix<T, 0>(v, -sc.post_t, a.mask);
