@@ -295,8 +295,9 @@ qaoa_status ensure_plan_bufs(qaoa_ctx c, PlanBufs &b, const PlanRun &r) {
     QAOA_TRY(b.out_dg.ensure(B * std::max(r.p, 1) * sizeof(double), h, bud));
     QAOA_TRY(b.out_db.ensure(B * std::max(r.p, 1) * sizeof(double), h, bud));
     const int kk = std::max(r.ktop, 1);
-    QAOA_TRY(b.topk_a.ensure((size_t)nb * kk * 8 + 64, h, bud));
-    QAOA_TRY(b.topk_b.ensure((size_t)((nb + 255) / 256 + 1) * kk * 8 + 64, h, bud));
+    const size_t nlists = (size_t)std::max(nb, c->num_sms * (PASS_THREADS / 32));  // final pass: one per warp
+    QAOA_TRY(b.topk_a.ensure(nlists * kk * 8 + 64, h, bud));
+    QAOA_TRY(b.topk_b.ensure((size_t)((nlists + 255) / 256 + 1) * kk * 8 + 64, h, bud));
     QAOA_TRY(c->status.ensure(16, h, bud));
     return QAOA_OK;
 }
@@ -462,9 +463,10 @@ qaoa_status run_single(qaoa_ctx c, const qaoa_cost_s *cost, int p, const double 
     std::vector<unsigned long long> keys(std::max(ktop, 1));
     if (ktop > 0) {
         int which = 0, nl = 0;
-        const int nb = 1 << (r.n - BLOCK_BITS);
-        CUDA_TRY(launch_topk_merge(b.topk_a.as<unsigned long long>(), nb, ktop, b.topk_b.as<unsigned long long>(),
-                                   &which, &nl, c->stream));
+        // the final pass leaves one list per warp of its persistent grid
+        const int grid = std::min(c->num_sms, 1 << (r.n - BLOCK_BITS));
+        CUDA_TRY(launch_topk_merge(b.topk_a.as<unsigned long long>(), grid * (PASS_THREADS / 32), ktop,
+                                   b.topk_b.as<unsigned long long>(), &which, &nl, c->stream));
         c->launches_total += nl;
         const void *src = which ? b.topk_b.p : b.topk_a.p;
         CUDA_TRY(cudaMemcpyAsync(keys.data(), src, (size_t)ktop * 8, cudaMemcpyDeviceToHost, c->stream));

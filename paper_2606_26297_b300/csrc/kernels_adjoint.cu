@@ -180,13 +180,14 @@ __global__ void __launch_bounds__(PASS_THREADS, 1)
     float2 *xbuf = reinterpret_cast<float2 *>(smraw + 65536 + 32768);  // transposes, 64 KB
     __shared__ __align__(8) unsigned long long mbar, mbarc;
     __shared__ double red[PASS_THREADS / 32][NSLOT];
-    __shared__ unsigned long long smk[8 * 16];
+    __shared__ unsigned long long tk_list[8 * 16], tk_scr[8 * 32];
     const uint32_t l = threadIdx.x & 31u, w = threadIdx.x >> 5;
     const int nbits = a.n - BLOCK_BITS;
     if (threadIdx.x == 0) {
         mbar_init(&mbar, 1);
         mbar_init(&mbarc, 1);
     }
+    if (threadIdx.x < 8 * 16) tk_list[threadIdx.x] = 0ull;
     __syncthreads();
     uint32_t parity = 0, parc = 0;
     if (threadIdx.x == 0 && (int)blockIdx.x < nunits) {
@@ -235,7 +236,7 @@ __global__ void __launch_bounds__(PASS_THREADS, 1)
         }
         if (a.ktop > 0) {
             const size_t xthread = base + goff<T>(local_idx<T, 1>(l, 0u, w), a.loA, a.loB);
-            block_topk<T, 1>(v, xthread, a.loA, a.loB, a.ktop, a.topk_keys + (size_t)un.b * a.ktop, smk);
+            warp_topk_running<T, 1>(v, xthread, a.loA, a.loB, a.ktop, tk_list + w * 16, tk_scr + w * 32);
         }
         const float x1 = xterm_pq<T, 1>(P, Q, a.mask);
         round_mix_pq<T, 1>(P, Q, -sc.pre_t, a.mask);
@@ -253,6 +254,9 @@ __global__ void __launch_bounds__(PASS_THREADS, 1)
         block_sum_write(vals, red, a.partials, u);
         __syncthreads();
     }
+    // one top-K list per warp: topk_keys[(CTA * 8 + warp) * K ..]
+    if (a.ktop > 0 && (int)l < a.ktop)
+        a.topk_keys[((size_t)blockIdx.x * (PASS_THREADS / 32) + w) * a.ktop + l] = tk_list[w * 16 + l];
 }
 
 // ---------------------------------------------------------------------------

@@ -99,43 +99,53 @@ __device__ __forceinline__ void transpose2(float2 (&v)[32], float2 (&u)[32], flo
     }
 }
 
-// Top-K (K <= 16) of the block's |psi|^2 by key (P desc, index asc):
-// key = (bits(P) << 33) | (2^33 - 1 - x); keys are unique since x is.
-// Writes K keys to out (global), using smk (shared, >= 8*16 keys).
+// Top-K keys of |psi|^2 (P desc, index asc): key = (bits(P) << 33) | (2^33 - 1 - x),
+// unique since x is.
+// Running top-K (K <= 16) of one warp over the units a persistent CTA visits.
+// list (shared, K keys, descending, 0 = empty) holds the warp's best keys so
+// far; a unit's amplitudes are ranked only if one of them can still enter the
+// list (P not below the list's K-th), which after the first few units is rare.
+// scratch: shared, 2K keys.  The union of the warps' lists contains the top K
+// of everything the CTA saw, whatever the order of the units.
 template <int T, int A>
-__device__ __forceinline__ void block_topk(const float2 (&v)[32], size_t xthread, int loA, int loB, int K,
-                                           unsigned long long *out, unsigned long long *smk) {
-    const uint32_t l = threadIdx.x & 31, w = threadIdx.x >> 5;
+__device__ __forceinline__ void warp_topk_running(const float2 (&v)[32], size_t xthread, int loA, int loB, int K,
+                                                  unsigned long long *list, unsigned long long *scratch) {
+    const uint32_t l = threadIdx.x & 31;
+    const uint32_t tp = (uint32_t)(list[K - 1] >> 33);
     uint32_t taken = 0;
-    // this thread's best and second-best remaining keys: a thread rescans its
-    // 32 amplitudes only when it wins a second time after its last scan
-    unsigned long long bk = 0, sk = 0;
-    int bm = -1, sm = -1;
-    // x grows with m inside a thread, so among equal probabilities the first
-    // m seen has the smaller index; P >= 0 orders like its bit pattern
-    auto key_of = [&](uint32_t pbits, int m) {
-        const unsigned long long x = xthread + goff<T>(local_idx<T, A>(0u, (uint32_t)m, 0u), loA, loB);
-        return ((unsigned long long)pbits << 33) | (0x1FFFFFFFFull - x);
-    };
+#pragma unroll
+    for (int m = 0; m < 32; ++m) {
+        const uint32_t p = __float_as_uint(fmaf(v[m].x, v[m].x, v[m].y * v[m].y));
+        if (p < tp) taken |= 1u << m;
+    }
+    if (!__any_sync(0xffffffffu, taken != 0xFFFFFFFFu)) return;
+    unsigned long long bk = 0;
+    int bm = -1;
     auto scan = [&]() {
-        uint32_t bp = 0, sp = 0;
-        bm = sm = -1;
+        uint32_t bp[4] = {0u, 0u, 0u, 0u};
+        int bj[4] = {-1, -1, -1, -1};
 #pragma unroll
         for (int m = 0; m < 32; ++m) {
             if ((taken >> m) & 1u) continue;
-            const uint32_t pb = __float_as_uint(fmaf(v[m].x, v[m].x, v[m].y * v[m].y));
-            if (bm < 0 || pb > bp) {
-                sp = bp;
-                sm = bm;
-                bp = pb;
-                bm = m;
-            } else if (sm < 0 || pb > sp) {
-                sp = pb;
-                sm = m;
+            const uint32_t p = __float_as_uint(fmaf(v[m].x, v[m].x, v[m].y * v[m].y));
+            if (bj[m & 3] < 0 || p > bp[m & 3]) {
+                bp[m & 3] = p;
+                bj[m & 3] = m;
             }
         }
-        bk = bm >= 0 ? key_of(bp, bm) : 0ull;
-        sk = sm >= 0 ? key_of(sp, sm) : 0ull;
+        uint32_t b = bp[0];
+        bm = bj[0];
+#pragma unroll
+        for (int j = 1; j < 4; ++j)
+            if (bj[j] >= 0 && (bm < 0 || bp[j] > b || (bp[j] == b && bj[j] < bm))) {
+                b = bp[j];
+                bm = bj[j];
+            }
+        bk = 0ull;
+        if (bm >= 0) {
+            const unsigned long long x = xthread + goff<T>(local_idx<T, A>(0u, (uint32_t)bm, 0u), loA, loB);
+            bk = ((unsigned long long)b << 33) | (0x1FFFFFFFFull - x);
+        }
     };
     scan();
     for (int r = 0; r < K; ++r) {
@@ -145,35 +155,20 @@ __device__ __forceinline__ void block_topk(const float2 (&v)[32], size_t xthread
             const unsigned long long t = __shfl_xor_sync(0xffffffffu, wb, o);
             wb = t > wb ? t : wb;
         }
-        if (l == 0) smk[w * 16 + r] = wb;
+        if (l == 0) scratch[r] = wb;
         if (bk == wb && bm >= 0) {
             taken |= 1u << bm;
-            if (sm >= 0) {
-                bk = sk;
-                bm = sm;
-                sk = 0;
-                sm = -1;
-            } else {
-                scan();
-            }
+            scan();
         }
     }
-    __syncthreads();
-    if (w == 0) {
-        // merge the 8 sorted warp lists: lane i (< 8) walks list i
-        int head = 0;
-        for (int r = 0; r < K; ++r) {
-            unsigned long long mine = (l < 8 && head < K) ? smk[l * 16 + head] : 0ull;
-            unsigned long long wb = mine;
-#pragma unroll
-            for (int o = 16; o; o >>= 1) {
-                const unsigned long long t = __shfl_xor_sync(0xffffffffu, wb, o);
-                wb = t > wb ? t : wb;
-            }
-            if (mine == wb && l < 8) ++head;
-            if (l == 0) out[r] = wb;
-        }
+    __syncwarp();
+    if (l == 0) {
+        // merge the two descending lists into scratch[K..2K), then back
+        int i = 0, j = 0;
+        for (int r = 0; r < K; ++r) scratch[K + r] = list[i] >= scratch[j] ? list[i++] : scratch[j++];
+        for (int r = 0; r < K; ++r) list[r] = scratch[K + r];
     }
+    __syncwarp();
 }
 
 // Read 32 amplitudes of arrangement A from a TMA-staged block (natural local
