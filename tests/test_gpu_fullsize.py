@@ -241,3 +241,48 @@ def test_uc32_properties_and_fd(q):
     q.qaoa_cost_destroy(cost)
     q.qaoa_ctx_destroy(ctx)
     gc.collect()
+
+
+def test_block_separable_n33_maximum_size(q):
+    """The largest supported state (n=33: 64 GiB of amplitudes, a 32 GiB
+    table): gradient (uncompute sweep, 224 GiB with the interleaved buffer)
+    and sampled amplitudes of an uncoupled three-block QUBO against the
+    oracle on each 11-variable block."""
+    blocks = [inst.upper_int_qubo(11, 1033 + k, lo=-3, hi=3) for k in range(3)]
+    g, b = inst.ramp_angles(2, gamma_scale=0.2)
+    Qb = inst.block_diagonal_qubo(blocks)
+    n = Qb.n
+    Fs = [oracle.cost_table(oracle.canonical_of(B)) for B in blocks]
+    grads = [oracle.grad_adjoint(Fb, g, b) for Fb in Fs]
+    psis = [oracle.evolve(Fb, g, b) for Fb in Fs]
+    Eo = sum(r[0] for r in grads)
+    dgo = sum(r[1] for r in grads)
+    dbo = sum(r[2] for r in grads)
+    fmax = sum(np.max(np.abs(Fb)) for Fb in Fs)
+    ctx = q.qaoa_ctx_create(0)
+    cost = _cost(q, ctx, Qb)
+    E, dg, db = q.qaoa_grad(ctx, cost, g, b)
+    assert abs(E - Eo) / fmax <= E_TOL
+    assert _grad_err(dg, db, dgo, dbo) <= G_TOL
+    q.qaoa_cost_destroy(cost)
+    q.qaoa_ctx_destroy(ctx)
+    gc.collect()
+    ctx = q.qaoa_ctx_create(0)
+    cost = _cost(q, ctx, Qb)
+    st = q.qaoa_forward(ctx, cost, g, b)
+    assert abs(q.qaoa_expect(ctx, cost, st) - Eo) / fmax <= E_TOL
+    rng = inst.SplitMix64(33)
+    xs = np.array([rng.next_u64() >> (64 - n) for _ in range(2048)], dtype=np.uint64)
+    got = q.qaoa_state_gather(ctx, st, xs).astype(np.complex128)
+    ref = np.ones(xs.size, dtype=np.complex128)
+    off = 0
+    for B, pb in zip(blocks, psis):
+        ref *= pb[(xs >> np.uint64(off)) & np.uint64((1 << B.n) - 1)]
+        off += B.n
+    assert np.linalg.norm(got - ref) * math.sqrt(2.0 ** n / xs.size) <= 1e-5
+    tk = q.qaoa_topk(ctx, cost, st, 4)
+    assert np.all(np.diff(tk["prob"]) <= 0)
+    q.qaoa_state_destroy(st)
+    q.qaoa_cost_destroy(cost)
+    q.qaoa_ctx_destroy(ctx)
+    gc.collect()

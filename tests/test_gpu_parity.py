@@ -362,6 +362,23 @@ def test_error_paths(q, ctx):
     with pytest.raises(q.QaoaError) as e:
         q.qaoa_build_cost(ctx, np.full((3, 3), 2 ** 30), None, 0.0, "i32")
     assert e.value.status == q.QAOA_ERR_RANGE
+    # batch, optimiser, gather, tuner and option arguments
+    with pytest.raises(q.QaoaError):
+        q.qaoa_grad_batch(ctx, [cost], np.zeros((0, 2)), np.zeros((0, 2)))
+    with pytest.raises(q.QaoaError):
+        q.qaoa_grad_batch(ctx, [cost], np.zeros((2, 1)), np.zeros((2, 1)), item_cost=[0, 3])
+    with pytest.raises(q.QaoaError):
+        q.qaoa_optimize_adam(ctx, [cost], np.zeros((1, 2)), np.zeros((1, 2)), 0)
+    with pytest.raises(q.QaoaError):
+        q.qaoa_state_gather(ctx, st, [1 << 14])
+    small = _cost(q, ctx, inst.upper_int_qubo(8, 2))
+    with pytest.raises(q.QaoaError):
+        q.qaoa_autotune(ctx, small, 2)
+    q.qaoa_cost_destroy(small)
+    for kw in ({"adjoint_mode": 3}, {"table_build": 2}, {"max_fused_qubits": 11}, {"max_fused_qubits": 2}):
+        with pytest.raises(q.QaoaError) as e:
+            q.qaoa_ctx_create(0, **kw)
+        assert e.value.status == q.QAOA_ERR_INVALID_ARG
     q.qaoa_state_destroy(st)
     q.qaoa_cost_destroy(cost)
     q.qaoa_cost_destroy(cost2)
