@@ -170,7 +170,7 @@ __device__ __forceinline__ void issue_table(uint32_t u, const PassArgs &a, const
 // RX_G on (psi, lambda) and write the interleaved (psi_in, lambda_in).
 // slots: 0 = sum P T, 1 = sum P, 2 = X-term (Y), 3 = X-term (X)
 // ---------------------------------------------------------------------------
-template <int T>
+template <int T, bool SPLIT, bool TOPK>
 __global__ void __launch_bounds__(PASS_THREADS, 1)
     final_pass_kernel(const PassArgs a, const __grid_constant__ CUtensorMap mpsi,
                       const __grid_constant__ CUtensorMap mcost, int nunits, unsigned int *status) {
@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(PASS_THREADS, 1)
             P[m] = make_float2(v[m].x, v[m].x * lf);
             Q[m] = make_float2(v[m].y, v[m].y * lf);
         }
-        if (a.ktop > 0) {
+        if (TOPK) {
             const size_t xthread = base + goff<T>(local_idx<T, 1>(l, 0u, w), a.loA, a.loB);
             warp_topk_running<T, 1>(v, xthread, a.loA, a.loB, a.ktop, tk_list + w * 16, tk_scr + w * 32);
         }
@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(PASS_THREADS, 1)
         round_mix_pq<T, 0>(P, Q, -sc.pre_t, a.mask);
 #pragma unroll
         for (int m = 0; m < 32; ++m) cmul_pq(P[m], Q[m], sc.kend2);
-        if (a.split)
+        if (SPLIT)
             store_lam<T, 0>(P, Q, a.lam + ((size_t)un.item << a.n) + base, l, w, a.loA, a.loB);
         else
             store_pq<T, 0>(P, Q, a.pl + ((size_t)un.item << a.n) + base, l, w, a.loA, a.loB);
@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(PASS_THREADS, 1)
         __syncthreads();
     }
     // one top-K list per warp: topk_keys[(CTA * 8 + warp) * K ..]
-    if (a.ktop > 0 && (int)l < a.ktop)
+    if (TOPK && (int)l < a.ktop)
         a.topk_keys[((size_t)blockIdx.x * (PASS_THREADS / 32) + w) * a.ktop + l] = tk_list[w * 16 + l];
 }
 
@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(PASS_THREADS, 1)
 // (psi, lambda).  slots: 0,1 = X-terms of the post mixer (arrangements X, Y);
 // 2 = cost term; 3,4 = X-terms of the pre mixer (Y, X).
 // ---------------------------------------------------------------------------
-template <int T, bool SPLIT>
+template <int T, bool SPLIT, bool PRE, bool COST, bool POST, bool STORE>
 __global__ void __launch_bounds__(PASS_THREADS, 1)
     rev_pass_kernel(const PassArgs a, const __grid_constant__ CUtensorMap mpl,
                     const __grid_constant__ CUtensorMap mcost, int nunits, unsigned int *status) {
@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(PASS_THREADS, 1)
     __shared__ double red[PASS_THREADS / 32][NSLOT];
     const uint32_t l = threadIdx.x & 31u, w = threadIdx.x >> 5;
     const int nbits = a.n - BLOCK_BITS;
-    const bool pre = a.has_pre, post = a.has_post;
+    constexpr bool pre = PRE, post = POST;
     if (threadIdx.x == 0) {
         mbar_init(&mbar, 1);
         mbar_init(&mbarc, 1);
@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(PASS_THREADS, 1)
     uint32_t parity = 0, parc = 0;
     if (threadIdx.x == 0 && (int)blockIdx.x < nunits) {
         issue_amps<T, true>(blockIdx.x, a, &mpl, stage, &mbar);
-        if (a.has_cost) issue_table<T>(blockIdx.x, a, &mcost, cstage, &mbarc);
+        if (COST) issue_table<T>(blockIdx.x, a, &mcost, cstage, &mbarc);
     }
     for (uint32_t u = blockIdx.x; (int)u < nunits; u += gridDim.x) {
         const Unit un = unit_of(u, nbits);
@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(PASS_THREADS, 1)
             acc[1] = xterm_pq<T, 1>(P, Q, a.mask);
             round_mix_pq<T, 1>(P, Q, -sc.post_t, a.mask);
         }
-        if (a.has_cost) {
+        if (COST) {
             int32_t c[32];
             if (!stage_ready(&mbarc, parc, status)) return;
             parc ^= 1u;
@@ -340,16 +340,16 @@ __global__ void __launch_bounds__(PASS_THREADS, 1)
             transpose1<T, 1, 0>(Q, xbuf, l, w, fa);
             acc[4] = xterm_pq<T, 0>(P, Q, a.mask);
             round_mix_pq<T, 0>(P, Q, -sc.pre_t, a.mask);
-            if (a.store) {
-                if (!a.has_cost) {
+            if (STORE) {
+                if (!COST) {
 #pragma unroll
                     for (int m = 0; m < 32; ++m) cmul_pq(P[m], Q[m], sc.kend);
                 }
                 if (SPLIT) store_lam<T, 0>(P, Q, a.lam + ((size_t)un.item << a.n) + base, l, w, a.loA, a.loB);
                 else store_pq<T, 0>(P, Q, dst, l, w, a.loA, a.loB);
             }
-        } else if (a.store) {
-            if (!a.has_cost) {
+        } else if (STORE) {
+            if (!COST) {
 #pragma unroll
                 for (int m = 0; m < 32; ++m) cmul_pq(P[m], Q[m], sc.kend);
             }
@@ -483,6 +483,15 @@ static cudaError_t set_smem(K kern, int bytes) {
     return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
+template <int T, bool SPLIT, bool TOPK>
+static cudaError_t final_launch(const PassArgs &a, const CUtensorMap &m, const CUtensorMap &mc, int grid, int nunits,
+                                int smem, unsigned int *status, cudaStream_t st) {
+    cudaError_t e = set_smem(final_pass_kernel<T, SPLIT, TOPK>, smem);
+    if (e) return e;
+    final_pass_kernel<T, SPLIT, TOPK><<<grid, PASS_THREADS, smem, st>>>(a, m, mc, nunits, status);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_final_pass(int type, const PassArgs &a, int grid, unsigned int *status, cudaStream_t st) {
     const int nunits = a.nitems << (a.n - BLOCK_BITS);
     const int smem = 65536 + 32768 + 65536;
@@ -495,14 +504,50 @@ cudaError_t launch_final_pass(int type, const PassArgs &a, int grid, unsigned in
         if ((e = make_block_map(&mc, a.C, a.n, a.loA, a.loB, 4, a.ntables))) return e;
     }
     if (grid > nunits) grid = nunits;
-    if (type == 0) {
-        if ((e = set_smem(final_pass_kernel<0>, smem))) return e;
-        final_pass_kernel<0><<<grid, PASS_THREADS, smem, st>>>(a, m, mc, nunits, status);
-    } else {
-        if ((e = set_smem(final_pass_kernel<1>, smem))) return e;
-        final_pass_kernel<1><<<grid, PASS_THREADS, smem, st>>>(a, m, mc, nunits, status);
+    const int key = (type ? 4 : 0) | (a.split ? 2 : 0) | (a.ktop > 0 ? 1 : 0);
+    switch (key) {
+        case 0: return final_launch<0, false, false>(a, m, mc, grid, nunits, smem, status, st);
+        case 1: return final_launch<0, false, true>(a, m, mc, grid, nunits, smem, status, st);
+        case 2: return final_launch<0, true, false>(a, m, mc, grid, nunits, smem, status, st);
+        case 3: return final_launch<0, true, true>(a, m, mc, grid, nunits, smem, status, st);
+        case 4: return final_launch<1, false, false>(a, m, mc, grid, nunits, smem, status, st);
+        case 5: return final_launch<1, false, true>(a, m, mc, grid, nunits, smem, status, st);
+        case 6: return final_launch<1, true, false>(a, m, mc, grid, nunits, smem, status, st);
+        default: return final_launch<1, true, true>(a, m, mc, grid, nunits, smem, status, st);
     }
+}
+
+template <int T, bool SPLIT, bool PRE, bool COST, bool POST, bool STORE>
+static cudaError_t rev_launch(const PassArgs &a, const CUtensorMap &m, const CUtensorMap &mc, int grid, int nunits,
+                              int smem, unsigned int *status, cudaStream_t st) {
+    cudaError_t e = set_smem(rev_pass_kernel<T, SPLIT, PRE, COST, POST, STORE>, smem);
+    if (e) return e;
+    rev_pass_kernel<T, SPLIT, PRE, COST, POST, STORE><<<grid, PASS_THREADS, smem, st>>>(a, m, mc, nunits, status);
     return cudaGetLastError();
+}
+
+// One instantiation per pass shape the schedules produce: a cost-layer pass
+// (mixer, cost, mixer), the first pass (cost, mixer; nothing to store) and,
+// without stored states, a mixer-only pass.
+template <int T, bool SPLIT>
+static cudaError_t rev_shape(const PassArgs &a, const CUtensorMap &m, const CUtensorMap &mc, int grid, int nunits,
+                             int smem, unsigned int *status, cudaStream_t st) {
+    const int key = (a.has_pre ? 8 : 0) | (a.has_cost ? 4 : 0) | (a.has_post ? 2 : 0) | (a.store ? 1 : 0);
+    switch (key) {
+        case 15: return rev_launch<T, SPLIT, true, true, true, true>(a, m, mc, grid, nunits, smem, status, st);
+        case 6: return rev_launch<T, SPLIT, false, true, true, false>(a, m, mc, grid, nunits, smem, status, st);
+        case 3: return rev_launch<T, SPLIT, false, false, true, true>(a, m, mc, grid, nunits, smem, status, st);
+        default: return cudaErrorInvalidValue;  // no schedule produces another shape
+    }
+}
+
+static cudaError_t rev_dispatch(int type, const PassArgs &a, const CUtensorMap &m, const CUtensorMap &mc, int grid,
+                                int nunits, int smem, unsigned int *status, cudaStream_t st) {
+    if (type == 0)
+        return a.split ? rev_shape<0, true>(a, m, mc, grid, nunits, smem, status, st)
+                       : rev_shape<0, false>(a, m, mc, grid, nunits, smem, status, st);
+    return a.split ? rev_shape<1, true>(a, m, mc, grid, nunits, smem, status, st)
+                   : rev_shape<1, false>(a, m, mc, grid, nunits, smem, status, st);
 }
 
 cudaError_t launch_rev_pass(int type, const PassArgs &a, int grid, unsigned int *status, cudaStream_t st) {
@@ -517,20 +562,7 @@ cudaError_t launch_rev_pass(int type, const PassArgs &a, int grid, unsigned int 
         if (a.has_cost && (e = make_block_map(&mc, a.C, a.n, a.loA, a.loB, 4, a.ntables))) return e;
     }
     if (grid > nunits) grid = nunits;
-    if (type == 0 && !a.split) {
-        if ((e = set_smem(rev_pass_kernel<0, false>, smem))) return e;
-        rev_pass_kernel<0, false><<<grid, PASS_THREADS, smem, st>>>(a, m, mc, nunits, status);
-    } else if (type == 0) {
-        if ((e = set_smem(rev_pass_kernel<0, true>, smem))) return e;
-        rev_pass_kernel<0, true><<<grid, PASS_THREADS, smem, st>>>(a, m, mc, nunits, status);
-    } else if (!a.split) {
-        if ((e = set_smem(rev_pass_kernel<1, false>, smem))) return e;
-        rev_pass_kernel<1, false><<<grid, PASS_THREADS, smem, st>>>(a, m, mc, nunits, status);
-    } else {
-        if ((e = set_smem(rev_pass_kernel<1, true>, smem))) return e;
-        rev_pass_kernel<1, true><<<grid, PASS_THREADS, smem, st>>>(a, m, mc, nunits, status);
-    }
-    return cudaGetLastError();
+    return rev_dispatch(type, a, m, mc, grid, nunits, smem, status, st);
 }
 
 cudaError_t launch_rev_mid(int type, const PassArgs &a, cudaStream_t st) {
