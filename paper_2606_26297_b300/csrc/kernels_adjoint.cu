@@ -170,11 +170,12 @@ __device__ __forceinline__ void issue_table(uint32_t u, const PassArgs &a, const
 // RX_G on (psi, lambda) and write the interleaved (psi_in, lambda_in).
 // slots: 0 = sum P T, 1 = sum P, 2 = X-term (Y), 3 = X-term (X)
 // ---------------------------------------------------------------------------
-template <int T, bool SPLIT, bool TOPK>
+template <int T, bool SPLIT, bool TOPK, bool FULL>
 __global__ void __launch_bounds__(PASS_THREADS, 1)
     final_pass_kernel(const PassArgs a, const __grid_constant__ CUtensorMap mpsi,
                       const __grid_constant__ CUtensorMap mcost, int nunits, unsigned int *status) {
     extern __shared__ __align__(1024) unsigned char smraw[];
+    const uint32_t mask = FULL ? full_mask<T>() : a.mask;
     float2 *stage = reinterpret_cast<float2 *>(smraw);                 // psi block, 64 KB
     int32_t *cstage = reinterpret_cast<int32_t *>(smraw + 65536);      // table block, 32 KB
     float2 *xbuf = reinterpret_cast<float2 *>(smraw + 65536 + 32768);  // transposes, 64 KB
@@ -197,7 +198,7 @@ __global__ void __launch_bounds__(PASS_THREADS, 1)
     for (uint32_t u = blockIdx.x; (int)u < nunits; u += gridDim.x) {
         const Unit un = unit_of(u, nbits);
         const PassScal sc = a.scal[un.item];
-        const uint32_t fm = sc.pre_flip ? a.mask : 0u;
+        const uint32_t fm = sc.pre_flip ? mask : 0u;
         const size_t base = block_base<T>(un.b, a.loA, a.loB);
         float2 v[32];
         if (!stage_ready(&mbar, parity, status)) return;
@@ -208,9 +209,9 @@ __global__ void __launch_bounds__(PASS_THREADS, 1)
             fence_proxy_async();
             issue_amps<T, false>(u + gridDim.x, a, &mpsi, stage, &mbar);
         }
-        round_mix<T, 0>(v, sc.pre_t, a.mask);
+        round_mix<T, 0>(v, sc.pre_t, mask);
         transpose1<T, 0, 1>(v, xbuf, l, w, fm);
-        round_mix<T, 1>(v, sc.pre_t, a.mask);
+        round_mix<T, 1>(v, sc.pre_t, mask);
         int32_t c[32];
         if (!stage_ready(&mbarc, parc, status)) return;
         parc ^= 1u;
@@ -238,12 +239,12 @@ __global__ void __launch_bounds__(PASS_THREADS, 1)
             const size_t xthread = base + goff<T>(local_idx<T, 1>(l, 0u, w), a.loA, a.loB);
             warp_topk_running<T, 1>(v, xthread, a.loA, a.loB, a.ktop, tk_list + w * 16, tk_scr + w * 32);
         }
-        const float x1 = xterm_pq<T, 1>(P, Q, a.mask);
-        round_mix_pq<T, 1>(P, Q, -sc.pre_t, a.mask);
+        const float x1 = xterm_pq<T, 1>(P, Q, mask);
+        round_mix_pq<T, 1>(P, Q, -sc.pre_t, mask);
         transpose1<T, 1, 0>(P, xbuf, l, w, fm);
         transpose1<T, 1, 0>(Q, xbuf, l, w, fm);
-        const float x0 = xterm_pq<T, 0>(P, Q, a.mask);
-        round_mix_pq<T, 0>(P, Q, -sc.pre_t, a.mask);
+        const float x0 = xterm_pq<T, 0>(P, Q, mask);
+        round_mix_pq<T, 0>(P, Q, -sc.pre_t, mask);
 #pragma unroll
         for (int m = 0; m < 32; ++m) cmul_pq(P[m], Q[m], sc.kend2);
         if (SPLIT)
@@ -264,11 +265,12 @@ __global__ void __launch_bounds__(PASS_THREADS, 1)
 // (psi, lambda).  slots: 0,1 = X-terms of the post mixer (arrangements X, Y);
 // 2 = cost term; 3,4 = X-terms of the pre mixer (Y, X).
 // ---------------------------------------------------------------------------
-template <int T, bool SPLIT, bool PRE, bool COST, bool POST, bool STORE>
+template <int T, bool SPLIT, bool PRE, bool COST, bool POST, bool STORE, bool FULL>
 __global__ void __launch_bounds__(PASS_THREADS, 1)
     rev_pass_kernel(const PassArgs a, const __grid_constant__ CUtensorMap mpl,
                     const __grid_constant__ CUtensorMap mcost, int nunits, unsigned int *status) {
     extern __shared__ __align__(1024) unsigned char smraw[];
+    const uint32_t mask = FULL ? full_mask<T>() : a.mask;
     float4 *stage = reinterpret_cast<float4 *>(smraw);                  // (psi, lambda) block, 128 KB
     int32_t *cstage = reinterpret_cast<int32_t *>(smraw + 131072);      // table block, 32 KB
     float2 *xbuf = reinterpret_cast<float2 *>(smraw + 131072 + 32768);  // transposes, 64 KB
@@ -290,7 +292,7 @@ __global__ void __launch_bounds__(PASS_THREADS, 1)
     for (uint32_t u = blockIdx.x; (int)u < nunits; u += gridDim.x) {
         const Unit un = unit_of(u, nbits);
         const PassScal sc = a.scal[un.item];
-        const uint32_t fa = sc.pre_flip ? a.mask : 0u, fb = sc.post_flip ? a.mask : 0u;
+        const uint32_t fa = sc.pre_flip ? mask : 0u, fb = sc.post_flip ? mask : 0u;
         const size_t base = block_base<T>(un.b, a.loA, a.loB);
         float2 P[32], Q[32];
         float acc[NSLOT] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -304,12 +306,12 @@ __global__ void __launch_bounds__(PASS_THREADS, 1)
             issue_amps<T, true>(u + gridDim.x, a, &mpl, stage, &mbar);
         }
         if (post) {
-            acc[0] = xterm_pq<T, 0>(P, Q, a.mask);
-            round_mix_pq<T, 0>(P, Q, -sc.post_t, a.mask);
+            acc[0] = xterm_pq<T, 0>(P, Q, mask);
+            round_mix_pq<T, 0>(P, Q, -sc.post_t, mask);
             transpose1<T, 0, 1>(P, xbuf, l, w, fb);
             transpose1<T, 0, 1>(Q, xbuf, l, w, fb);
-            acc[1] = xterm_pq<T, 1>(P, Q, a.mask);
-            round_mix_pq<T, 1>(P, Q, -sc.post_t, a.mask);
+            acc[1] = xterm_pq<T, 1>(P, Q, mask);
+            round_mix_pq<T, 1>(P, Q, -sc.post_t, mask);
         }
         if (COST) {
             int32_t c[32];
@@ -334,12 +336,12 @@ __global__ void __launch_bounds__(PASS_THREADS, 1)
         }
         float4 *dst = a.pl + ((size_t)un.item << a.n) + base;
         if (pre) {
-            acc[3] = xterm_pq<T, 1>(P, Q, a.mask);
-            round_mix_pq<T, 1>(P, Q, -sc.pre_t, a.mask);
+            acc[3] = xterm_pq<T, 1>(P, Q, mask);
+            round_mix_pq<T, 1>(P, Q, -sc.pre_t, mask);
             transpose1<T, 1, 0>(P, xbuf, l, w, fa);
             transpose1<T, 1, 0>(Q, xbuf, l, w, fa);
-            acc[4] = xterm_pq<T, 0>(P, Q, a.mask);
-            round_mix_pq<T, 0>(P, Q, -sc.pre_t, a.mask);
+            acc[4] = xterm_pq<T, 0>(P, Q, mask);
+            round_mix_pq<T, 0>(P, Q, -sc.pre_t, mask);
             if (STORE) {
                 if (!COST) {
 #pragma unroll
@@ -402,15 +404,16 @@ __device__ __forceinline__ float xterm_stream(const float2 (&v)[32], const float
     return s0 + s1;
 }
 
-template <int T, bool PLOUT>
+template <int T, bool PLOUT, bool FULL>
 __global__ void __launch_bounds__(PASS_THREADS, 2) rev_mid_kernel(const PassArgs a) {
     extern __shared__ __align__(16) float2 sm[];
+    const uint32_t mask = FULL ? full_mask<T>() : a.mask;
     __shared__ double red[PASS_THREADS / 32][NSLOT];
     const uint32_t l = threadIdx.x & 31u, w = threadIdx.x >> 5;
     const int nbits = a.n - BLOCK_BITS;
     const uint32_t item = blockIdx.x >> nbits, b = blockIdx.x & ((1u << nbits) - 1u);
     const PassScal sc = a.scal[item];
-    const uint32_t fb = sc.post_flip ? a.mask : 0u;
+    const uint32_t fb = sc.post_flip ? mask : 0u;
     const size_t base = block_base<T>(b, a.loA, a.loB);
     float2 *lp = a.lam + ((size_t)item << a.n) + base;
     const float2 *pp = a.psi_src + ((size_t)item << a.n) + base;
@@ -422,18 +425,18 @@ __global__ void __launch_bounds__(PASS_THREADS, 2) rev_mid_kernel(const PassArgs
     }
     float2 v[32];
     load_arr<T, 0>(v, lp, l, w, a.loA, a.loB);
-    round_mix<T, 0>(v, -sc.post_t, a.mask);
+    round_mix<T, 0>(v, -sc.post_t, mask);
     transpose1<T, 0, 1>(v, sm, l, w, fb);
-    round_mix<T, 1>(v, -sc.post_t, a.mask);
+    round_mix<T, 1>(v, -sc.post_t, mask);
 #pragma unroll
     for (int m = 0; m < 32; ++m) v[m] = cmul(v[m], sc.kend);
     // lambda_in: interleaved with psi_in for a following reverse pass that
     // undoes a cost layer (it uncomputes psi), else alone
     float4 *plo = a.pl + ((size_t)item << a.n) + base;
-    const float xy = xterm_stream<T, 1, false>(v, pp, plo, l, w, a.loA, a.loB, a.mask);
+    const float xy = xterm_stream<T, 1, false>(v, pp, plo, l, w, a.loA, a.loB, mask);
     if (!PLOUT) store_arr<T, 1>(v, lp, l, w, a.loA, a.loB);
     transpose1<T, 1, 0>(v, sm, l, w, 0u);
-    const float xx = xterm_stream<T, 0, PLOUT>(v, pp, plo, l, w, a.loA, a.loB, a.mask);
+    const float xx = xterm_stream<T, 0, PLOUT>(v, pp, plo, l, w, a.loA, a.loB, mask);
     double vals[NSLOT] = {(double)xy, (double)xx, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     block_sum_write(vals, red, a.partials, blockIdx.x);
 }
@@ -483,13 +486,20 @@ static cudaError_t set_smem(K kern, int bytes) {
     return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
+template <int T, bool SPLIT, bool TOPK, bool FULL>
+static cudaError_t final_launch_f(const PassArgs &a, const CUtensorMap &m, const CUtensorMap &mc, int grid,
+                                  int nunits, int smem, unsigned int *status, cudaStream_t st) {
+    cudaError_t e = set_smem(final_pass_kernel<T, SPLIT, TOPK, FULL>, smem);
+    if (e) return e;
+    final_pass_kernel<T, SPLIT, TOPK, FULL><<<grid, PASS_THREADS, smem, st>>>(a, m, mc, nunits, status);
+    return cudaGetLastError();
+}
+
 template <int T, bool SPLIT, bool TOPK>
 static cudaError_t final_launch(const PassArgs &a, const CUtensorMap &m, const CUtensorMap &mc, int grid, int nunits,
                                 int smem, unsigned int *status, cudaStream_t st) {
-    cudaError_t e = set_smem(final_pass_kernel<T, SPLIT, TOPK>, smem);
-    if (e) return e;
-    final_pass_kernel<T, SPLIT, TOPK><<<grid, PASS_THREADS, smem, st>>>(a, m, mc, nunits, status);
-    return cudaGetLastError();
+    return a.mask == full_mask<T>() ? final_launch_f<T, SPLIT, TOPK, true>(a, m, mc, grid, nunits, smem, status, st)
+                                    : final_launch_f<T, SPLIT, TOPK, false>(a, m, mc, grid, nunits, smem, status, st);
 }
 
 cudaError_t launch_final_pass(int type, const PassArgs &a, int grid, unsigned int *status, cudaStream_t st) {
@@ -517,13 +527,22 @@ cudaError_t launch_final_pass(int type, const PassArgs &a, int grid, unsigned in
     }
 }
 
+template <int T, bool SPLIT, bool PRE, bool COST, bool POST, bool STORE, bool FULL>
+static cudaError_t rev_launch_f(const PassArgs &a, const CUtensorMap &m, const CUtensorMap &mc, int grid, int nunits,
+                                int smem, unsigned int *status, cudaStream_t st) {
+    cudaError_t e = set_smem(rev_pass_kernel<T, SPLIT, PRE, COST, POST, STORE, FULL>, smem);
+    if (e) return e;
+    rev_pass_kernel<T, SPLIT, PRE, COST, POST, STORE, FULL><<<grid, PASS_THREADS, smem, st>>>(a, m, mc, nunits,
+                                                                                               status);
+    return cudaGetLastError();
+}
+
 template <int T, bool SPLIT, bool PRE, bool COST, bool POST, bool STORE>
 static cudaError_t rev_launch(const PassArgs &a, const CUtensorMap &m, const CUtensorMap &mc, int grid, int nunits,
                               int smem, unsigned int *status, cudaStream_t st) {
-    cudaError_t e = set_smem(rev_pass_kernel<T, SPLIT, PRE, COST, POST, STORE>, smem);
-    if (e) return e;
-    rev_pass_kernel<T, SPLIT, PRE, COST, POST, STORE><<<grid, PASS_THREADS, smem, st>>>(a, m, mc, nunits, status);
-    return cudaGetLastError();
+    return a.mask == full_mask<T>()
+               ? rev_launch_f<T, SPLIT, PRE, COST, POST, STORE, true>(a, m, mc, grid, nunits, smem, status, st)
+               : rev_launch_f<T, SPLIT, PRE, COST, POST, STORE, false>(a, m, mc, grid, nunits, smem, status, st);
 }
 
 // One instantiation per pass shape the schedules produce: a cost-layer pass
@@ -565,24 +584,24 @@ cudaError_t launch_rev_pass(int type, const PassArgs &a, int grid, unsigned int 
     return rev_dispatch(type, a, m, mc, grid, nunits, smem, status, st);
 }
 
-cudaError_t launch_rev_mid(int type, const PassArgs &a, cudaStream_t st) {
+template <int T, bool PLOUT, bool FULL>
+static cudaError_t mid_launch_f(const PassArgs &a, cudaStream_t st) {
     const unsigned grid = (unsigned)a.nitems << (a.n - BLOCK_BITS);
     const int smem = 8192 * (int)sizeof(float2);
-    cudaError_t e;
-    if (type == 0 && a.pl_out) {
-        if ((e = set_smem(rev_mid_kernel<0, true>, smem))) return e;
-        rev_mid_kernel<0, true><<<grid, PASS_THREADS, smem, st>>>(a);
-    } else if (type == 0) {
-        if ((e = set_smem(rev_mid_kernel<0, false>, smem))) return e;
-        rev_mid_kernel<0, false><<<grid, PASS_THREADS, smem, st>>>(a);
-    } else if (a.pl_out) {
-        if ((e = set_smem(rev_mid_kernel<1, true>, smem))) return e;
-        rev_mid_kernel<1, true><<<grid, PASS_THREADS, smem, st>>>(a);
-    } else {
-        if ((e = set_smem(rev_mid_kernel<1, false>, smem))) return e;
-        rev_mid_kernel<1, false><<<grid, PASS_THREADS, smem, st>>>(a);
-    }
+    cudaError_t e = set_smem(rev_mid_kernel<T, PLOUT, FULL>, smem);
+    if (e) return e;
+    rev_mid_kernel<T, PLOUT, FULL><<<grid, PASS_THREADS, smem, st>>>(a);
     return cudaGetLastError();
+}
+
+template <int T, bool PLOUT>
+static cudaError_t mid_launch(const PassArgs &a, cudaStream_t st) {
+    return a.mask == full_mask<T>() ? mid_launch_f<T, PLOUT, true>(a, st) : mid_launch_f<T, PLOUT, false>(a, st);
+}
+
+cudaError_t launch_rev_mid(int type, const PassArgs &a, cudaStream_t st) {
+    if (type == 0) return a.pl_out ? mid_launch<0, true>(a, st) : mid_launch<0, false>(a, st);
+    return a.pl_out ? mid_launch<1, true>(a, st) : mid_launch<1, false>(a, st);
 }
 
 }  // namespace qaoa

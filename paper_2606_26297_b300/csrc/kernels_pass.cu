@@ -13,8 +13,9 @@
 
 namespace qaoa {
 
-template <int T, bool INIT, bool PRE, bool COST, bool POST>
+template <int T, bool INIT, bool PRE, bool COST, bool POST, bool FULL>
 __global__ void __launch_bounds__(PASS_THREADS, 2) fwd_pass_kernel(const PassArgs a) {
+    const uint32_t mask = FULL ? full_mask<T>() : a.mask;
     extern __shared__ __align__(16) float2 sm[];
     const uint32_t l = threadIdx.x & 31u, w = threadIdx.x >> 5;
     const int nbits = a.n - BLOCK_BITS;
@@ -34,9 +35,9 @@ __global__ void __launch_bounds__(PASS_THREADS, 2) fwd_pass_kernel(const PassArg
         load_arr<T, 1>(v, pb, l, w, a.loA, a.loB);
     }
     if (PRE) {
-        round_mix<T, 0>(v, sc.pre_t, a.mask);
-        transpose1<T, 0, 1>(v, sm, l, w, sc.pre_flip ? a.mask : 0u);
-        round_mix<T, 1>(v, sc.pre_t, a.mask);
+        round_mix<T, 0>(v, sc.pre_t, mask);
+        transpose1<T, 0, 1>(v, sm, l, w, sc.pre_flip ? mask : 0u);
+        round_mix<T, 1>(v, sc.pre_t, mask);
     }
     // arrangement Y
     if (COST) {
@@ -46,9 +47,9 @@ __global__ void __launch_bounds__(PASS_THREADS, 2) fwd_pass_kernel(const PassArg
         for (int m = 0; m < 32; ++m) v[m] = cmul(v[m], cost_phase(c[m], sc.phi, sc.off, sc.kmag, a.precise_phase));
     }
     if (POST) {
-        round_mix<T, 1>(v, sc.post_t, a.mask);
-        transpose1<T, 1, 0>(v, sm, l, w, sc.post_flip ? a.mask : 0u);
-        round_mix<T, 0>(v, sc.post_t, a.mask);
+        round_mix<T, 1>(v, sc.post_t, mask);
+        transpose1<T, 1, 0>(v, sm, l, w, sc.post_flip ? mask : 0u);
+        round_mix<T, 0>(v, sc.post_t, mask);
         if (!COST) {
 #pragma unroll
             for (int m = 0; m < 32; ++m) v[m] = cmul(v[m], sc.kend);
@@ -126,15 +127,22 @@ __global__ void topk_merge_kernel(const unsigned long long *__restrict__ in, int
     }
 }
 
-template <int T, bool INIT, bool PRE, bool COST, bool POST>
-static cudaError_t fwd_launch(const PassArgs &a, cudaStream_t st) {
+template <int T, bool INIT, bool PRE, bool COST, bool POST, bool FULL>
+static cudaError_t fwd_launch_f(const PassArgs &a, cudaStream_t st) {
     const unsigned grid = (unsigned)a.nitems << (a.n - BLOCK_BITS);
     const int smem = 8192 * (int)sizeof(float2);
-    cudaError_t e = cudaFuncSetAttribute(fwd_pass_kernel<T, INIT, PRE, COST, POST>,
+    cudaError_t e = cudaFuncSetAttribute(fwd_pass_kernel<T, INIT, PRE, COST, POST, FULL>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e) return e;
-    fwd_pass_kernel<T, INIT, PRE, COST, POST><<<grid, PASS_THREADS, smem, st>>>(a);
+    fwd_pass_kernel<T, INIT, PRE, COST, POST, FULL><<<grid, PASS_THREADS, smem, st>>>(a);
     return cudaGetLastError();
+}
+
+// a full group (every register bit mixed) gets code without per-bit tests
+template <int T, bool INIT, bool PRE, bool COST, bool POST>
+static cudaError_t fwd_launch(const PassArgs &a, cudaStream_t st) {
+    return a.mask == full_mask<T>() ? fwd_launch_f<T, INIT, PRE, COST, POST, true>(a, st)
+                                    : fwd_launch_f<T, INIT, PRE, COST, POST, false>(a, st);
 }
 
 // One instantiation per pass shape (first pass, mixer only, cost layer, ...):

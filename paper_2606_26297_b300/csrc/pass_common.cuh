@@ -52,6 +52,13 @@ __device__ __forceinline__ constexpr uint32_t swz(uint32_t e) {
     return T == 0 ? (e ^ ((e >> 4) & 7u) ^ (((e >> 8) & 1u) << 3)) : (e ^ (((e >> 5) & 1u) << 3));
 }
 
+// Mixed-bit mask of a group that fills its block: type 0 bits 0..9, type 1
+// bits 3..12 (every register bit of both arrangements is then mixed).
+template <int T>
+__device__ __forceinline__ constexpr uint32_t full_mask() {
+    return T == 0 ? 0x3FFu : 0x1FF8u;
+}
+
 // Global element offset of local index e, relative to the block base.  Type 1:
 // local bits 0..2 -> global bits 0..2, local bits 3..7 -> loA.., 8..12 -> loB..
 template <int T>
