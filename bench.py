@@ -330,7 +330,12 @@ def run_workload(args):
       ragged   64 integer QUBOs with n in [10, 22], p=4, one request;
       uc32     unit-commitment QUBO n=32, p=6: `--iters` Adam steps on the
                exact gradient (CUDA graph);
-      autotune fusion widths 10..5 timed on the dense workload (--n, depth 2)."""
+      autotune fusion widths 10..5 timed on the dense workload (--n, depth 2);
+      sample   measurement of the dense workload's final state (--n, --p) with
+               `--shots` shots per request: weights pass (one read of the
+               state) and shot kernel timed with CUDA events;
+      spsa     SPSA-Adam with shots (Sec. 3.4): 16 starts on the n=20 integer
+               QUBO, p=4, 1024 shots per evaluation, `--iters` iterations."""
     import torch
     from paper_2606_26297_b300 import build_lib
     build_lib.build()
@@ -441,6 +446,51 @@ def run_workload(args):
                     "layer_evals_per_s": args.iters * p / dt, "E_start": float(hist[0, 0]),
                     "E_end": float(Ef[0]), "E_min_history": float(hist[:, 0].min())})
         q.qaoa_cost_destroy(cost)
+    elif args.workload == "sample":
+        Q, g, b = inst.workload_dense30(args.n, args.p)
+        pctx = q.qaoa_ctx_create(0, stream.cuda_stream, profile=True)
+        cost = q.qaoa_build_cost(pctx, Q.H, Q.f, Q.c0, "f32")
+        st = q.qaoa_forward(pctx, cost, g, b)
+        E = q.qaoa_expect(pctx, cost, st)
+        S = args.shots
+        for k in range(max(args.warmup, 1)):
+            q.qaoa_sample(pctx, cost, st, S, seed=1, stream=1000 + k, want_mean=True)
+        for kind in (6, 7):
+            q.qaoa_profile_read(pctx, kind, reset=True)
+        means = []
+        t, _ = _event_time(torch, stream, lambda: means.append(
+            q.qaoa_sample(pctx, cost, st, S, seed=1, stream=len(means), want_mean=True)[2]), args.steps)
+        w = q.qaoa_profile_read(pctx, 6)
+        sh = q.qaoa_profile_read(pctx, 7)
+        peak, peak_src = _peaks()
+        w_ms = w["ms"] / max(w["launches"], 1)
+        gbs = 8 * 2 ** args.n / (w_ms / 1e3) / 1e9
+        sh_ms = sh["ms"] / max(sh["launches"], 1)
+        res.update({"n": args.n, "p": args.p, "shots": S, "ms_per_request": 1e3 * t,
+                    "shots_per_s_end_to_end": S / t,
+                    "weights_ms": w_ms, "weights_GBps": gbs,
+                    "weights_frac_of_hbm": gbs / peak, "hbm_peak": f"{peak:g} GB/s ({peak_src})",
+                    "shot_kernel_ms": sh_ms, "shots_per_s_kernel": S / (sh_ms / 1e3),
+                    "exact_E": E, "sampled_mean_avg": float(np.mean(means)),
+                    "gpu_launches_per_request": 3})
+        q.qaoa_state_destroy(st)
+        q.qaoa_cost_destroy(cost)
+        q.qaoa_ctx_destroy(pctx)
+    elif args.workload == "spsa":
+        Q, G0, B0 = inst.workload_batch20()
+        cost = q.qaoa_build_cost(ctx, Q.H, Q.f, Q.c0, "i32")
+        G0, B0 = G0[:16], B0[:16]
+        p = G0.shape[1]
+        q.qaoa_optimize_spsa(ctx, [cost], G0, B0, 2, shots=1024, seed=5)
+        t0 = time.perf_counter()
+        g1, b1, hist, Ef = q.qaoa_optimize_spsa(ctx, [cost], G0, B0, args.iters, shots=1024, seed=5, lr=0.02)
+        dt = time.perf_counter() - t0
+        E0 = q.qaoa_grad_batch(ctx, [cost], G0, B0, grad=False)
+        res.update({"n": 20, "p": p, "starts": 16, "shots": 1024, "iters": args.iters,
+                    "ms_per_iteration": 1e3 * dt / args.iters,
+                    "evaluations_per_s": 32 * args.iters / dt,
+                    "mean_E_start": float(np.mean(E0)), "mean_E_end": float(np.mean(Ef))})
+        q.qaoa_cost_destroy(cost)
     print(json.dumps(res), flush=True)
     q.qaoa_ctx_destroy(ctx)
     return 0
@@ -455,9 +505,11 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--n", type=int, default=N_QUBITS, help="qubits (default: the n=30 workload)")
     ap.add_argument("--p", type=int, default=DEPTH, help="depth (default 8)")
-    ap.add_argument("--workload", default="", choices=["", "fd", "batch20", "ragged", "uc32", "autotune"],
+    ap.add_argument("--workload", default="",
+                    choices=["", "fd", "batch20", "ragged", "uc32", "autotune", "sample", "spsa"],
                     help="a secondary measurement instead of the headline step")
-    ap.add_argument("--iters", type=int, default=200, help="Adam steps for --workload batch20/uc32")
+    ap.add_argument("--iters", type=int, default=200, help="Adam steps for --workload batch20/uc32/spsa")
+    ap.add_argument("--shots", type=int, default=1 << 20, help="shots per request for --workload sample")
     args = ap.parse_args()
     if args.workload:
         return run_workload(args)

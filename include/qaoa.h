@@ -225,6 +225,88 @@ qaoa_status qaoa_optimize_adam(qaoa_ctx ctx, int nq, const qaoa_cost *costs, con
                                int B, int p, double *gamma, double *beta,
                                const qaoa_adam_options *opt, double *history, double *final_expect);
 
+/* ---- measurement by shots (Sec. 3.4 shot objective, Sec. 3.6 final evaluation) */
+
+/* A state handle holding `amps` (host, 2^n complex64 values, or complex128
+ * with fp64 = 1 and n <= 12), copied to the device.  1 <= n <= 33.  For
+ * measuring a state the caller made. */
+qaoa_status qaoa_state_from_host(qaoa_ctx ctx, int n, int fp64, const void *amps, qaoa_state *out);
+
+/* Measure `state` with `shots` shots (1 <= shots <= 2^34), the circuit
+ * execution whose counts Sec. 3.4 turns into the sampled mean cost and Sec.
+ * 3.6 into the final distribution.  Inverse-CDF sampling on exact integer
+ * weights: P_x = fl(re^2) + fl(im^2) in FP64, q_x = floor(P_x 2^60),
+ * Q = sum_x q_x; shot s with 64-bit random integer R_s lands on the smallest x
+ * whose prefix q_0 + ... + q_x exceeds floor(R_s Q / 2^64).  R_s = rand[s]
+ * (host array of `shots` integers) or, with rand = NULL, the counter-based
+ * Philox4x32-10 (Salmon et al., SC 2011): counter (s lo, s hi, stream lo,
+ * stream hi), key (seed lo, seed hi), R = out0 + 2^32 out1.
+ * Outputs (host, each may be NULL): idx[s] = x_s; cost_out[s] = F(x_s) from
+ * the cost table (needs `cost`, of the same n); *mean_cost = mean of F over
+ * the shots (needs `cost`), summed exactly in integers.  QAOA_ERR_RANGE if
+ * the state's total probability is outside [0.25, 4].  Device scratch: about
+ * 2^n / 128 bytes plus 8 bytes per shot for each output kept. */
+qaoa_status qaoa_sample(qaoa_ctx ctx, qaoa_cost cost, qaoa_state state, int64_t shots, uint64_t seed,
+                        uint64_t stream, const uint64_t *rand, uint64_t *idx, double *cost_out,
+                        double *mean_cost);
+
+/* Final distribution metrics of Sec. 3.6 from measured indices. */
+typedef struct {
+    int64_t shots, distinct;      /* shots, distinct bitstrings seen */
+    double mean_cost;             /* sampled mean cost */
+    double best_cost;             /* lowest sampled cost */
+    uint64_t best_index;          /* smallest index with that cost */
+    double p_best_index;          /* frequency of best_index */
+    double p_best_cost;           /* frequency of all shots with best_cost */
+    double low_cost_mass;         /* frequency of shots with cost <= best_cost + margin */
+    double p_ref_cost, p_ref_index;  /* frequency of the reference cost (within tol) / index; NaN without one */
+    int32_t best_cost_matches_ref;   /* |best_cost - ref_cost| <= tol; -1 without a reference */
+    int32_t best_index_matches_ref;  /* best_index == ref_index; -1 without a reference */
+} qaoa_sample_metrics;
+
+/* Host only.  idx, cost: host arrays of `shots` measured indices and their
+ * costs (as qaoa_sample returns them).  The elite set (Sec. 3.6, the top
+ * sampled bitstrings with their costs and counts) orders distinct indices by
+ * count descending, then cost ascending, then index ascending, and fills
+ * elite_idx/elite_cost/elite_count (host, `elite` entries each; entries past
+ * the distinct count get index ~0, cost NaN, count 0; NULL allowed when
+ * elite = 0).  has_ref = 1 adds the reference-based quantities for the
+ * classical optimum (ref_cost, ref_index), costs compared within tol. */
+qaoa_status qaoa_sample_stats(int64_t shots, const uint64_t *idx, const double *cost, double margin, int elite,
+                              uint64_t *elite_idx, double *elite_cost, int64_t *elite_count, int has_ref,
+                              double ref_cost, uint64_t ref_index, double tol, qaoa_sample_metrics *out);
+
+/* Hyper-parameters of qaoa_optimize_spsa.  Zero fields take the defaults
+ * lr = 0.01, beta1 = 0.9, beta2 = 0.999, eps = 1e-8, c = 0.1, averaging = 1;
+ * c_decay is used as given (0 keeps c_k = c). */
+typedef struct {
+    double lr, beta1, beta2, eps;  /* Adam */
+    double c, c_decay;             /* perturbation size c_k = c / (k + 1)^c_decay at iteration k = 0, 1, ... */
+    int32_t iterations;            /* >= 1 */
+    int32_t shots;                 /* shots per objective evaluation; 0 = exact expectation */
+    int32_t averaging;             /* independent shot estimates averaged per evaluation, 1..512 */
+    int32_t pad;
+    uint64_t seed;                 /* Philox key of the perturbations and the shots */
+    int32_t reserved[6];           /* must be zero */
+} qaoa_spsa_options;
+
+/* Sec. 3.4: Adam on the SPSA gradient estimate, for B starts at once.  At
+ * iteration k every start b draws one perturbation D (+-1 per entry of its
+ * interleaved x = [gamma_1, beta_1, ...]; entry i is -1 when bit 0 of word 0
+ * of Philox4x32-10 at counter (i, b, k, 0x53505341), key (seed lo, seed hi),
+ * is set), evaluates J at x + c_k D and x - c_k D as one batch of 2B items,
+ * forms g_i = (J+ - J-) / (2 c_k D_i) and takes one bias-corrected Adam step.
+ * J is the exact expectation (shots = 0) or the mean cost of `averaging` x
+ * `shots` shots of the item's state measured as by qaoa_sample with
+ * stream = k 2^32 + b 2^10 + (0 for +, 1 for -) 2^9 + pass.  Items and costs
+ * as in qaoa_grad_batch (B < 2^22).  gamma, beta: host, B*p doubles each,
+ * read as the start and overwritten with the result.  history: host,
+ * iterations*B*2 doubles or NULL; history[(k*B + b)*2 + 0/1] = J+/J-.
+ * final_expect: host, B doubles or NULL: exact E at the final parameters. */
+qaoa_status qaoa_optimize_spsa(qaoa_ctx ctx, int nq, const qaoa_cost *costs, const int32_t *item_cost,
+                               int B, int p, double *gamma, double *beta, const qaoa_spsa_options *opt,
+                               double *history, double *final_expect);
+
 /* ---- autotuning ---------------------------------------------------------- */
 
 /* Pick the fusion width (qubits per mixer pass) for states of cost's n by
@@ -301,8 +383,9 @@ qaoa_status qaoa_expect_noalloc(const void *amps, const int32_t *table, int n, i
 /* With options.profile = 1, every kernel launch of the given kind is timed
  * with CUDA events on the context stream.  kind: 0 = forward mixer pass,
  * 1 = reverse (adjoint) pass, 2 = objective table build, 3 = small-n resident
- * kernel, 4 = factorisation check; kind 5 counts every kernel the context
- * launched (timed or not; ms and bytes are 0).  Returns launches, summed
+ * kernel, 4 = factorisation check, 6 = measurement weights and prefix scan,
+ * 7 = measurement shots; kind 5 counts every kernel the context launched
+ * (timed or not; ms and bytes are 0).  Returns launches, summed
  * milliseconds and summed algorithmic bytes (bytes the method must move) since
  * the last reset; reset = 1 clears the counters after reading. */
 qaoa_status qaoa_profile_read(qaoa_ctx ctx, int kind, int64_t *launches, double *ms,

@@ -14,121 +14,9 @@
 
 using namespace qaoa;
 
-namespace qaoa {
-const char *last_error();
-}
+#include "api_state.h"
 
-#define CUDA_TRY(expr)                                                                             \
-    do {                                                                                           \
-        cudaError_t e__ = (expr);                                                                  \
-        if (e__ != cudaSuccess)                                                                    \
-            return fail(e__ == cudaErrorMemoryAllocation ? QAOA_ERR_OUT_OF_MEMORY : QAOA_ERR_CUDA, \
-                        "%s: %s (%s:%d)", #expr, cudaGetErrorString(e__), __FILE__, __LINE__);     \
-    } while (0)
-
-#define QAOA_TRY(expr)                  \
-    do {                                \
-        qaoa_status s__ = (expr);       \
-        if (s__ != QAOA_OK) return s__; \
-    } while (0)
-
-namespace {
-
-// growable device buffer
-struct DevBuf {
-    void *p = nullptr;
-    size_t cap = 0;
-    DevBuf() = default;
-    DevBuf(const DevBuf &) = delete;
-    DevBuf &operator=(const DevBuf &) = delete;
-    ~DevBuf() {
-        if (p) cudaFree(p);
-    }
-    qaoa_status ensure(size_t bytes, int64_t *held, int64_t budget) {
-        if (bytes <= cap) return QAOA_OK;
-        if (budget > 0 && *held - (int64_t)cap + (int64_t)bytes > budget)
-            return fail(QAOA_ERR_OUT_OF_MEMORY, "memory budget of %lld bytes exceeded", (long long)budget);
-        if (p) cudaFree(p);
-        p = nullptr;
-        *held -= (int64_t)cap;
-        cap = 0;
-        cudaError_t e = cudaMalloc(&p, bytes);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            p = nullptr;
-            return fail(QAOA_ERR_OUT_OF_MEMORY, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
-        }
-        cap = bytes;
-        *held += (int64_t)bytes;
-        return QAOA_OK;
-    }
-    void release(int64_t *held) {
-        if (p) cudaFree(p);
-        p = nullptr;
-        *held -= (int64_t)cap;
-        cap = 0;
-    }
-    template <typename T>
-    T *as() const {
-        return reinterpret_cast<T *>(p);
-    }
-};
-
-struct ProfRec {
-    int kind;
-    cudaEvent_t a, b;
-    double bytes;
-};
-
-// Device buffers of one plan execution (one n, a batch of items).
-struct PlanBufs {
-    DevBuf psi, pl, states, lam, partials, sums, scal, slot_scale, plan, gamma, beta, item_s, item_kc, item_table, tables,
-        out_E, out_dg, out_db, topk_a, topk_b, adam_m, adam_v, adam_step, history, small_items, small_out;
-};
-
-}  // namespace
-
-struct qaoa_ctx_s {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    qaoa_options opt{};
-    int64_t held = 0;
-    int num_sms = 148;
-    PlanBufs single;                  // qaoa_grad / qaoa_forward working set
-    std::map<int, std::unique_ptr<PlanBufs>> groups;  // batched working sets, by n
-    DevBuf partials_e, sums_e, topk_a, topk_b, small_items, small_out, misc, status;
-    std::vector<ProfRec> pending;
-    std::vector<cudaEvent_t> ev_free;
-    int64_t prof_launches[5] = {0, 0, 0, 0, 0};
-    double prof_ms[5] = {0, 0, 0, 0, 0};
-    double prof_bytes[5] = {0, 0, 0, 0, 0};
-    int64_t launches_total = 0;  // every kernel launched by this context
-    cudaStream_t aux_stream = nullptr;  // owned; runs captured optimisation loops
-    std::map<int, int> tuned_k;         // fusion width picked by the autotuner, by n
-};
-
-struct qaoa_cost_s {
-    int device = 0;
-    int n = 0;
-    Canonical can;
-    FixedPoint fp;
-    int32_t *T = nullptr;
-    uint64_t argmin = 0;
-    int64_t minval = 0;
-    ~qaoa_cost_s() {
-        if (T) cudaFree(T);
-    }
-};
-
-struct qaoa_state_s {
-    int device = 0;
-    int n = 0;
-    bool fp64 = false;
-    void *amps = nullptr;
-    ~qaoa_state_s() {
-        if (amps) cudaFree(amps);
-    }
-};
+using namespace qaoa::api;
 
 namespace {
 
@@ -1094,8 +982,11 @@ qaoa_status qaoa_grad(qaoa_ctx c, qaoa_cost cost, int p, const double *gamma, co
     return run_single(c, cost, p, gamma, beta, true, nullptr, out_expect, dgamma, dbeta, k_top, top_idx, top_prob);
 }
 
-qaoa_status qaoa_grad_batch(qaoa_ctx c, int nq, const qaoa_cost *costs, const int32_t *item_cost, int B, int p,
-                            const double *gamma, const double *beta, double *expect, double *dgamma, double *dbeta) {
+}  // extern "C"
+
+qaoa_status qaoa::api::run_batch(qaoa_ctx c, int nq, const qaoa_cost *costs, const int32_t *item_cost, int B, int p,
+                                 const double *gamma, const double *beta, double *expect, double *dgamma,
+                                 double *dbeta, std::vector<ItemState> *states) {
     if (!c || !costs || nq < 1 || B < 1 || !gamma || !beta || !expect)
         return fail(QAOA_ERR_INVALID_ARG, "bad batch arguments");
     if ((dgamma == nullptr) != (dbeta == nullptr))
@@ -1111,12 +1002,35 @@ qaoa_status qaoa_grad_batch(qaoa_ctx c, int nq, const qaoa_cost *costs, const in
     SmallSet small;
     QAOA_TRY(build_groups(c, nq, costs, item_cost, B, p, grad, groups, small));
     QAOA_TRY(build_small(c, small, costs, item_cost, p, gamma, beta, grad));
+    if (states) {
+        if (grad) return fail(QAOA_ERR_INVALID_ARG, "final states are kept by forward-only batches");
+        states->assign(B, ItemState{});
+        // small items write their final state to a context buffer
+        size_t off = 0;
+        for (size_t i = 0; i < small.items.size(); ++i) off += (size_t)8 << small.host[i].n;
+        QAOA_TRY(c->small_states.ensure(off + 16, &c->held, c->opt.memory_budget));
+        off = 0;
+        for (size_t i = 0; i < small.items.size(); ++i) {
+            small.host[i].psi_out = c->small_states.as<char>() + off;
+            const int b = small.items[i];
+            (*states)[b] = ItemState{small.host[i].psi_out, small.host[i].n,
+                                     costs[item_cost ? item_cost[b] : 0]};
+            off += (size_t)8 << small.host[i].n;
+        }
+        if (!small.items.empty())
+            CUDA_TRY(cudaMemcpyAsync(small.b->small_items.p, small.host.data(), small.host.size() * sizeof(SmallItem),
+                                     cudaMemcpyHostToDevice, c->stream));
+    }
     CUDA_TRY(cudaMemsetAsync(c->status.p, 0, 16, c->stream));
     QAOA_TRY(enqueue_small(c, small, p, false));
     for (BatchGroup &g : groups) {
         QAOA_TRY(upload_angles(c, g.items, p, gamma, beta, g.b->gamma, g.b->beta));
         QAOA_TRY(enqueue_group(c, g, true));
         if (!grad) {
+            if (states)
+                for (size_t i = 0; i < g.items.size(); ++i)
+                    (*states)[g.items[i]] =
+                        ItemState{g.b->psi.as<float2>() + i * ((size_t)1 << g.n), g.n, g.tabs[g.item_table[i]]};
             // forward only: <H_C> of every item's final state
             const int nb = 1 << (g.n - BLOCK_BITS);
             const size_t N = (size_t)1 << g.n;
@@ -1174,6 +1088,13 @@ qaoa_status qaoa_grad_batch(qaoa_ctx c, int nq, const qaoa_cost *costs, const in
         }
     }
     return QAOA_OK;
+}
+
+extern "C" {
+
+qaoa_status qaoa_grad_batch(qaoa_ctx c, int nq, const qaoa_cost *costs, const int32_t *item_cost, int B, int p,
+                            const double *gamma, const double *beta, double *expect, double *dgamma, double *dbeta) {
+    return run_batch(c, nq, costs, item_cost, B, p, gamma, beta, expect, dgamma, dbeta, nullptr);
 }
 
 qaoa_status qaoa_optimize_adam(qaoa_ctx c, int nq, const qaoa_cost *costs, const int32_t *item_cost, int B, int p,
@@ -1486,7 +1407,7 @@ qaoa_status qaoa_check_factorisation(qaoa_ctx c, qaoa_cost cost, const int32_t *
 }
 
 qaoa_status qaoa_profile_read(qaoa_ctx c, int kind, int64_t *launches, double *ms, double *bytes, int reset) {
-    if (!c || kind < 0 || kind > 5) return fail(QAOA_ERR_INVALID_ARG, "bad context or kind");
+    if (!c || kind < 0 || kind > 7) return fail(QAOA_ERR_INVALID_ARG, "bad context or kind");
     QAOA_TRY(set_device(c->device));
     if (kind == 5) {
         if (launches) *launches = c->launches_total;

@@ -70,6 +70,28 @@ cudaError_t launch_small(const SmallItem *items_dev, int count, int max_n, bool 
 cudaError_t launch_small_prep(SmallItem *items, int count, const double *gamma, const double *beta, int p,
                               const int *item_s, const long long *item_kc, cudaStream_t st);
 
+// One state measured by shots (kernels_sample.cu).  Device pointers.
+struct SampleItem {
+    const void *amps;                  // [2^n] complex64 (float2) or complex128 (double2)
+    const int32_t *T;                  // [2^n] objective table, or null (no costs)
+    unsigned long long *chunk;         // [sample_chunk_count(n)] scratch
+    unsigned long long *sup;           // [sample_super_count(n)] scratch
+    unsigned long long *total;         // [1] Q = sum of the weights
+    const unsigned long long *rand;    // [shots] random integers, or null: Philox(seed, stream, s)
+    unsigned long long *idx;           // [shots] measured indices, or null
+    int32_t *tval;                     // [shots] table values of the measured indices, or null
+    long long *tsum;                   // [1] += sum of the table values (zeroed by the caller), or null
+    unsigned long long seed, stream;
+    long long shots;
+    int n;
+};
+long long sample_chunk_count(int n);
+long long sample_super_count(int n);
+// weights + per-item scan; then the caller checks Q and launches the shots
+cudaError_t launch_sample_weights(const SampleItem *items_dev, int count, int max_n, bool fp64, cudaStream_t st);
+cudaError_t launch_sample_shots(const SampleItem *items_dev, int count, long long max_shots, bool fp64,
+                                unsigned int *status, cudaStream_t st);
+
 struct FactArgs {
     const int32_t *T;
     int n, M;

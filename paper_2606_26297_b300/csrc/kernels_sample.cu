@@ -1,0 +1,250 @@
+// Measurement of a statevector by shots (the shot-based objective of Sec. 3.4
+// and the final evaluation of Sec. 3.6), as inverse-CDF sampling on exact
+// integer weights:
+//   P_x = fl(re^2) + fl(im^2) in FP64,  q_x = floor(P_x 2^60),  Q = sum q_x,
+//   shot s: T = floor(R_s Q / 2^64), x_s = min { x : q_0 + ... + q_x > T }.
+// Integer prefix sums are exact, so the blocked order used here gives the same
+// x_s as a sequential scan.  Three launches per request:
+//   1. weights: one CTA per super-chunk (64 chunks of 1024 amplitudes), chunk
+//      sums and their inclusive prefix inside the super-chunk, super totals;
+//   2. scan: one CTA per item, exclusive prefix of the super totals and Q;
+//   3. shots: one warp per shot, a 32-ary search over the super prefixes, a
+//      ballot over the 64 chunk prefixes and a warp scan inside the chunk.
+// Traffic: one read of the state for (1), one chunk (8 KB) per shot for (3).
+#include "kernels_misc.h"
+#include "philox.cuh"
+
+namespace qaoa {
+
+namespace {
+
+constexpr int SAMPLE_THREADS = 256;
+
+struct Geo {
+    unsigned long long N;
+    int ch;      // amplitudes per chunk
+    int cps;     // chunks per super-chunk
+    int per;     // amplitudes per lane inside a chunk
+    long long nsuper;
+};
+
+__host__ __device__ inline Geo geo_of(int n) {
+    Geo g;
+    g.N = 1ull << n;
+    g.ch = n >= 10 ? 1024 : (1 << n);
+    const unsigned long long chunks = g.N / (unsigned long long)g.ch;
+    g.cps = chunks >= 64 ? 64 : (int)chunks;
+    g.per = g.ch >= 32 ? g.ch / 32 : 1;
+    g.nsuper = (long long)(chunks / (unsigned long long)g.cps);
+    return g;
+}
+
+template <typename E>
+__device__ __forceinline__ unsigned long long weight_of(const E &a) {
+    const double re = (double)a.x, im = (double)a.y;
+    const double P = __dadd_rn(__dmul_rn(re, re), __dmul_rn(im, im));
+    return __double2ull_rz(P * 1152921504606846976.0);  // 2^60
+}
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long warp_incl_scan(unsigned long long v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+template <typename E>
+__global__ void __launch_bounds__(SAMPLE_THREADS) sample_weights_kernel(const SampleItem *__restrict__ items) {
+    const SampleItem &it = items[blockIdx.y];
+    const Geo g = geo_of(it.n);
+    if ((long long)blockIdx.x >= g.nsuper) return;
+    __shared__ unsigned long long cs[64];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const E *amps = static_cast<const E *>(it.amps);
+    const unsigned long long sbase = (unsigned long long)blockIdx.x * g.cps * g.ch;
+    for (int c = warp; c < g.cps; c += SAMPLE_THREADS / 32) {
+        const E *p = amps + sbase + (unsigned long long)c * g.ch;
+        unsigned long long s = 0;
+        if (g.ch >= 32) {
+#pragma unroll 8
+            for (int j = 0; j < g.ch / 32; ++j) s += weight_of(p[lane + 32 * j]);
+        } else if (lane < g.ch) {
+            s = weight_of(p[lane]);
+        }
+        s = warp_sum(s);
+        if (lane == 0) cs[c] = s;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const unsigned long long a = 2 * lane < g.cps ? cs[2 * lane] : 0ull;
+        const unsigned long long b = 2 * lane + 1 < g.cps ? cs[2 * lane + 1] : 0ull;
+        const unsigned long long incl = warp_incl_scan(a + b, lane);
+        const unsigned long long excl = incl - a - b;
+        unsigned long long *out = it.chunk + (unsigned long long)blockIdx.x * g.cps;
+        if (2 * lane < g.cps) out[2 * lane] = excl + a;
+        if (2 * lane + 1 < g.cps) out[2 * lane + 1] = incl;
+        if (lane == 31) it.sup[blockIdx.x] = incl;
+    }
+}
+
+// One CTA per item: exclusive prefix of the super totals (in place) and Q.
+__global__ void __launch_bounds__(1024) sample_scan_kernel(const SampleItem *__restrict__ items) {
+    const SampleItem &it = items[blockIdx.x];
+    const Geo g = geo_of(it.n);
+    __shared__ unsigned long long wsum[32];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const long long per = (g.nsuper + 1023) / 1024;
+    const long long lo = (long long)t * per;
+    const long long hi = lo + per < g.nsuper ? lo + per : g.nsuper;
+    unsigned long long s = 0;
+    for (long long i = lo; i < hi; ++i) s += it.sup[i];
+    const unsigned long long incl = warp_incl_scan(s, lane);
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const unsigned long long w = wsum[lane];
+        const unsigned long long wi = warp_incl_scan(w, lane);
+        wsum[lane] = wi - w;
+    }
+    __syncthreads();
+    unsigned long long run = wsum[warp] + incl - s;
+    for (long long i = lo; i < hi; ++i) {
+        const unsigned long long v = it.sup[i];
+        it.sup[i] = run;
+        run += v;
+    }
+    if (t == 1023) *it.total = run;
+}
+
+template <typename E>
+__global__ void __launch_bounds__(SAMPLE_THREADS) sample_shot_kernel(const SampleItem *__restrict__ items,
+                                                                     unsigned int *status) {
+    const SampleItem &it = items[blockIdx.y];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long s = (long long)blockIdx.x * (SAMPLE_THREADS / 32) + warp;
+    __shared__ long long tsum[SAMPLE_THREADS / 32];
+    long long tv = 0;
+    if (s < it.shots) {
+        const Geo g = geo_of(it.n);
+        const unsigned long long Q = *it.total;
+        const unsigned long long R = it.rand ? it.rand[s] : shot_random(it.seed, it.stream, (uint64_t)s);
+        const unsigned long long T = __umul64hi(R, Q);
+        // largest super-chunk whose exclusive prefix is <= T (sup[0] = 0 <= T)
+        long long lo = 0, hi = g.nsuper;
+        while (hi - lo > 1) {
+            const long long step = (hi - lo + 31) / 32;
+            const long long pos = lo + lane * step;
+            const bool pred = pos < hi && it.sup[pos] <= T;
+            const unsigned m = __ballot_sync(0xffffffffu, pred);
+            lo += (long long)(31 - __clz(m)) * step;
+            hi = lo + step < hi ? lo + step : hi;
+        }
+        const unsigned long long r = T - it.sup[lo];
+        // first chunk of the super-chunk whose inclusive prefix exceeds r
+        const unsigned long long *inc = it.chunk + (unsigned long long)lo * g.cps;
+        const unsigned m1 = __ballot_sync(0xffffffffu, lane < g.cps && inc[lane] > r);
+        const unsigned m2 = __ballot_sync(0xffffffffu, lane + 32 < g.cps && inc[lane + 32] > r);
+        int c;
+        if (m1)
+            c = __ffs(m1) - 1;
+        else if (m2)
+            c = 32 + __ffs(m2) - 1;
+        else {
+            c = g.cps - 1;  // unreachable with exact sums; recorded
+            if (lane == 0) atomicOr(status, 2u);
+        }
+        const unsigned long long r2 = r - (c ? inc[c - 1] : 0ull);
+        // inside the chunk: lane l owns amplitudes [l per, (l+1) per)
+        const unsigned long long base = (unsigned long long)lo * g.cps * g.ch + (unsigned long long)c * g.ch;
+        const E *p = static_cast<const E *>(it.amps) + base;
+        const bool act = g.ch >= 32 || lane < g.ch;
+        unsigned long long ls = 0;
+        if (act)
+            for (int j = 0; j < g.per; ++j) ls += weight_of(p[lane * g.per + j]);
+        const unsigned long long li = warp_incl_scan(ls, lane);
+        const unsigned m3 = __ballot_sync(0xffffffffu, act && li > r2);
+        int L = m3 ? __ffs(m3) - 1 : -1;
+        if (L < 0) {
+            L = (g.ch >= 32 ? 32 : g.ch) - 1;
+            if (lane == 0) atomicOr(status, 2u);
+        }
+        unsigned long long x = 0;
+        if (lane == L) {
+            const unsigned long long r3 = r2 - (li - ls);
+            unsigned long long acc = 0;
+            int j = 0;
+            for (; j < g.per - 1; ++j) {
+                acc += weight_of(p[lane * g.per + j]);
+                if (acc > r3) break;
+            }
+            x = base + (unsigned long long)(lane * g.per + j);
+        }
+        x = __shfl_sync(0xffffffffu, x, L);
+        if (lane == 0) {
+            if (it.idx) it.idx[s] = x;
+            if (it.T) {
+                tv = it.T[x];
+                if (it.tval) it.tval[s] = (int32_t)tv;
+            }
+        }
+    }
+    if (lane == 0) tsum[warp] = tv;
+    __syncthreads();
+    if (threadIdx.x == 0 && it.tsum) {
+        long long a = 0;
+        for (int w = 0; w < SAMPLE_THREADS / 32; ++w) a += tsum[w];
+        if (a) atomicAdd(reinterpret_cast<unsigned long long *>(it.tsum), (unsigned long long)a);
+    }
+}
+
+}  // namespace
+
+long long sample_chunk_count(int n) {
+    const Geo g = geo_of(n);
+    return g.nsuper * g.cps;
+}
+
+long long sample_super_count(int n) { return geo_of(n).nsuper; }
+
+constexpr int MAX_GRID_Y = 65535;
+
+cudaError_t launch_sample_weights(const SampleItem *items_dev, int count, int max_n, bool fp64, cudaStream_t st) {
+    for (int o = 0; o < count; o += MAX_GRID_Y) {
+        const int k = count - o < MAX_GRID_Y ? count - o : MAX_GRID_Y;
+        const dim3 grid((unsigned)sample_super_count(max_n), (unsigned)k);
+        if (fp64)
+            sample_weights_kernel<double2><<<grid, SAMPLE_THREADS, 0, st>>>(items_dev + o);
+        else
+            sample_weights_kernel<float2><<<grid, SAMPLE_THREADS, 0, st>>>(items_dev + o);
+        cudaError_t e = cudaGetLastError();
+        if (e) return e;
+    }
+    sample_scan_kernel<<<count, 1024, 0, st>>>(items_dev);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sample_shots(const SampleItem *items_dev, int count, long long max_shots, bool fp64,
+                                unsigned int *status, cudaStream_t st) {
+    const long long per_cta = SAMPLE_THREADS / 32;
+    for (int o = 0; o < count; o += MAX_GRID_Y) {
+        const int k = count - o < MAX_GRID_Y ? count - o : MAX_GRID_Y;
+        const dim3 grid((unsigned)((max_shots + per_cta - 1) / per_cta), (unsigned)k);
+        if (fp64)
+            sample_shot_kernel<double2><<<grid, SAMPLE_THREADS, 0, st>>>(items_dev + o, status);
+        else
+            sample_shot_kernel<float2><<<grid, SAMPLE_THREADS, 0, st>>>(items_dev + o, status);
+        cudaError_t e = cudaGetLastError();
+        if (e) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace qaoa

@@ -261,3 +261,22 @@ def workload_uc32(n: int = 32, p: int = 6) -> tuple[Qubo, np.ndarray, np.ndarray
     q = unit_commitment_qubo(n, 1005)
     g, b = ramp_angles(p, gamma_scale=math.sqrt(n) / coefficient_norm(q))
     return q, g, b
+
+
+def random_state(n: int, seed: int, zero_mask=None, dtype=np.complex64) -> np.ndarray:
+    """A normalised random statevector of 2^n amplitudes (independent complex
+    normals), with the amplitudes where zero_mask (bool, 2^n) is true set to
+    zero; for measuring states of a chosen shape."""
+    rng = np.random.default_rng(seed)
+    N = 1 << n
+    a = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    if zero_mask is not None:
+        a[np.asarray(zero_mask, dtype=bool)] = 0.0
+    a /= np.linalg.norm(a)
+    return a.astype(dtype)
+
+
+def random_u64(count: int, seed: int) -> np.ndarray:
+    """count uniform 64-bit integers (numpy PCG64)."""
+    rng = np.random.default_rng(seed)
+    return rng.integers(0, np.iinfo(np.uint64).max, size=count, dtype=np.uint64, endpoint=True)

@@ -51,6 +51,21 @@ class qaoa_adam_options(ctypes.Structure):
                 ("reserved", ctypes.c_int32 * 6)]
 
 
+class qaoa_sample_metrics(ctypes.Structure):
+    _fields_ = [("shots", ctypes.c_int64), ("distinct", ctypes.c_int64), ("mean_cost", ctypes.c_double),
+                ("best_cost", ctypes.c_double), ("best_index", ctypes.c_uint64), ("p_best_index", ctypes.c_double),
+                ("p_best_cost", ctypes.c_double), ("low_cost_mass", ctypes.c_double),
+                ("p_ref_cost", ctypes.c_double), ("p_ref_index", ctypes.c_double),
+                ("best_cost_matches_ref", ctypes.c_int32), ("best_index_matches_ref", ctypes.c_int32)]
+
+
+class qaoa_spsa_options(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_double), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
+                ("eps", ctypes.c_double), ("c", ctypes.c_double), ("c_decay", ctypes.c_double),
+                ("iterations", ctypes.c_int32), ("shots", ctypes.c_int32), ("averaging", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("seed", ctypes.c_uint64), ("reserved", ctypes.c_int32 * 6)]
+
+
 _P = ctypes.c_void_p
 _I = ctypes.c_int
 _D = ctypes.c_double
@@ -80,6 +95,12 @@ _SIGS = {
     "qaoa_optimize_adam": ([_P, _I, ctypes.POINTER(_P), _PI32, _I, _I, _PD, _PD,
                             ctypes.POINTER(qaoa_adam_options), _PD, _PD], _I),
     "qaoa_autotune": ([_P, _P, _I, _PI32, _PD], _I),
+    "qaoa_state_from_host": ([_P, _I, _I, _P, ctypes.POINTER(_P)], _I),
+    "qaoa_sample": ([_P, _P, _P, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint64, _PU64, _PU64, _PD, _PD], _I),
+    "qaoa_sample_stats": ([ctypes.c_int64, _PU64, _PD, _D, _I, _PU64, _PD, _PI64, _I, _D, ctypes.c_uint64, _D,
+                           ctypes.POINTER(qaoa_sample_metrics)], _I),
+    "qaoa_optimize_spsa": ([_P, _I, ctypes.POINTER(_P), _PI32, _I, _I, _PD, _PD,
+                            ctypes.POINTER(qaoa_spsa_options), _PD, _PD], _I),
     "qaoa_partition": ([_I, _I, _PI32, _PI32, _PI32], _I),
     "qaoa_classify": ([_P, _PI32, _I, _PI64, _PI64, _PI64, _PI64], _I),
     "qaoa_check_factorisation": ([_P, _P, _PI32, _D, _PI64, _PD], _I),
@@ -290,6 +311,80 @@ def qaoa_autotune(ctx, cost, p: int = 2):
     return k.value, {w: float(ms[w - 3]) for w in range(3, 11) if not np.isnan(ms[w - 3])}
 
 
+# ---- measurement by shots and SPSA ----------------------------------------------------------
+
+def qaoa_state_from_host(ctx, amps, n: int | None = None):
+    """A device state holding `amps` (complex64, or complex128 for n <= 12)."""
+    a = np.ascontiguousarray(amps)
+    if a.dtype not in (np.complex64, np.complex128):
+        raise TypeError("amps must be complex64 or complex128")
+    nn = int(a.size).bit_length() - 1 if n is None else int(n)
+    out = _P()
+    _check(_lib.qaoa_state_from_host(ctx, nn, 1 if a.dtype == np.complex128 else 0, a.ctypes.data, ctypes.byref(out)))
+    return out
+
+
+def qaoa_sample(ctx, cost, state, shots: int, seed: int = 0, stream: int = 0, rand=None,
+                want_idx: bool = True, want_cost: bool = False, want_mean: bool = False):
+    """Measure `state` with `shots` shots.  Returns (idx uint64[shots] or None,
+    cost float64[shots] or None, mean cost or None)."""
+    S = int(shots)
+    r = None if rand is None else np.ascontiguousarray(np.asarray(rand, dtype=np.uint64))
+    if r is not None and r.size != S:
+        raise ValueError("rand must hold one integer per shot")
+    idx = np.zeros(S, dtype=np.uint64) if want_idx else None
+    cst = np.zeros(S) if want_cost else None
+    mean = ctypes.c_double()
+    _check(_lib.qaoa_sample(ctx, cost, state, S, int(seed) & 0xFFFFFFFFFFFFFFFF, int(stream) & 0xFFFFFFFFFFFFFFFF,
+                            None if r is None else r.ctypes.data_as(_PU64),
+                            None if idx is None else idx.ctypes.data_as(_PU64),
+                            None if cst is None else _dptr(cst), ctypes.byref(mean) if want_mean else None))
+    return idx, cst, (mean.value if want_mean else None)
+
+
+def qaoa_sample_stats(idx, cost, margin: float = 0.0, elite: int = 10, ref_cost=None, ref_index=None,
+                      tol: float = 1e-9) -> dict:
+    """Sec. 3.6 metrics of measured indices and their costs (host)."""
+    x = np.ascontiguousarray(np.asarray(idx, dtype=np.uint64))
+    c = _f64(cost)
+    m = qaoa_sample_metrics()
+    ei = np.zeros(max(int(elite), 1), dtype=np.uint64)
+    ec = np.zeros(max(int(elite), 1))
+    en = np.zeros(max(int(elite), 1), dtype=np.int64)
+    has = ref_cost is not None
+    _check(_lib.qaoa_sample_stats(x.size, x.ctypes.data_as(_PU64), _dptr(c), float(margin), int(elite),
+                                  ei.ctypes.data_as(_PU64), _dptr(ec), en.ctypes.data_as(_PI64), 1 if has else 0,
+                                  float(ref_cost) if has else 0.0,
+                                  int(ref_index) if ref_index is not None else 0xFFFFFFFFFFFFFFFF, float(tol),
+                                  ctypes.byref(m)))
+    out = {f: getattr(m, f) for f, _ in qaoa_sample_metrics._fields_}
+    out["elite"] = [(int(ei[i]), float(ec[i]), int(en[i]), float(en[i]) / m.shots)
+                    for i in range(int(elite)) if en[i] > 0]
+    return out
+
+
+def qaoa_optimize_spsa(ctx, costs, gamma, beta, iterations: int, item_cost=None, shots: int = 0,
+                       averaging: int = 1, seed: int = 0, c: float = 0.1, c_decay: float = 0.101,
+                       lr: float = 0.0, beta1: float = 0.0, beta2: float = 0.0, eps: float = 0.0):
+    """SPSA-Adam (Sec. 3.4) for B parameter sets (gamma, beta: (B, p)).
+    Returns (gamma, beta, history (iterations, B, 2) of (J+, J-), final exact E (B,))."""
+    g = np.array(np.asarray(gamma, dtype=np.float64), order="C", copy=True)
+    b = np.array(np.asarray(beta, dtype=np.float64), order="C", copy=True)
+    B, p = g.shape
+    arr = (_P * len(costs))(*[x.value if isinstance(x, _P) else x for x in costs])
+    ic = None if item_cost is None else np.ascontiguousarray(np.asarray(item_cost, dtype=np.int32))
+    o = qaoa_spsa_options()
+    o.lr, o.beta1, o.beta2, o.eps = float(lr), float(beta1), float(beta2), float(eps)
+    o.c, o.c_decay = float(c), float(c_decay)
+    o.iterations, o.shots, o.averaging = int(iterations), int(shots), int(averaging)
+    o.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    hist = np.zeros((int(iterations), B, 2))
+    E = np.zeros(B)
+    _check(_lib.qaoa_optimize_spsa(ctx, len(costs), arr, None if ic is None else ic.ctypes.data_as(_PI32), B, p,
+                                   _dptr(g), _dptr(b), ctypes.byref(o), _dptr(hist), _dptr(E)))
+    return g, b, hist, E
+
+
 # ---- DQAOA ----------------------------------------------------------------------------------
 
 def qaoa_partition(n: int, M: int, caps=None, manual=None) -> np.ndarray:
@@ -335,7 +430,8 @@ def qaoa_profile_read(ctx, kind: int, reset: bool = False):
     return {"launches": n.value, "ms": ms.value, "bytes": by.value}
 
 
-PROFILE_KINDS = {"fwd_pass": 0, "rev_pass": 1, "cost_build": 2, "small_resident": 3, "factorisation": 4}
+PROFILE_KINDS = {"fwd_pass": 0, "rev_pass": 1, "cost_build": 2, "small_resident": 3, "factorisation": 4,
+                 "sample_weights": 6, "sample_shots": 7}
 PROFILE_ALL_LAUNCHES = 5
 
 

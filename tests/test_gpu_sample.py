@@ -1,0 +1,272 @@
+"""GPU parity of the measurement by shots (qaoa_sample), the SPSA-Adam
+optimiser (qaoa_optimize_spsa) and their edge cases, against the oracle in
+oracle/sampling.py.
+
+Sampling is integer work once the weights q_x = floor(P_x 2^60) are fixed, so
+shots on a state both sides hold (uploaded with qaoa_state_from_host) must
+agree bit for bit, including the device's Philox stream.  States the GPU
+evolves in FP32 differ from the oracle's FP64 states in the last bits, so
+their shots are checked through properties that hold at any size and against
+the exact expectation within the central limit theorem.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import sampling as osm
+from paper_2606_26297_b300 import instances as inst
+
+pytestmark = pytest.mark.gpu
+
+E_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def q():
+    from paper_2606_26297_b300 import build_lib
+    build_lib.build()
+    from paper_2606_26297_b300 import qaoa
+    return qaoa
+
+
+@pytest.fixture(scope="module")
+def ctx(q):
+    c = q.qaoa_ctx_create(0)
+    yield c
+    q.qaoa_ctx_destroy(c)
+
+
+def _cost(q, ctx, Q):
+    return q.qaoa_build_cost(ctx, Q.H, Q.f, Q.c0, "i32" if Q.dtype == "i32" else "f32")
+
+
+@pytest.mark.parametrize("n", [1, 3, 5, 9, 10, 12, 13, 16, 17, 19, 22])
+def test_sample_bit_exact_philox(q, ctx, n):
+    """Shots of an uploaded random state: device Philox stream and inverse CDF
+    equal the oracle's index for index (one chunk, one super-chunk, several,
+    and the multi-round super-chunk search at n = 22)."""
+    amps = inst.random_state(n, 500 + n)
+    st = q.qaoa_state_from_host(ctx, amps)
+    S, seed, stream = 2500, 0x1234_5678_9ABC + n, (n << 40) + 7
+    idx, _, _ = q.qaoa_sample(ctx, None, st, S, seed=seed, stream=stream)
+    ref = osm.sample(amps, osm.shot_randoms(seed, stream, S))
+    assert np.array_equal(idx, ref)
+    q.qaoa_state_destroy(st)
+
+
+@pytest.mark.parametrize("n", [4, 11, 18])
+def test_sample_bit_exact_caller_randoms(q, ctx, n):
+    """Caller-supplied random integers, including the extremes 0 and 2^64 - 1."""
+    amps = inst.random_state(n, 900 + n)
+    R = inst.random_u64(3000, 77 + n)
+    R[:4] = [0, np.iinfo(np.uint64).max, 1 << 63, (1 << 63) - 1]
+    st = q.qaoa_state_from_host(ctx, amps)
+    idx, _, _ = q.qaoa_sample(ctx, None, st, len(R), rand=R)
+    assert np.array_equal(idx, osm.sample(amps, [int(r) for r in R]))
+    nz = np.flatnonzero(osm.weights(amps))
+    assert idx[0] == nz[0] and idx[1] == nz[-1]
+    q.qaoa_state_destroy(st)
+
+
+def test_sample_sparse_and_empty_regions(q, ctx):
+    """Whole super-chunks and chunks of zero probability (n = 18): the search
+    skips them, shots never land on a zero weight, and indices match the
+    oracle; a basis state always returns its index."""
+    n = 18
+    N = 1 << n
+    keep = np.zeros(N, dtype=bool)
+    keep[:37] = True
+    keep[N - 70:] = True
+    keep[[70_000, 131_072, 200_001]] = True
+    amps = inst.random_state(n, 41, zero_mask=~keep)
+    st = q.qaoa_state_from_host(ctx, amps)
+    idx, _, _ = q.qaoa_sample(ctx, None, st, 4000, seed=5, stream=6)
+    assert np.array_equal(idx, osm.sample(amps, osm.shot_randoms(5, 6, 4000)))
+    assert np.all(keep[idx.astype(np.int64)])
+    q.qaoa_state_destroy(st)
+    basis = np.zeros(N, dtype=np.complex64)
+    basis[123_457] = 1j
+    st = q.qaoa_state_from_host(ctx, basis)
+    idx, _, _ = q.qaoa_sample(ctx, None, st, 1000, seed=9)
+    assert set(idx.tolist()) == {123_457}
+    q.qaoa_state_destroy(st)
+
+
+def test_sample_complex128_state(q, ctx):
+    """A complex128 state (n <= 12): weights from FP64 amplitudes, both
+    products rounded, match the oracle bit for bit."""
+    n = 8
+    amps = inst.random_state(n, 88, dtype=np.complex128)
+    st = q.qaoa_state_from_host(ctx, amps)
+    idx, _, _ = q.qaoa_sample(ctx, None, st, 3000, seed=3, stream=4)
+    assert np.array_equal(idx, osm.sample(amps, osm.shot_randoms(3, 4, 3000)))
+    q.qaoa_state_destroy(st)
+
+
+def test_sample_rejects_bad_input(q, ctx):
+    """Zero states (total probability outside [0.25, 4]), shots < 1, costs
+    without a cost handle, and a cost of another n are refused."""
+    st = q.qaoa_state_from_host(ctx, np.zeros(1 << 6, dtype=np.complex64))
+    with pytest.raises(q.QaoaError):
+        q.qaoa_sample(ctx, None, st, 10)
+    q.qaoa_state_destroy(st)
+    st = q.qaoa_state_from_host(ctx, inst.random_state(6, 1))
+    with pytest.raises(q.QaoaError):
+        q.qaoa_sample(ctx, None, st, 0)
+    with pytest.raises(q.QaoaError):
+        q.qaoa_sample(ctx, None, st, 10, want_mean=True)
+    cost = _cost(q, ctx, inst.upper_int_qubo(7, 3))
+    with pytest.raises(q.QaoaError):
+        q.qaoa_sample(ctx, cost, st, 10, want_cost=True)
+    q.qaoa_cost_destroy(cost)
+    q.qaoa_state_destroy(st)
+
+
+@pytest.mark.parametrize("n", [12, 16])
+def test_sample_costs_and_mean(q, ctx, n):
+    """Costs of the shots of an evolved state equal the oracle's F at those
+    indices exactly (integer QUBO), the mean cost is their mean, and it lies
+    within five standard errors of the exact expectation."""
+    Q = inst.upper_int_qubo(n, 1200 + n)
+    g, b = inst.ramp_angles(2, gamma_scale=1.0 / math.sqrt(n))
+    cost = _cost(q, ctx, Q)
+    st = q.qaoa_forward(ctx, cost, g, b)
+    S = 20000
+    idx, cs, mean = q.qaoa_sample(ctx, cost, st, S, seed=11, stream=12, want_cost=True, want_mean=True)
+    cq = oracle.canonical_of(Q)
+    assert np.array_equal(cs, oracle.cost_at(cq, idx))
+    assert mean == pytest.approx(float(np.mean(cs)), rel=1e-12, abs=1e-9)
+    F = oracle.cost_table(cq)
+    psi = oracle.evolve(F, g, b)
+    E = oracle.expectation(F, psi)
+    sd = math.sqrt(float(np.sum(oracle.probabilities(psi) * (F - E) ** 2)))
+    assert abs(mean - E) < 5 * sd / math.sqrt(S)
+    q.qaoa_state_destroy(st)
+    q.qaoa_cost_destroy(cost)
+
+
+def test_sample_stratified_monotone_n26(q, ctx):
+    """Properties of inverse-CDF sampling at any size (n = 26, an evolved
+    state): stratified randoms R_s = s 2^64 / S give non-decreasing indices,
+    R = 0 gives the first and R = 2^64 - 1 the last index of non-zero weight,
+    and every measured amplitude is non-zero."""
+    n = 26
+    Q = inst.normal_qubo(n, 2600)
+    g, b = inst.ramp_angles(2, gamma_scale=1.0 / math.sqrt(n))
+    cost = _cost(q, ctx, Q)
+    st = q.qaoa_forward(ctx, cost, g, b)
+    S = 4096
+    R = np.array([(s << 64) // S + (1 << 40) for s in range(S)], dtype=np.uint64)
+    R[0], R[-1] = 0, np.iinfo(np.uint64).max
+    idx, _, _ = q.qaoa_sample(ctx, None, st, S, rand=R)
+    assert np.all(np.diff(idx.astype(np.int64)) >= 0)
+    assert idx[0] == 0 and idx[-1] == (1 << n) - 1
+    amps = q.qaoa_state_gather(ctx, st, idx[::64])
+    assert np.all(np.abs(amps) > 0)
+    q.qaoa_state_destroy(st)
+    q.qaoa_cost_destroy(cost)
+
+
+def _oracle_objective(F, p, shots, seed, b):
+    def J(x, k, which):
+        g, be = x[0::2], x[1::2]
+        psi = oracle.evolve(F, g, be)
+        if shots == 0:
+            return oracle.expectation(F, psi)
+        stream = (k << 32) | (b << 10) | (which << 9)
+        return osm.sampled_mean(F, osm.sample(psi, osm.shot_randoms(seed, stream, shots)))
+    return J
+
+
+@pytest.mark.parametrize("n", [10, 14])
+def test_spsa_exact_vs_oracle(q, ctx, n):
+    """SPSA-Adam on the exact expectation (shots = 0) for two starts against
+    the oracle's SPSA-Adam driving the FP64 expectation: same perturbations,
+    J+ and J- of every iteration within 1e-5 max|F| and the final angles close."""
+    Q = inst.upper_int_qubo(n, 3000 + n)
+    p, B, iters, seed = 2, 2, 5, 4242
+    g0, b0 = inst.random_angles(p, B, 3001 + n, gamma_scale=1.0 / math.sqrt(n))
+    cost = _cost(q, ctx, Q)
+    g, b, hist, Ef = q.qaoa_optimize_spsa(ctx, [cost], g0, b0, iters, seed=seed, c=0.15, c_decay=0.101, lr=0.05)
+    F = oracle.cost_table(oracle.canonical_of(Q))
+    scale = float(np.max(np.abs(F)))
+    for s in range(B):
+        x0 = oracle.interleave(g0[s], b0[s])
+        x, h = osm.spsa_adam(_oracle_objective(F, p, 0, seed, s), x0, iters, seed, b=s, c=0.15, decay=0.101,
+                             lr=0.05)
+        assert np.max(np.abs(hist[:, s, :] - np.array(h))) / scale <= E_TOL
+        assert np.max(np.abs(oracle.interleave(g[s], b[s]) - x)) <= 1e-4
+        assert abs(Ef[s] - oracle.expectation(F, oracle.evolve(F, g[s], b[s]))) / scale <= E_TOL
+    q.qaoa_cost_destroy(cost)
+
+
+def test_spsa_shots_first_iteration_vs_oracle(q, ctx):
+    """Shot-based J+ and J- of the first iteration against the oracle's shots
+    of its FP64 states with the same streams: equal up to the few shots whose
+    target falls within rounding of a weight boundary (at most 3 shots'
+    worth of cost here)."""
+    n, p, S, seed = 8, 2, 4000, 99
+    Q = inst.upper_int_qubo(n, 3100)
+    g0, b0 = inst.random_angles(p, 1, 3101, gamma_scale=0.3)
+    cost = _cost(q, ctx, Q)
+    _, _, hist, _ = q.qaoa_optimize_spsa(ctx, [cost], g0, b0, 1, shots=S, seed=seed, c=0.2)
+    F = oracle.cost_table(oracle.canonical_of(Q))
+    J = _oracle_objective(F, p, S, seed, 0)
+    D = osm.spsa_signs(seed, 0, 0, 2 * p)
+    x0 = oracle.interleave(g0[0], b0[0])
+    spread = float(F.max() - F.min())
+    assert abs(hist[0, 0, 0] - J(x0 + 0.2 * D, 0, 0)) <= 3 * spread / S
+    assert abs(hist[0, 0, 1] - J(x0 - 0.2 * D, 0, 1)) <= 3 * spread / S
+    q.qaoa_cost_destroy(cost)
+
+
+def test_spsa_shots_match_sample_api(q, ctx):
+    """J+ of the first iteration equals qaoa_sample's mean cost of the state
+    qaoa_forward evolves at x0 + c D with the same stream (n = 13, pass path)."""
+    n, p, S, seed, c = 13, 2, 5000, 7, 0.12
+    Q = inst.upper_int_qubo(n, 3200)
+    g0, b0 = inst.random_angles(p, 1, 3201, gamma_scale=0.3)
+    cost = _cost(q, ctx, Q)
+    _, _, hist, _ = q.qaoa_optimize_spsa(ctx, [cost], g0, b0, 1, shots=S, seed=seed, c=c)
+    D = osm.spsa_signs(seed, 0, 0, 2 * p)
+    x = oracle.interleave(g0[0], b0[0]) + c * D
+    st = q.qaoa_forward(ctx, cost, x[0::2], x[1::2])
+    _, _, mean = q.qaoa_sample(ctx, cost, st, S, seed=seed, stream=0, want_idx=False, want_mean=True)
+    assert hist[0, 0, 0] == pytest.approx(mean, rel=0, abs=1e-12)
+    q.qaoa_state_destroy(st)
+    q.qaoa_cost_destroy(cost)
+
+
+def test_spsa_deterministic_and_improves(q, ctx):
+    """Same seed, same history (bit for bit); another seed, another history;
+    30 shot-based iterations on a ragged batch (n = 9 and n = 14) lower the
+    exact expectation of every start."""
+    Qa, Qb = inst.upper_int_qubo(9, 3300), inst.upper_int_qubo(14, 3301)
+    ca, cb = _cost(q, ctx, Qa), _cost(q, ctx, Qb)
+    p = 2
+    g0 = np.array([[0.05, 0.08], [0.03, 0.05]])
+    b0 = np.array([[0.3, 0.2], [0.3, 0.2]])
+    kw = dict(shots=2000, seed=31, c=0.1, lr=0.03, item_cost=[0, 1])
+    r1 = q.qaoa_optimize_spsa(ctx, [ca, cb], g0, b0, 30, **kw)
+    r2 = q.qaoa_optimize_spsa(ctx, [ca, cb], g0, b0, 30, **kw)
+    assert np.array_equal(r1[2], r2[2]) and np.array_equal(r1[0], r2[0])
+    kw["seed"] = 32
+    r3 = q.qaoa_optimize_spsa(ctx, [ca, cb], g0, b0, 30, **kw)
+    assert not np.array_equal(r1[2], r3[2])
+    E0 = q.qaoa_grad_batch(ctx, [ca, cb], g0, b0, item_cost=[0, 1], grad=False)
+    assert np.all(r1[3] < E0)
+    q.qaoa_cost_destroy(ca)
+    q.qaoa_cost_destroy(cb)
+
+
+def test_spsa_rejects_bad_options(q, ctx):
+    cost = _cost(q, ctx, inst.upper_int_qubo(6, 1))
+    g0, b0 = np.zeros((1, 1)), np.zeros((1, 1))
+    for kw in [dict(averaging=600), dict(shots=-1), dict(c=-0.1), dict(c_decay=-1.0)]:
+        with pytest.raises(q.QaoaError):
+            q.qaoa_optimize_spsa(ctx, [cost], g0, b0, 2, **kw)
+    with pytest.raises(q.QaoaError):
+        q.qaoa_optimize_spsa(ctx, [cost], g0, b0, 0)
+    q.qaoa_cost_destroy(cost)
