@@ -235,9 +235,10 @@ qaoa_status qaoa_state_from_host(qaoa_ctx ctx, int n, int fp64, const void *amps
 /* Measure `state` with `shots` shots (1 <= shots <= 2^34), the circuit
  * execution whose counts Sec. 3.4 turns into the sampled mean cost and Sec.
  * 3.6 into the final distribution.  Inverse-CDF sampling on exact integer
- * weights: P_x = fl(re^2) + fl(im^2) in FP64, q_x = floor(P_x 2^60),
- * Q = sum_x q_x; shot s with 64-bit random integer R_s lands on the smallest x
- * whose prefix q_0 + ... + q_x exceeds floor(R_s Q / 2^64).  R_s = rand[s]
+ * weights: q_x = floor(re^2 2^60) + floor(im^2 2^60) with the squares of the
+ * stored components taken exactly, Q = sum_x q_x; shot s with 64-bit random
+ * integer R_s lands on the smallest x whose prefix q_0 + ... + q_x exceeds
+ * floor(R_s Q / 2^64).  R_s = rand[s]
  * (host array of `shots` integers) or, with rand = NULL, the counter-based
  * Philox4x32-10 (Salmon et al., SC 2011): counter (s lo, s hi, stream lo,
  * stream hi), key (seed lo, seed hi), R = out0 + 2^32 out1.
@@ -245,7 +246,7 @@ qaoa_status qaoa_state_from_host(qaoa_ctx ctx, int n, int fp64, const void *amps
  * the cost table (needs `cost`, of the same n); *mean_cost = mean of F over
  * the shots (needs `cost`), summed exactly in integers.  QAOA_ERR_RANGE if
  * the state's total probability is outside [0.25, 4].  Device scratch: about
- * 2^n / 128 bytes plus 8 bytes per shot for each output kept. */
+ * 2^n / 32 bytes plus 8 bytes per shot for each output kept. */
 qaoa_status qaoa_sample(qaoa_ctx ctx, qaoa_cost cost, qaoa_state state, int64_t shots, uint64_t seed,
                         uint64_t stream, const uint64_t *rand, uint64_t *idx, double *cost_out,
                         double *mean_cost);
@@ -307,6 +308,66 @@ qaoa_status qaoa_optimize_spsa(qaoa_ctx ctx, int nq, const qaoa_cost *costs, con
                                int B, int p, double *gamma, double *beta, const qaoa_spsa_options *opt,
                                double *history, double *final_expect);
 
+/* ---- depth progression and multi-start search (Sec. 3.5, Algorithm 1) ---- */
+
+typedef struct {
+    int32_t p_max;          /* depths 1 .. p_max, p_max <= 64 */
+    int32_t optimizer;      /* 0 = SPSA-Adam (qaoa_optimize_spsa), 1 = Adam on the exact gradient */
+    int32_t iterations;     /* optimiser steps per start, >= 1 */
+    int32_t shots;          /* SPSA: shots per objective evaluation, 0 = exact expectation */
+    int32_t averaging;      /* SPSA: shot estimates averaged per evaluation; 0 -> 1 */
+    int32_t random_starts;  /* random initial points per depth (>= 1) */
+    int32_t warm_perturb;   /* perturbed copies of the lifted previous best, depths >= 2 */
+    int32_t include_warm;   /* 1: the lifted previous best itself is a start, depths >= 2 */
+    int32_t final_shots;    /* shots of every candidate's final evaluation, >= 1 */
+    int32_t use_reference;  /* 1: rank by agreement with the brute-force optimum first */
+    double lr, beta1, beta2, eps;   /* Adam; zero fields -> 0.01, 0.9, 0.999, 1e-8 */
+    double c, c_decay;              /* SPSA perturbation as in qaoa_spsa_options */
+    double warm_sigma;              /* standard deviation of the warm-start perturbations */
+    double gamma_range, beta_range; /* random starts: gamma ~ U[0, gamma_range), beta ~ U[0, beta_range) */
+    double margin;                  /* low-cost mass margin (qaoa_sample_stats) */
+    double tol;                     /* cost tolerance of the reference comparison */
+    uint64_t seed;
+    int32_t reserved[8];            /* must be zero */
+} qaoa_solve_options;
+
+typedef struct {
+    int32_t best_p;               /* depth of the selected candidate */
+    int32_t runs;                 /* optimisation runs over all depths */
+    double expect;                /* exact <H_C> at the selected parameters */
+    qaoa_sample_metrics metrics;  /* final evaluation of the selected candidate */
+} qaoa_solve_result;
+
+/* Algorithm 1 (Sec. 3.5) on one cost handle.  For p = 1 .. p_max: the starts
+ * are the previous depth's best lifted to depth p by linear interpolation
+ * (INTERP of Zhou et al., PRX 10, 021067: x'_i = (i-1)/p x_{i-1} +
+ * (p-i+1)/p x_i, x_0 = x_{p+1} = 0, for gamma and beta) if include_warm,
+ * warm_perturb copies of it plus warm_sigma N(0, 1) per entry, and
+ * random_starts random points, in that order; all starts of a depth are
+ * optimised as one batch (the paper's parallel restarts), then each result is
+ * measured with final_shots shots and scored with qaoa_sample_stats; the
+ * candidates are ranked lexicographically (Sec. 3.5): with use_reference,
+ * best cost equals the brute-force optimum, best index equals it, mass on the
+ * optimum cost, probability of the optimum index (larger first); then best
+ * sampled cost (smaller first), mass on it, probability of the best index
+ * (larger first), mean cost (smaller first), and without a reference the gap
+ * mean - best (smaller first); ties keep the earlier start.  The best of each
+ * depth warm-starts the next; the depth representatives are ranked the same
+ * way.  Random numbers: Philox4x32-10 with key (seed lo, seed hi) and counter
+ * (i, j, p, 0x52414E44) for entry i of the interleaved x of start j at depth
+ * p (uniform u = (w0 + 2^32 w1) >> 11 times 2^-53), counter (i, j, p,
+ * 0x57415250) for the perturbations (Box-Muller on the uniforms of (w0, w1)
+ * and (w2, w3)); SPSA at depth p uses seed + p 0x9E3779B97F4A7C15; the final
+ * evaluation of start j at depth p uses shot stream 0xF000000000000000 +
+ * p 2^32 + j.
+ * Outputs (host): gamma, beta: p_max doubles each, the first best_p set (the
+ * rest 0); elite (>= 0) entries of elite_idx/elite_cost/elite_count for the
+ * selected candidate (as qaoa_sample_stats; NULL allowed when elite = 0);
+ * depth_metrics: p_max entries or NULL, each depth's representative; *out. */
+qaoa_status qaoa_solve(qaoa_ctx ctx, qaoa_cost cost, const qaoa_solve_options *opt, double *gamma,
+                       double *beta, int elite, uint64_t *elite_idx, double *elite_cost, int64_t *elite_count,
+                       qaoa_sample_metrics *depth_metrics, qaoa_solve_result *out);
+
 /* ---- autotuning ---------------------------------------------------------- */
 
 /* Pick the fusion width (qubits per mixer pass) for states of cost's n by
@@ -329,6 +390,28 @@ qaoa_status qaoa_autotune(qaoa_ctx ctx, qaoa_cost cost, int p, int32_t *best_k, 
  * is validated (every variable once, no capacity exceeded, every QPU used);
  * QAOA_ERR_ALLOCATION if not.  qpu_of: host output, n entries. */
 qaoa_status qaoa_partition(int n, int M, const int32_t *caps, const int32_t *manual, int32_t *qpu_of);
+
+/* Graph-aware allocation (Sec. 3.1), host only: the weighted interaction
+ * graph has edge weight |b_ij| (canonical couplings of the QUBO *q); QPUs are
+ * filled in order, QPU m opening with the unassigned variable of largest
+ * weighted degree towards the unassigned variables and then taking the
+ * unassigned variable with the largest total weight to its members (ties:
+ * larger weighted degree towards the unassigned variables, then smaller
+ * index) until it holds min(caps[m], unassigned - QPUs still to open).  caps:
+ * M capacities, or NULL for balanced ones.  qpu_of: host output, n entries;
+ * the result is validated as by qaoa_partition. */
+qaoa_status qaoa_partition_graph(const qaoa_qubo *q, int M, const int32_t *caps, int32_t *qpu_of);
+
+/* Allocation candidates and their selection (Sec. 3.1), host only: the
+ * contiguous (kind 0), graph-aware (kind 1) and, when manual != NULL, the
+ * manual (kind 2) allocation are scored by their cross-QPU couplings
+ * b_ij != 0; the fewest wins, ties resolved in the order manual, graph-aware,
+ * contiguous.  Outputs (host): qpu_of (n) and *kind of the selected one;
+ * cross[3] and remote_cx[3] (may be NULL) per kind, remote_cx = 2 cross p,
+ * -1 for a kind not built. */
+qaoa_status qaoa_allocation_candidates(const qaoa_qubo *q, int M, const int32_t *caps, const int32_t *manual,
+                                       int p, int32_t *qpu_of, int32_t *kind, int64_t *cross,
+                                       int64_t *remote_cx);
 
 /* Classify the couplings b_ij != 0 (i<j) of `cost` as local (q(i) = q(j)) or
  * cross-QPU (Eq. local_cross_rule), and estimate the remote CNOTs as

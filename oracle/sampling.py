@@ -20,10 +20,11 @@ What it follows:
 Readings (the paper does not fix these; the CUDA path implements the same
 definitions independently):
 
-* Measurement is inverse-CDF sampling on integer weights.  The probability of
-  index x is P_x = fl(re^2) + fl(im^2), rounded once more by the sum, in FP64
-  from the stored amplitude; its weight is q_x = floor(P_x * 2^60).  With
-  Q = sum_x q_x and a 64-bit random integer R per shot, the shot's target is
+* Measurement is inverse-CDF sampling on integer weights.  The weight of
+  index x is q_x = floor(re^2 2^60) + floor(im^2 2^60), each square taken
+  exactly from the stored amplitude component (float32 or float64), so q_x is
+  |psi_x|^2 in units of 2^-60, truncated per component.  With Q = sum_x q_x
+  and a 64-bit random integer R per shot, the shot's target is
   T = floor(R * Q / 2^64) and the shot lands on the smallest x whose inclusive
   prefix sum of q exceeds T.  Integer sums are exact, so every order of
   summation gives the same x.
@@ -88,14 +89,29 @@ def spsa_signs(seed: int, k: int, b: int, nparam: int) -> np.ndarray:
                      for i in range(nparam)])
 
 
+def _sq60(v: np.ndarray) -> np.ndarray:
+    """floor(v^2 2^60) of every entry (|v| < 2), exact: v = M 2^(e - d) with an
+    integer mantissa M of d bits (24 for float32, 53 for float64), so v^2 2^60
+    is M^2 shifted left by 2(e - d) + 60 (right when negative)."""
+    m, e = np.frexp(v)
+    if v.dtype == np.float32:
+        M = np.abs(m.astype(np.float64) * 2.0 ** 24).astype(np.int64)
+        sh = 2 * (e.astype(np.int64) - 24) + 60
+        M2 = M * M  # < 2^48: exact in int64
+        left = M2 << np.clip(sh, 0, 14)
+        right = M2 >> np.clip(-sh, 0, 63)
+        return np.where(sh >= 0, left, right).astype(np.uint64)
+    M = np.abs(m * 2.0 ** 53).astype(np.int64)
+    sh = 2 * (e.astype(np.int64) - 53) + 60
+    out = [(int(a) * int(a)) << int(t) if t >= 0 else (int(a) * int(a)) >> int(-t) for a, t in zip(M, sh)]
+    return np.array(out, dtype=np.uint64)
+
+
 def weights(amps: np.ndarray) -> np.ndarray:
-    """q_x = floor(P_x 2^60) as Python-int-valued uint64, P_x in FP64 from the
-    stored amplitude (complex64 or complex128)."""
+    """q_x = floor(re^2 2^60) + floor(im^2 2^60) (uint64) of a complex64 or
+    complex128 state."""
     a = np.asarray(amps)
-    re = a.real.astype(np.float64)
-    im = a.imag.astype(np.float64)
-    P = re * re + im * im  # numpy: each product rounded, then the sum
-    return np.floor(P * float(2 ** WEIGHT_BITS)).astype(np.uint64)
+    return _sq60(np.ascontiguousarray(a.real)) + _sq60(np.ascontiguousarray(a.imag))
 
 
 def sample(amps: np.ndarray, R) -> np.ndarray:

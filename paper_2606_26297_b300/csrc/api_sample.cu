@@ -116,7 +116,7 @@ qaoa_status measure(qaoa_ctx c, const std::vector<ItemState> &st, bool fp64, con
         CUDA_TRY(cudaMemsetAsync(c->status.p, 0, 4, c->stream));
         double sb = 0;
         for (const ShotSet &x : sets)
-            sb += (double)x.shots * std::ldexp(fp64 ? 16.0 : 8.0, std::min(st[x.state].n, 10));
+            sb += (double)x.shots * std::ldexp(fp64 ? 16.0 : 8.0, std::min(st[x.state].n, 8));
         SampleProf prof(c, 7, sb);
         CUDA_TRY(launch_sample_shots(dev + K, (int)sets.size(), max_shots, fp64, c->status.as<unsigned int>(),
                                      c->stream));
@@ -141,6 +141,62 @@ double fixed_to_cost(long long t, const qaoa_cost_s *cs) { return std::ldexp((do
 // Mean cost of `shots` shots whose table values sum to tsum.
 double mean_of(long long tsum, long long shots, const qaoa_cost_s *cs) {
     return std::ldexp((double)tsum + (double)shots * (double)cs->fp.k_c, -cs->fp.s) / (double)shots;
+}
+
+// ---- Algorithm 1 helpers ------------------------------------------------------
+
+constexpr uint32_t TAG_RAND = 0x52414E44u, TAG_WARM = 0x57415250u;
+constexpr uint64_t FINAL_STREAM = 0xF000000000000000ull;
+constexpr uint64_t DEPTH_SEED_STEP = 0x9E3779B97F4A7C15ull;
+
+double unit_of(uint32_t w0, uint32_t w1) {
+    return (double)((((uint64_t)w1 << 32) | w0) >> 11) * 0x1p-53;
+}
+
+double start_uniform(uint64_t seed, uint32_t i, uint32_t j, uint32_t p) {
+    const Philox4 o = philox4x32_10(i, j, p, TAG_RAND, (uint32_t)seed, (uint32_t)(seed >> 32));
+    return unit_of(o.w[0], o.w[1]);
+}
+
+double start_normal(uint64_t seed, uint32_t i, uint32_t j, uint32_t p) {
+    const Philox4 o = philox4x32_10(i, j, p, TAG_WARM, (uint32_t)seed, (uint32_t)(seed >> 32));
+    const double u1 = unit_of(o.w[0], o.w[1]), u2 = unit_of(o.w[2], o.w[3]);
+    return std::sqrt(-2.0 * std::log(1.0 - u1)) * std::cos(2.0 * M_PI * u2);
+}
+
+// INTERP lifting of one angle sequence from depth p to p + 1.
+std::vector<double> lift_interp(const std::vector<double> &v) {
+    const int p = (int)v.size();
+    std::vector<double> out(p + 1);
+    for (int i = 1; i <= p + 1; ++i) {
+        const double prev = i - 1 >= 1 ? v[i - 2] : 0.0, cur = i <= p ? v[i - 1] : 0.0;
+        out[i - 1] = ((double)(i - 1) / p) * prev + ((double)(p - i + 1) / p) * cur;
+    }
+    return out;
+}
+
+// Lexicographic ranking key of a candidate (smaller is better).
+std::vector<double> rank_key(const qaoa_sample_metrics &m, bool ref) {
+    std::vector<double> k;
+    if (ref) {
+        k = {-(double)m.best_cost_matches_ref, -(double)m.best_index_matches_ref, -m.p_ref_cost, -m.p_ref_index};
+    }
+    k.insert(k.end(), {m.best_cost, -m.p_best_cost, -m.p_best_index, m.mean_cost});
+    if (!ref) k.push_back(m.mean_cost - m.best_cost);
+    return k;
+}
+
+int best_candidate(const std::vector<qaoa_sample_metrics> &ms, bool ref) {
+    int best = 0;
+    std::vector<double> kb = rank_key(ms[0], ref);
+    for (size_t j = 1; j < ms.size(); ++j) {
+        std::vector<double> kj = rank_key(ms[j], ref);
+        if (kj < kb) {
+            kb = kj;
+            best = (int)j;
+        }
+    }
+    return best;
 }
 
 }  // namespace
@@ -380,6 +436,162 @@ qaoa_status qaoa_optimize_spsa(qaoa_ctx c, int nq, const qaoa_cost *costs, const
         }
     if (final_expect)
         QAOA_TRY(run_batch(c, nq, costs, item_cost, B, p, gamma, beta, final_expect, nullptr, nullptr, nullptr));
+    return QAOA_OK;
+}
+
+qaoa_status qaoa_solve(qaoa_ctx c, qaoa_cost cost, const qaoa_solve_options *sopt, double *gamma, double *beta,
+                       int elite, uint64_t *elite_idx, double *elite_cost, int64_t *elite_count,
+                       qaoa_sample_metrics *depth_metrics, qaoa_solve_result *out) {
+    if (!c || !cost || !sopt || !gamma || !beta || !out) return fail(QAOA_ERR_INVALID_ARG, "null argument");
+    qaoa_solve_options o = *sopt;
+    for (int k = 0; k < 8; ++k)
+        if (o.reserved[k]) return fail(QAOA_ERR_INVALID_ARG, "reserved solve option field %d is not zero", k);
+    if (o.lr == 0) o.lr = 0.01;
+    if (o.beta1 == 0) o.beta1 = 0.9;
+    if (o.beta2 == 0) o.beta2 = 0.999;
+    if (o.eps == 0) o.eps = 1e-8;
+    if (o.c == 0) o.c = 0.1;
+    if (o.averaging == 0) o.averaging = 1;
+    if (o.p_max < 1 || o.p_max > SMALL_MAXP || (o.optimizer != 0 && o.optimizer != 1) || o.iterations < 1 ||
+        o.shots < 0 || o.averaging < 1 || o.random_starts < 1 || o.warm_perturb < 0 || o.final_shots < 1 ||
+        (o.include_warm != 0 && o.include_warm != 1) || !(o.warm_sigma >= 0) || !std::isfinite(o.gamma_range) ||
+        !std::isfinite(o.beta_range) || !(o.margin >= 0) || !(o.tol >= 0))
+        return fail(QAOA_ERR_INVALID_ARG, "solve options out of range");
+    if (elite < 0 || (elite > 0 && (!elite_idx || !elite_cost || !elite_count)))
+        return fail(QAOA_ERR_INVALID_ARG, "elite=%d needs elite_idx, elite_cost and elite_count", elite);
+    if (c->opt.state_fp64) return fail(QAOA_ERR_INVALID_ARG, "the search runs in complex64 only");
+    CUDA_TRY(cudaSetDevice(c->device));
+    const bool ref = o.use_reference != 0;
+    const double ref_cost = fixed_to_cost(cost->minval, cost);
+    const uint64_t ref_index = cost->argmin;
+    const long long S = o.final_shots;
+    struct Rep {
+        int p;
+        std::vector<double> g, b;
+        qaoa_sample_metrics m;
+        std::vector<uint64_t> idx;
+        std::vector<double> cst;
+        double E;
+    };
+    std::vector<Rep> reps;
+    std::vector<double> prev_g, prev_b;
+    int runs = 0;
+    for (int p = 1; p <= o.p_max; ++p) {
+        // initial points: lifted best, its perturbations, random points
+        std::vector<std::vector<double>> X;
+        uint32_t j = 0;
+        if (!prev_g.empty()) {
+            const std::vector<double> lg = lift_interp(prev_g), lb = lift_interp(prev_b);
+            std::vector<double> lifted(2 * p);
+            for (int l = 0; l < p; ++l) {
+                lifted[2 * l] = lg[l];
+                lifted[2 * l + 1] = lb[l];
+            }
+            if (o.include_warm) {
+                X.push_back(lifted);
+                ++j;
+            }
+            for (int r = 0; r < o.warm_perturb; ++r, ++j) {
+                std::vector<double> x = lifted;
+                for (int i = 0; i < 2 * p; ++i) x[i] += o.warm_sigma * start_normal(o.seed, (uint32_t)i, j, (uint32_t)p);
+                X.push_back(x);
+            }
+        }
+        for (int r = 0; r < o.random_starts; ++r, ++j) {
+            std::vector<double> x(2 * p);
+            for (int i = 0; i < 2 * p; ++i)
+                x[i] = ((i & 1) ? o.beta_range : o.gamma_range) * start_uniform(o.seed, (uint32_t)i, j, (uint32_t)p);
+            X.push_back(x);
+        }
+        const int B = (int)X.size();
+        std::vector<double> g((size_t)B * p), b((size_t)B * p);
+        for (int k = 0; k < B; ++k)
+            for (int l = 0; l < p; ++l) {
+                g[(size_t)k * p + l] = X[k][2 * l];
+                b[(size_t)k * p + l] = X[k][2 * l + 1];
+            }
+        // optimise every start of this depth as one batch
+        if (o.optimizer == 0) {
+            qaoa_spsa_options so;
+            std::memset(&so, 0, sizeof(so));
+            so.lr = o.lr;
+            so.beta1 = o.beta1;
+            so.beta2 = o.beta2;
+            so.eps = o.eps;
+            so.c = o.c;
+            so.c_decay = o.c_decay;
+            so.iterations = o.iterations;
+            so.shots = o.shots;
+            so.averaging = o.averaging;
+            so.seed = o.seed + (uint64_t)p * DEPTH_SEED_STEP;
+            QAOA_TRY(qaoa_optimize_spsa(c, 1, &cost, nullptr, B, p, g.data(), b.data(), &so, nullptr, nullptr));
+        } else {
+            qaoa_adam_options ao;
+            std::memset(&ao, 0, sizeof(ao));
+            ao.lr = o.lr;
+            ao.beta1 = o.beta1;
+            ao.beta2 = o.beta2;
+            ao.eps = o.eps;
+            ao.iterations = o.iterations;
+            QAOA_TRY(qaoa_optimize_adam(c, 1, &cost, nullptr, B, p, g.data(), b.data(), &ao, nullptr, nullptr));
+        }
+        runs += B;
+        // final shot-based evaluation of every candidate
+        std::vector<ItemState> st;
+        std::vector<double> E(B);
+        QAOA_TRY(run_batch(c, 1, &cost, nullptr, B, p, g.data(), b.data(), E.data(), nullptr, nullptr, &st));
+        QAOA_TRY(c->sample_out.ensure((size_t)B * S * 12 + 64, &c->held, c->opt.memory_budget));
+        unsigned long long *didx = c->sample_out.as<unsigned long long>();
+        int32_t *dtv = reinterpret_cast<int32_t *>(didx + (size_t)B * S);
+        std::vector<ShotSet> sets(B);
+        for (int k = 0; k < B; ++k) {
+            sets[k].state = k;
+            sets[k].shots = S;
+            sets[k].seed = o.seed;
+            sets[k].stream = FINAL_STREAM + ((uint64_t)p << 32) + (uint64_t)k;
+            sets[k].idx = didx + (size_t)k * S;
+            sets[k].tval = dtv + (size_t)k * S;
+        }
+        QAOA_TRY(measure(c, st, false, sets));
+        std::vector<uint64_t> hidx((size_t)B * S);
+        std::vector<int32_t> htv((size_t)B * S);
+        CUDA_TRY(cudaMemcpyAsync(hidx.data(), didx, hidx.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(cudaMemcpyAsync(htv.data(), dtv, htv.size() * 4, cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+        std::vector<qaoa_sample_metrics> ms(B);
+        std::vector<double> hc((size_t)B * S);
+        for (size_t t = 0; t < hc.size(); ++t) hc[t] = fixed_to_cost(htv[t], cost);
+        for (int k = 0; k < B; ++k)
+            QAOA_TRY(qaoa_sample_stats(S, hidx.data() + (size_t)k * S, hc.data() + (size_t)k * S, o.margin, 0,
+                                       nullptr, nullptr, nullptr, ref ? 1 : 0, ref_cost, ref_index, o.tol, &ms[k]));
+        const int kb = best_candidate(ms, ref);
+        Rep r;
+        r.p = p;
+        r.g.assign(g.begin() + (size_t)kb * p, g.begin() + (size_t)(kb + 1) * p);
+        r.b.assign(b.begin() + (size_t)kb * p, b.begin() + (size_t)(kb + 1) * p);
+        r.m = ms[kb];
+        r.idx.assign(hidx.begin() + (size_t)kb * S, hidx.begin() + (size_t)(kb + 1) * S);
+        r.cst.assign(hc.begin() + (size_t)kb * S, hc.begin() + (size_t)(kb + 1) * S);
+        r.E = E[kb];
+        prev_g = r.g;
+        prev_b = r.b;
+        if (depth_metrics) depth_metrics[p - 1] = r.m;
+        reps.push_back(std::move(r));
+    }
+    std::vector<qaoa_sample_metrics> rm;
+    for (const Rep &r : reps) rm.push_back(r.m);
+    const Rep &best = reps[best_candidate(rm, ref)];
+    for (int l = 0; l < o.p_max; ++l) {
+        gamma[l] = l < best.p ? best.g[l] : 0.0;
+        beta[l] = l < best.p ? best.b[l] : 0.0;
+    }
+    qaoa_sample_metrics m;
+    QAOA_TRY(qaoa_sample_stats(S, best.idx.data(), best.cst.data(), o.margin, elite, elite_idx, elite_cost,
+                               elite_count, ref ? 1 : 0, ref_cost, ref_index, o.tol, &m));
+    out->best_p = best.p;
+    out->runs = runs;
+    out->expect = best.E;
+    out->metrics = m;
     return QAOA_OK;
 }
 

@@ -189,4 +189,128 @@ void classify(const Canonical &c, const int32_t *qpu_of, int64_t *n_local, int64
     if (n_cross_all) *n_cross_all = cra;
 }
 
+// Graph-aware greedy allocation (Sec. 3.1): edge weight |b_ij|; QPU m opens
+// with the free variable of largest weighted degree towards the free
+// variables, then takes the free variable with the largest total weight to
+// its members (ties: larger weighted degree to the free variables, then the
+// smaller index) until it holds min(c_m, free - QPUs still to open).
+qaoa_status graph_aware(const Canonical &c, int M, const std::vector<int32_t> &caps, int32_t *qpu_of) {
+    const int n = c.n;
+    auto w = [&](int i, int j) {
+        return i == j ? 0.0 : std::fabs(i < j ? c.b[(size_t)i * n + j] : c.b[(size_t)j * n + i]);
+    };
+    std::vector<char> freev(n, 1);
+    int nfree = n;
+    for (int i = 0; i < n; ++i) qpu_of[i] = -1;
+    auto free_degree = [&](int v) {
+        double d = 0.0;
+        for (int u = 0; u < n; ++u)
+            if (freev[u] && u != v) d += w(v, u);
+        return d;
+    };
+    for (int m = 0; m < M && nfree > 0; ++m) {
+        const int take = std::min<int>(caps[m], nfree - (M - m - 1));
+        if (take <= 0) continue;
+        std::vector<int> members;
+        int seed = -1;
+        double sd = 0.0;
+        for (int v = 0; v < n; ++v) {
+            if (!freev[v]) continue;
+            const double d = free_degree(v);
+            if (seed < 0 || d > sd) {
+                seed = v;
+                sd = d;
+            }
+        }
+        members.push_back(seed);
+        freev[seed] = 0;
+        --nfree;
+        while ((int)members.size() < take && nfree > 0) {
+            int best = -1;
+            double bw = 0.0, bd = 0.0;
+            for (int v = 0; v < n; ++v) {
+                if (!freev[v]) continue;
+                double tw = 0.0;
+                for (int u : members) tw += w(v, u);
+                const double d = free_degree(v);
+                if (best < 0 || tw > bw || (tw == bw && d > bd)) {
+                    best = v;
+                    bw = tw;
+                    bd = d;
+                }
+            }
+            members.push_back(best);
+            freev[best] = 0;
+            --nfree;
+        }
+        for (int v : members) qpu_of[v] = m;
+    }
+    return QAOA_OK;
+}
+
 }  // namespace qaoa
+
+namespace {
+
+qaoa_status capacities(int n, int M, const int32_t *caps, std::vector<int32_t> *out) {
+    if (n < 1 || M < 1 || M > n) return qaoa::fail(QAOA_ERR_INVALID_ARG, "bad n=%d or M=%d", n, M);
+    out->resize(M);
+    int64_t tot = 0;
+    for (int m = 0; m < M; ++m) {
+        (*out)[m] = caps ? caps[m] : (n / M + (m < n % M ? 1 : 0));
+        if ((*out)[m] < 1) return qaoa::fail(QAOA_ERR_ALLOCATION, "capacity of QPU %d is %d < 1", m, (*out)[m]);
+        tot += (*out)[m];
+    }
+    if (tot < n) return qaoa::fail(QAOA_ERR_ALLOCATION, "total capacity %lld < n=%d", (long long)tot, n);
+    return QAOA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+qaoa_status qaoa_partition_graph(const qaoa_qubo *q, int M, const int32_t *caps, int32_t *qpu_of) {
+    if (!q || !qpu_of) return qaoa::fail(QAOA_ERR_INVALID_ARG, "null argument");
+    qaoa::Canonical c;
+    qaoa_status st = qaoa::canonicalize(q, &c);
+    if (st) return st;
+    std::vector<int32_t> cp;
+    if ((st = capacities(c.n, M, caps, &cp))) return st;
+    if ((st = qaoa::graph_aware(c, M, cp, qpu_of))) return st;
+    return qaoa::partition(c.n, M, cp.data(), qpu_of, qpu_of);  // validate_allocation
+}
+
+qaoa_status qaoa_allocation_candidates(const qaoa_qubo *q, int M, const int32_t *caps, const int32_t *manual, int p,
+                                       int32_t *qpu_of, int32_t *kind, int64_t *cross, int64_t *remote_cx) {
+    if (!q || !qpu_of || !kind || p < 0) return qaoa::fail(QAOA_ERR_INVALID_ARG, "null argument or p < 0");
+    qaoa::Canonical c;
+    qaoa_status st = qaoa::canonicalize(q, &c);
+    if (st) return st;
+    const int n = c.n;
+    std::vector<int32_t> cp;
+    if ((st = capacities(n, M, caps, &cp))) return st;
+    std::vector<std::vector<int32_t>> cand(3, std::vector<int32_t>(n));
+    if ((st = qaoa::partition(n, M, cp.data(), nullptr, cand[0].data()))) return st;
+    if ((st = qaoa::graph_aware(c, M, cp, cand[1].data()))) return st;
+    if ((st = qaoa::partition(n, M, cp.data(), cand[1].data(), cand[1].data()))) return st;
+    const int nc = manual ? 3 : 2;
+    if (manual && (st = qaoa::partition(n, M, cp.data(), manual, cand[2].data()))) return st;
+    const int prio[3] = {2, 1, 0};  // on equal cross counts: manual, graph-aware, contiguous
+    int best = -1;
+    int64_t bc = 0;
+    for (int k = 0; k < 3; ++k) {
+        int64_t loc = 0, cr = -1;
+        if (k < nc) qaoa::classify(c, cand[k].data(), &loc, &cr, nullptr);
+        if (cross) cross[k] = cr;
+        if (remote_cx) remote_cx[k] = cr < 0 ? -1 : 2 * cr * p;
+        if (k < nc && (best < 0 || cr < bc || (cr == bc && prio[k] < prio[best]))) {
+            best = k;
+            bc = cr;
+        }
+    }
+    for (int i = 0; i < n; ++i) qpu_of[i] = cand[best][i];
+    *kind = best;
+    return QAOA_OK;
+}
+
+}  // extern "C"

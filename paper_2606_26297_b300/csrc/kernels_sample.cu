@@ -1,16 +1,18 @@
 // Measurement of a statevector by shots (the shot-based objective of Sec. 3.4
 // and the final evaluation of Sec. 3.6), as inverse-CDF sampling on exact
 // integer weights:
-//   P_x = fl(re^2) + fl(im^2) in FP64,  q_x = floor(P_x 2^60),  Q = sum q_x,
+//   q_x = floor(re^2 2^60) + floor(im^2 2^60) (exact squares), Q = sum q_x,
 //   shot s: T = floor(R_s Q / 2^64), x_s = min { x : q_0 + ... + q_x > T }.
-// Integer prefix sums are exact, so the blocked order used here gives the same
-// x_s as a sequential scan.  Three launches per request:
-//   1. weights: one CTA per super-chunk (64 chunks of 1024 amplitudes), chunk
+// The weights use integer arithmetic only (the FP64 pipe of this GPU is a
+// small fraction of its integer rate), and integer prefix sums are exact, so
+// the blocked order used here gives the same x_s as a sequential scan.  Three
+// launches per request:
+//   1. weights: one CTA per super-chunk (64 chunks of 256 amplitudes), chunk
 //      sums and their inclusive prefix inside the super-chunk, super totals;
 //   2. scan: one CTA per item, exclusive prefix of the super totals and Q;
 //   3. shots: one warp per shot, a 32-ary search over the super prefixes, a
 //      ballot over the 64 chunk prefixes and a warp scan inside the chunk.
-// Traffic: one read of the state for (1), one chunk (8 KB) per shot for (3).
+// Traffic: one read of the state for (1), one chunk (2 KB) per shot for (3).
 #include "kernels_misc.h"
 #include "philox.cuh"
 
@@ -31,7 +33,7 @@ struct Geo {
 __host__ __device__ inline Geo geo_of(int n) {
     Geo g;
     g.N = 1ull << n;
-    g.ch = n >= 10 ? 1024 : (1 << n);
+    g.ch = n >= 8 ? 256 : (1 << n);
     const unsigned long long chunks = g.N / (unsigned long long)g.ch;
     g.cps = chunks >= 64 ? 64 : (int)chunks;
     g.per = g.ch >= 32 ? g.ch / 32 : 1;
@@ -39,11 +41,34 @@ __host__ __device__ inline Geo geo_of(int n) {
     return g;
 }
 
+// floor(v^2 2^60) for |v| < 2 (larger or non-finite values saturate at 2^62):
+// v = M 2^e2 with an integer mantissa M, so v^2 2^60 = M^2 2^(2 e2 + 60).
+__device__ __forceinline__ unsigned long long sq60(float v) {
+    const uint32_t u = __float_as_uint(v) & 0x7FFFFFFFu;
+    const int E = (int)(u >> 23);
+    const unsigned long long M = E ? ((u & 0x7FFFFFu) | 0x800000u) : (u & 0x7FFFFFu);
+    const int sh = 2 * (E ? E - 150 : -149) + 60;
+    const unsigned long long m2 = M * M;
+    if (sh >= 0) return sh > 14 ? (1ull << 62) : (m2 << sh);
+    return sh <= -64 ? 0ull : (m2 >> -sh);
+}
+
+__device__ __forceinline__ unsigned long long sq60(double v) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+    const int E = (int)(u >> 52);
+    const unsigned long long M = E ? ((u & 0xFFFFFFFFFFFFFull) | (1ull << 52)) : (u & 0xFFFFFFFFFFFFFull);
+    const int sh = 2 * (E ? E - 1075 : -1074) + 60;  // M^2 < 2^106 as (hi, lo)
+    const unsigned long long lo = M * M, hi = __umul64hi(M, M);
+    if (sh > -44) return 1ull << 62;
+    const int r = -sh;
+    if (r >= 128) return 0ull;
+    if (r >= 64) return hi >> (r - 64);
+    return (lo >> r) | (hi << (64 - r));
+}
+
 template <typename E>
 __device__ __forceinline__ unsigned long long weight_of(const E &a) {
-    const double re = (double)a.x, im = (double)a.y;
-    const double P = __dadd_rn(__dmul_rn(re, re), __dmul_rn(im, im));
-    return __double2ull_rz(P * 1152921504606846976.0);  // 2^60
+    return sq60(a.x) + sq60(a.y);
 }
 
 __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {

@@ -42,6 +42,7 @@ qaoa_status make_fixed_point(const Canonical &c, FixedPoint *out);
 
 // Sec. 3.1 allocation helpers and Sec. 3.2 classification.
 qaoa_status partition(int n, int M, const int32_t *caps, const int32_t *manual, int32_t *qpu_of);
+qaoa_status graph_aware(const Canonical &c, int M, const std::vector<int32_t> &caps, int32_t *qpu_of);
 void classify(const Canonical &c, const int32_t *qpu_of, int64_t *n_local, int64_t *n_cross,
               int64_t *n_cross_all);
 

@@ -66,6 +66,22 @@ class qaoa_spsa_options(ctypes.Structure):
                 ("pad", ctypes.c_int32), ("seed", ctypes.c_uint64), ("reserved", ctypes.c_int32 * 6)]
 
 
+class qaoa_solve_options(ctypes.Structure):
+    _fields_ = [("p_max", ctypes.c_int32), ("optimizer", ctypes.c_int32), ("iterations", ctypes.c_int32),
+                ("shots", ctypes.c_int32), ("averaging", ctypes.c_int32), ("random_starts", ctypes.c_int32),
+                ("warm_perturb", ctypes.c_int32), ("include_warm", ctypes.c_int32), ("final_shots", ctypes.c_int32),
+                ("use_reference", ctypes.c_int32), ("lr", ctypes.c_double), ("beta1", ctypes.c_double),
+                ("beta2", ctypes.c_double), ("eps", ctypes.c_double), ("c", ctypes.c_double),
+                ("c_decay", ctypes.c_double), ("warm_sigma", ctypes.c_double), ("gamma_range", ctypes.c_double),
+                ("beta_range", ctypes.c_double), ("margin", ctypes.c_double), ("tol", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("reserved", ctypes.c_int32 * 8)]
+
+
+class qaoa_solve_result(ctypes.Structure):
+    _fields_ = [("best_p", ctypes.c_int32), ("runs", ctypes.c_int32), ("expect", ctypes.c_double),
+                ("metrics", qaoa_sample_metrics)]
+
+
 _P = ctypes.c_void_p
 _I = ctypes.c_int
 _D = ctypes.c_double
@@ -101,7 +117,12 @@ _SIGS = {
                            ctypes.POINTER(qaoa_sample_metrics)], _I),
     "qaoa_optimize_spsa": ([_P, _I, ctypes.POINTER(_P), _PI32, _I, _I, _PD, _PD,
                             ctypes.POINTER(qaoa_spsa_options), _PD, _PD], _I),
+    "qaoa_solve": ([_P, _P, ctypes.POINTER(qaoa_solve_options), _PD, _PD, _I, _PU64, _PD, _PI64,
+                    ctypes.POINTER(qaoa_sample_metrics), ctypes.POINTER(qaoa_solve_result)], _I),
     "qaoa_partition": ([_I, _I, _PI32, _PI32, _PI32], _I),
+    "qaoa_partition_graph": ([ctypes.POINTER(qaoa_qubo), _I, _PI32, _PI32], _I),
+    "qaoa_allocation_candidates": ([ctypes.POINTER(qaoa_qubo), _I, _PI32, _PI32, _I, _PI32, _PI32, _PI64, _PI64],
+                                   _I),
     "qaoa_classify": ([_P, _PI32, _I, _PI64, _PI64, _PI64, _PI64], _I),
     "qaoa_check_factorisation": ([_P, _P, _PI32, _D, _PI64, _PD], _I),
     "qaoa_profile_read": ([_P, _I, _PI64, _PD, _PD, _I], _I),
@@ -385,6 +406,44 @@ def qaoa_optimize_spsa(ctx, costs, gamma, beta, iterations: int, item_cost=None,
     return g, b, hist, E
 
 
+def _metrics_dict(m) -> dict:
+    return {f: getattr(m, f) for f, _ in qaoa_sample_metrics._fields_}
+
+
+def qaoa_solve(ctx, cost, p_max: int, optimizer: str = "spsa", iterations: int = 50, shots: int = 0,
+               averaging: int = 1, random_starts: int = 2, warm_perturb: int = 1, include_warm: bool = True,
+               final_shots: int = 4096, use_reference: bool = True, lr: float = 0.0, beta1: float = 0.0,
+               beta2: float = 0.0, eps: float = 0.0, c: float = 0.1, c_decay: float = 0.101,
+               warm_sigma: float = 0.05, gamma_range: float = 0.5, beta_range: float = 1.5707963267948966,
+               margin: float = 0.0, tol: float = 1e-9, seed: int = 0, elite: int = 10) -> dict:
+    """Algorithm 1 (Sec. 3.5): depth progression with warm starts and random
+    restarts.  Returns a dict with the selected depth, angles, metrics, elite
+    set and each depth's representative metrics."""
+    o = qaoa_solve_options()
+    o.p_max, o.optimizer, o.iterations = int(p_max), {"spsa": 0, "adam": 1}[optimizer], int(iterations)
+    o.shots, o.averaging, o.random_starts = int(shots), int(averaging), int(random_starts)
+    o.warm_perturb, o.include_warm, o.final_shots = int(warm_perturb), int(bool(include_warm)), int(final_shots)
+    o.use_reference = int(bool(use_reference))
+    o.lr, o.beta1, o.beta2, o.eps, o.c, o.c_decay = float(lr), float(beta1), float(beta2), float(eps), float(c), \
+        float(c_decay)
+    o.warm_sigma, o.gamma_range, o.beta_range = float(warm_sigma), float(gamma_range), float(beta_range)
+    o.margin, o.tol, o.seed = float(margin), float(tol), int(seed) & 0xFFFFFFFFFFFFFFFF
+    g = np.zeros(int(p_max))
+    b = np.zeros(int(p_max))
+    ne = max(int(elite), 1)
+    ei, ec, en = np.zeros(ne, dtype=np.uint64), np.zeros(ne), np.zeros(ne, dtype=np.int64)
+    dm = (qaoa_sample_metrics * int(p_max))()
+    r = qaoa_solve_result()
+    _check(_lib.qaoa_solve(ctx, cost, ctypes.byref(o), _dptr(g), _dptr(b), int(elite), ei.ctypes.data_as(_PU64),
+                           _dptr(ec), en.ctypes.data_as(_PI64), dm, ctypes.byref(r)))
+    m = _metrics_dict(r.metrics)
+    return {"best_p": r.best_p, "runs": r.runs, "expect": r.expect, "gamma": g[:r.best_p].copy(),
+            "beta": b[:r.best_p].copy(), "metrics": m,
+            "elite": [(int(ei[i]), float(ec[i]), int(en[i]), float(en[i]) / m["shots"])
+                      for i in range(int(elite)) if en[i] > 0],
+            "depth_metrics": [_metrics_dict(dm[i]) for i in range(int(p_max))]}
+
+
 # ---- DQAOA ----------------------------------------------------------------------------------
 
 def qaoa_partition(n: int, M: int, caps=None, manual=None) -> np.ndarray:
@@ -394,6 +453,36 @@ def qaoa_partition(n: int, M: int, caps=None, manual=None) -> np.ndarray:
     _check(_lib.qaoa_partition(int(n), int(M), None if c is None else c.ctypes.data_as(_PI32),
                                None if m is None else m.ctypes.data_as(_PI32), out.ctypes.data_as(_PI32)))
     return out
+
+
+def qaoa_partition_graph(H, f, c0: float, caps, dtype: str = "f64") -> np.ndarray:
+    """Graph-aware allocation of the QUBO (H, f, c0) for the capacities caps."""
+    qb, keep = make_qubo(H, f, c0, dtype)
+    n = qb.n
+    c = np.ascontiguousarray(np.asarray(caps, dtype=np.int32))
+    out = np.zeros(n, dtype=np.int32)
+    _check(_lib.qaoa_partition_graph(ctypes.byref(qb), len(c), c.ctypes.data_as(_PI32), out.ctypes.data_as(_PI32)))
+    return out
+
+
+def qaoa_allocation_candidates(H, f, c0: float, caps, manual=None, p: int = 1, dtype: str = "f64") -> dict:
+    """Contiguous, graph-aware and manual candidates scored by cross-QPU
+    couplings; returns the selected allocation and every candidate's counts."""
+    qb, keep = make_qubo(H, f, c0, dtype)
+    n = qb.n
+    c = np.ascontiguousarray(np.asarray(caps, dtype=np.int32))
+    m = None if manual is None else np.ascontiguousarray(np.asarray(manual, dtype=np.int32))
+    out = np.zeros(n, dtype=np.int32)
+    kind = ctypes.c_int32()
+    cross = np.zeros(3, dtype=np.int64)
+    rcx = np.zeros(3, dtype=np.int64)
+    _check(_lib.qaoa_allocation_candidates(ctypes.byref(qb), len(c), c.ctypes.data_as(_PI32),
+                                           None if m is None else m.ctypes.data_as(_PI32), int(p),
+                                           out.ctypes.data_as(_PI32), ctypes.byref(kind),
+                                           cross.ctypes.data_as(_PI64), rcx.ctypes.data_as(_PI64)))
+    k = 3 if manual is not None else 2
+    return {"qpu_of": out, "kind": kind.value, "cross": [int(v) for v in cross[:k]],
+            "remote_cx": [int(v) for v in rcx[:k]]}
 
 
 def qaoa_classify(cost, qpu_of, p: int):

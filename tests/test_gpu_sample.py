@@ -42,7 +42,7 @@ def _cost(q, ctx, Q):
     return q.qaoa_build_cost(ctx, Q.H, Q.f, Q.c0, "i32" if Q.dtype == "i32" else "f32")
 
 
-@pytest.mark.parametrize("n", [1, 3, 5, 9, 10, 12, 13, 16, 17, 19, 22])
+@pytest.mark.parametrize("n", [1, 3, 5, 7, 8, 9, 12, 14, 15, 17, 19, 22])
 def test_sample_bit_exact_philox(q, ctx, n):
     """Shots of an uploaded random state: device Philox stream and inverse CDF
     equal the oracle's index for index (one chunk, one super-chunk, several,
@@ -269,4 +269,65 @@ def test_spsa_rejects_bad_options(q, ctx):
             q.qaoa_optimize_spsa(ctx, [cost], g0, b0, 2, **kw)
     with pytest.raises(q.QaoaError):
         q.qaoa_optimize_spsa(ctx, [cost], g0, b0, 0)
+    q.qaoa_cost_destroy(cost)
+
+
+def _solve_opts(**kw):
+    o = dict(p_max=2, optimizer="adam", iterations=15, shots=0, averaging=1, random_starts=2, warm_perturb=1,
+             include_warm=True, final_shots=3000, use_reference=True, lr=0.05, beta1=0.9, beta2=0.999, eps=1e-8,
+             c=0.1, c_decay=0.101, warm_sigma=0.05, gamma_range=0.3, beta_range=1.0, margin=0.0, tol=1e-9,
+             seed=11, elite=5)
+    o.update(kw)
+    return o
+
+
+@pytest.mark.parametrize("n,use_ref", [(6, True), (7, False)])
+def test_solve_vs_oracle_exact_adam(q, ctx, n, use_ref):
+    """Algorithm 1 with exact-gradient Adam against the oracle's Algorithm 1:
+    the same starts at every depth (lifted, perturbed, random), the same
+    selected depth, angles within 1e-4, and final metrics within a few shots
+    (the GPU measures its FP32 state, the oracle its FP64 state)."""
+    Q = inst.upper_int_qubo(n, 5000 + n)
+    o = _solve_opts(use_reference=use_ref)
+    cost = _cost(q, ctx, Q)
+    kw = {k: v for k, v in o.items() if k not in ("elite",)}
+    r = q.qaoa_solve(ctx, cost, elite=o["elite"], **kw)
+    F = oracle.cost_table(oracle.canonical_of(Q))
+    from oracle import search as osr
+    ro = osr.solve(F, dict(o, optimizer="adam"))
+    assert r["best_p"] == ro["best_p"]
+    assert np.max(np.abs(oracle.interleave(r["gamma"], r["beta"]) - ro["x"])) <= 1e-4
+    mo = ro["metrics"]
+    S = o["final_shots"]
+    assert r["metrics"]["best_cost"] == mo["best_cost"]
+    for k in ("p_best_cost", "low_cost_mass", "p_best_index"):
+        assert abs(r["metrics"][k] - mo[k]) <= 3.0 / S
+    assert abs(r["metrics"]["mean_cost"] - mo["mean_cost"]) <= 3.0 * float(F.max() - F.min()) / S
+    assert r["runs"] == 2 + 4
+    assert len(r["depth_metrics"]) == 2
+    assert abs(r["expect"] - oracle.expectation(F, oracle.evolve(F, r["gamma"], r["beta"]))) <= E_TOL * np.max(np.abs(F))
+    q.qaoa_cost_destroy(cost)
+
+
+def test_solve_spsa_shots_runs_and_ranks(q, ctx):
+    """Algorithm 1 with shot-based SPSA on n = 14 (pass path): deterministic for
+    a seed, every depth reported, the selected candidate ranked best among the
+    depth representatives, and its elite set consistent with its metrics."""
+    Q = inst.upper_int_qubo(14, 5100)
+    cost = _cost(q, ctx, Q)
+    kw = dict(p_max=3, optimizer="spsa", iterations=20, shots=1024, random_starts=2, warm_perturb=1,
+              final_shots=4096, gamma_range=0.2, seed=21, lr=0.03)
+    r1 = q.qaoa_solve(ctx, cost, **kw)
+    r2 = q.qaoa_solve(ctx, cost, **kw)
+    assert r1["best_p"] == r2["best_p"] and np.array_equal(r1["gamma"], r2["gamma"])
+    from oracle import search as osr
+    k = osr.best_of([dict(m, best_cost_matches_ref=bool(m["best_cost_matches_ref"]),
+                          best_index_matches_ref=bool(m["best_index_matches_ref"])) for m in r1["depth_metrics"]],
+                    True)
+    assert r1["best_p"] == k + 1
+    m = r1["metrics"]
+    assert r1["elite"][0][2] >= r1["elite"][-1][2]
+    assert m["best_cost"] <= min(e[1] for e in r1["elite"])
+    assert sum(e[2] for e in r1["elite"]) <= m["shots"]
+    assert r1["runs"] == 2 + 4 + 4
     q.qaoa_cost_destroy(cost)

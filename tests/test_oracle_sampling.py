@@ -163,3 +163,21 @@ def test_spsa_signs_balanced():
     s = np.concatenate([osm.spsa_signs(77, k, b, 16) for k in range(40) for b in range(3)])
     assert set(np.unique(s)) == {-1.0, 1.0}
     assert abs(float(s.mean())) < 5 / math.sqrt(len(s))
+
+
+def test_weights_exact_fractions():
+    """q = floor(re^2 2^60) + floor(im^2 2^60) against exact rational
+    arithmetic (fractions.Fraction of the stored float) for float32 and float64
+    components: random values, zero, +-1, powers of two, float32 denormals."""
+    from fractions import Fraction
+    rng = np.random.default_rng(8)
+    vals32 = np.concatenate([rng.standard_normal(300) * 0.3, [0.0, 1.0, -1.0, 2.0 ** -20, 2.0 ** -31, 2.0 ** -40,
+                                                               1e-38, 1e-44, -3e-45]]).astype(np.float32)
+    vals64 = np.concatenate([rng.standard_normal(300) * 0.3, [0.0, 1.0, -1.0, 2.0 ** -31, 1e-300]])
+    for vals in (vals32, vals64):
+        a = vals[: len(vals) // 2 * 2]
+        z = (a[0::2] + 1j * a[1::2]).astype(np.complex64 if vals.dtype == np.float32 else np.complex128)
+        got = osm.weights(z)
+        for k, c in enumerate(z):
+            want = sum(math.floor(Fraction(float(v)) ** 2 * 2 ** 60) for v in (c.real, c.imag))
+            assert int(got[k]) == want
