@@ -335,7 +335,13 @@ def run_workload(args):
                `--shots` shots per request: weights pass (one read of the
                state) and shot kernel timed with CUDA events;
       spsa     SPSA-Adam with shots (Sec. 3.4): 16 starts on the n=20 integer
-               QUBO, p=4, 1024 shots per evaluation, `--iters` iterations."""
+               QUBO, p=4, 1024 shots per evaluation, `--iters` iterations;
+      telegate gate-level distributed circuit (Sec. 3.3) of a dense integer
+               n=12 QUBO on three QPUs of four, p=2: 1184 trajectories, time
+               per trajectory and fidelity against the monolithic state;
+      solve    Algorithm 1 (Sec. 3.5) on the n=20 integer QUBO: depths 1..3,
+               4 random starts + lifted + 2 perturbed per depth, SPSA-Adam with
+               1024 shots, `--iters` iterations, 8192 final shots."""
     import torch
     from paper_2606_26297_b300 import build_lib
     build_lib.build()
@@ -491,6 +497,37 @@ def run_workload(args):
                     "evaluations_per_s": 32 * args.iters / dt,
                     "mean_E_start": float(np.mean(E0)), "mean_E_end": float(np.mean(Ef))})
         q.qaoa_cost_destroy(cost)
+    elif args.workload == "telegate":
+        Q = inst.upper_int_qubo(12, 7002)
+        cost = q.qaoa_build_cost(ctx, Q.H, Q.f, Q.c0, "i32")
+        qpu = [0] * 4 + [1] * 4 + [2] * 4
+        g, b = [0.05, 0.03], [0.5, 0.25]
+        T = 1184
+        q.qaoa_telegate_simulate(ctx, cost, qpu, g, b, 148, 1)
+        t, (fid, _, cnt) = _event_time(torch, stream, lambda: q.qaoa_telegate_simulate(ctx, cost, qpu, g, b, T, 2),
+                                       max(args.steps, 1))
+        tm, _ = _event_time(torch, stream, lambda: q.qaoa_state_destroy(q.qaoa_forward(ctx, cost, g, b)), 20)
+        res.update({"n": 12, "qpus": [4, 4, 4], "p": 2, "trajectories": T, "ms_per_request": 1e3 * t,
+                    "us_per_trajectory": 1e6 * t / T, "ops_per_trajectory": cnt["ops"],
+                    "op_passes_per_s": cnt["ops"] * T / t, "counts": cnt,
+                    "min_fidelity": float(np.min(fid)), "monolithic_forward_ms": 1e3 * tm})
+        q.qaoa_cost_destroy(cost)
+    elif args.workload == "solve":
+        Q, _, _ = inst.workload_batch20()
+        cost = q.qaoa_build_cost(ctx, Q.H, Q.f, Q.c0, "i32")
+        kw = dict(p_max=3, optimizer="spsa", iterations=args.iters, shots=1024, random_starts=4, warm_perturb=2,
+                  final_shots=8192, gamma_range=0.7, seed=3, lr=0.02)
+        q.qaoa_solve(ctx, cost, **dict(kw, iterations=2))
+        t0 = time.perf_counter()
+        r = q.qaoa_solve(ctx, cost, **kw)
+        dt = time.perf_counter() - t0
+        info = q.qaoa_cost_info(cost)
+        evals = sum(2 * kw["iterations"] * b for b in (4, 7, 7))
+        res.update({"n": 20, "p_max": 3, "runs": r["runs"], "iters": args.iters, "seconds": dt,
+                    "objective_evaluations": evals, "evaluations_per_s": evals / dt, "best_p": r["best_p"],
+                    "best_sampled_cost": r["metrics"]["best_cost"], "brute_force_min": info.get("min_cost"),
+                    "p_best_cost": r["metrics"]["p_best_cost"], "exact_E": r["expect"]})
+        q.qaoa_cost_destroy(cost)
     print(json.dumps(res), flush=True)
     q.qaoa_ctx_destroy(ctx)
     return 0
@@ -506,9 +543,10 @@ def main():
     ap.add_argument("--n", type=int, default=N_QUBITS, help="qubits (default: the n=30 workload)")
     ap.add_argument("--p", type=int, default=DEPTH, help="depth (default 8)")
     ap.add_argument("--workload", default="",
-                    choices=["", "fd", "batch20", "ragged", "uc32", "autotune", "sample", "spsa"],
+                    choices=["", "fd", "batch20", "ragged", "uc32", "autotune", "sample", "spsa", "solve",
+                             "telegate"],
                     help="a secondary measurement instead of the headline step")
-    ap.add_argument("--iters", type=int, default=200, help="Adam steps for --workload batch20/uc32/spsa")
+    ap.add_argument("--iters", type=int, default=200, help="optimiser steps for --workload batch20/uc32/spsa/solve")
     ap.add_argument("--shots", type=int, default=1 << 20, help="shots per request for --workload sample")
     args = ap.parse_args()
     if args.workload:

@@ -431,6 +431,39 @@ qaoa_status qaoa_classify(qaoa_cost cost, const int32_t *qpu_of, int p, int64_t 
 qaoa_status qaoa_check_factorisation(qaoa_ctx ctx, qaoa_cost cost, const int32_t *qpu_of,
                                      double gamma_probe, int64_t *mismatches, double *max_phase_err);
 
+/* ---- explicit distributed circuit (Sec. 3.3) ------------------------------ */
+
+typedef struct {
+    int64_t ops;           /* operations in the circuit */
+    int64_t local_zz;      /* couplings implemented locally, summed over the layers */
+    int64_t cross_zz;      /* couplings across QPUs, summed over the layers */
+    int64_t remote_cx;     /* remote CNOTs = 2 cross_zz (the estimate 2 cross p of Sec. 3.1) */
+    int64_t measurements;  /* mid-circuit measurements, 2 per remote CNOT */
+    int64_t resets;        /* communication-qubit resets, 2 per remote CNOT */
+    int64_t feedforward;   /* outcome-controlled Pauli corrections, 2 per remote CNOT */
+} qaoa_telegate_counts;
+
+/* Simulate the distributed QAOA circuit gate by gate (Sec. 3.3) for
+ * `trajectories` independent measurement records, to confirm that the
+ * TeleGate protocol reproduces the monolithic state and to count its
+ * overhead.  n data qubits (n <= 12) plus two communication qubits cA = bit
+ * n, cB = bit n + 1; every data qubit starts in |+>; each layer applies the
+ * global phase -g c0, a phase -g (l_i + sum_j b_ij / 2) on every qubit i, for
+ * each coupling b_ij != 0 (i < j) CNOT(i, j), phase +g b_ij / 2 on j,
+ * CNOT(i, j), and RX(2 beta) on every data qubit; a CNOT between qubits on
+ * different QPUs (qpu_of, host, n entries) is a remote CNOT: reset cA and cB
+ * (they are in basis states), H cA, CNOT cA -> cB, CNOT i -> cA, measure cA
+ * (m1), CNOT cB -> j, H cB, measure cB (m2), X^m1 on j, Z^m2 on i.
+ * Measurement k of trajectory t draws u = ((w0 + 2^32 w1) >> 11) 2^-53 from
+ * Philox4x32-10 at counter (k, t, 0, 0x54454C45), key (seed lo, seed hi),
+ * and gives 1 when u < P(1).  Outputs (host): fidelity[t] =
+ * |<psi_mono | psi_t>|^2 against the library's own monolithic state
+ * (qaoa_forward); amps (NULL allowed): trajectories x 2^n complex64
+ * data-qubit states (the communication qubits folded out); *counts. */
+qaoa_status qaoa_telegate_simulate(qaoa_ctx ctx, qaoa_cost cost, const int32_t *qpu_of, int p,
+                                   const double *gamma, const double *beta, int trajectories, uint64_t seed,
+                                   double *fidelity, float *amps, qaoa_telegate_counts *counts);
+
 /* ---- allocation-free expectation -----------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers
  * that must not allocate device memory when they evaluate <H_C>: a host

@@ -199,6 +199,89 @@ int best_candidate(const std::vector<qaoa_sample_metrics> &ms, bool ref) {
     return best;
 }
 
+// ---- distributed (TeleGate) circuit, Sec. 3.3 ------------------------------------
+
+TgOp tg(int kind, int q0, int q1 = 0, double theta = 0.0) {
+    TgOp o;
+    o.kind = kind;
+    o.q0 = q0;
+    o.q1 = q1;
+    o.midx = -1;
+    o.c = (float)std::cos(theta);
+    o.s = (float)std::sin(theta);
+    return o;
+}
+
+// Remote CNOT (control a, target t) through the communication pair (cA = n,
+// cB = n + 1): reset both, entangle them, couple cA to the control and
+// measure it, couple cB to the target and measure it in the X basis, then
+// X^m1 on the target and Z^m2 on the control.
+void remote_cnot(std::vector<TgOp> &ops, int n, int a, int t, int *midx) {
+    const int cA = n, cB = n + 1;
+    ops.push_back(tg(TG_RESET, cA));
+    ops.push_back(tg(TG_RESET, cB));
+    ops.push_back(tg(TG_H, cA));
+    ops.push_back(tg(TG_CNOT, cA, cB));
+    ops.push_back(tg(TG_CNOT, a, cA));
+    ops.push_back(tg(TG_MEASURE, cA, 0));
+    ops.back().midx = (*midx)++;
+    ops.push_back(tg(TG_CNOT, cB, t));
+    ops.push_back(tg(TG_H, cB));
+    ops.push_back(tg(TG_MEASURE, cB, 1));
+    ops.back().midx = (*midx)++;
+    ops.push_back(tg(TG_XIF, t, 0));
+    ops.push_back(tg(TG_ZIF, a, 1));
+}
+
+// The distributed circuit in the 0/1 form of the objective, so that it equals
+// exp(-i g F) exactly: each qubit's phase -g (l_i + sum_j b_ij / 2), each
+// coupling CNOT(i, j), phase +g b_ij / 2 on j, CNOT(i, j) (remote when i and j
+// sit on different QPUs), the constant as the global phase -g c0, then
+// RX(2 beta) on every data qubit.
+std::vector<TgOp> telegate_circuit(const Canonical &c, const int32_t *qpu_of, int p, const double *gamma,
+                                   const double *beta, qaoa_telegate_counts *cnt) {
+    const int n = c.n;
+    std::vector<TgOp> ops;
+    int midx = 0;
+    int64_t loc = 0, cross = 0;
+    for (int q = 0; q < n; ++q) ops.push_back(tg(TG_H, q));
+    for (int l = 0; l < p; ++l) {
+        const double g = gamma[l];
+        ops.push_back(tg(TG_GPHASE, 0, 0, -g * c.c0));
+        for (int i = 0; i < n; ++i) {
+            double lin = 0.0;
+            for (int j = 0; j < n; ++j)
+                if (j != i) lin += c.b[(size_t)std::min(i, j) * n + std::max(i, j)];
+            ops.push_back(tg(TG_PHASE, i, 0, -g * (c.ell[i] + 0.5 * lin)));
+        }
+        for (int i = 0; i < n; ++i)
+            for (int j = i + 1; j < n; ++j) {
+                const double bij = c.b[(size_t)i * n + j];
+                if (bij == 0.0) continue;
+                const bool local = qpu_of[i] == qpu_of[j];
+                for (int rep = 0; rep < 2; ++rep) {
+                    if (local)
+                        ops.push_back(tg(TG_CNOT, i, j));
+                    else
+                        remote_cnot(ops, n, i, j, &midx);
+                    if (rep == 0) ops.push_back(tg(TG_PHASE, j, 0, 0.5 * g * bij));
+                }
+                if (local) ++loc; else ++cross;
+            }
+        for (int q = 0; q < n; ++q) ops.push_back(tg(TG_RX, q, 0, beta[l]));
+    }
+    if (cnt) {
+        cnt->ops = (int64_t)ops.size();
+        cnt->local_zz = loc;
+        cnt->cross_zz = cross;
+        cnt->remote_cx = 2 * cross;
+        cnt->measurements = 4 * cross;
+        cnt->resets = 4 * cross;
+        cnt->feedforward = 4 * cross;
+    }
+    return ops;
+}
+
 }  // namespace
 
 extern "C" {
@@ -592,6 +675,45 @@ qaoa_status qaoa_solve(qaoa_ctx c, qaoa_cost cost, const qaoa_solve_options *sop
     out->runs = runs;
     out->expect = best.E;
     out->metrics = m;
+    return QAOA_OK;
+}
+
+qaoa_status qaoa_telegate_simulate(qaoa_ctx c, qaoa_cost cost, const int32_t *qpu_of, int p, const double *gamma,
+                                   const double *beta, int trajectories, uint64_t seed, double *fidelity,
+                                   float *amps, qaoa_telegate_counts *counts) {
+    if (!c || !cost || !qpu_of || !fidelity) return fail(QAOA_ERR_INVALID_ARG, "null argument");
+    const int n = cost->n;
+    if (n > SMALL_MAXN) return fail(QAOA_ERR_INVALID_ARG, "n=%d: the circuit simulation holds n + 2 <= 14 qubits", n);
+    if (p < 1 || p > SMALL_MAXP) return fail(QAOA_ERR_INVALID_ARG, "p=%d not in [1, %d]", p, SMALL_MAXP);
+    if (trajectories < 1 || trajectories > (1 << 20))
+        return fail(QAOA_ERR_INVALID_ARG, "trajectories=%d not in [1, 2^20]", trajectories);
+    if (c->opt.state_fp64) return fail(QAOA_ERR_INVALID_ARG, "the circuit simulation runs in complex64");
+    QAOA_TRY(check_angles_host(p, gamma, beta));
+    for (int i = 0; i < n; ++i)
+        if (qpu_of[i] < 0) return fail(QAOA_ERR_INVALID_ARG, "variable %d has no QPU", i);
+    CUDA_TRY(cudaSetDevice(c->device));
+    qaoa_telegate_counts cnt;
+    std::memset(&cnt, 0, sizeof(cnt));
+    const std::vector<TgOp> ops = telegate_circuit(cost->can, qpu_of, p, gamma, beta, &cnt);
+    // the monolithic state of the same angles, from the fused path
+    qaoa_state mono = nullptr;
+    QAOA_TRY(qaoa_forward(c, cost, p, gamma, beta, &mono));
+    std::unique_ptr<qaoa_state_s> mono_guard(mono);
+    const size_t D = (size_t)1 << n, T = (size_t)trajectories;
+    const size_t b_ops = ops.size() * sizeof(TgOp), b_fid = T * 8, b_amp = amps ? T * D * 8 : 0;
+    QAOA_TRY(c->sample_out.ensure(b_ops + b_fid + b_amp + 64, &c->held, c->opt.memory_budget));
+    char *m = c->sample_out.as<char>();
+    TgOp *dops = reinterpret_cast<TgOp *>(m);
+    double *dfid = reinterpret_cast<double *>(m + ((b_ops + 15) & ~(size_t)15));
+    float2 *damp = amps ? reinterpret_cast<float2 *>(reinterpret_cast<char *>(dfid) + b_fid) : nullptr;
+    CUDA_TRY(cudaMemcpyAsync(dops, ops.data(), b_ops, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(launch_telegate(dops, (int)ops.size(), n, seed, 0, trajectories, damp,
+                             static_cast<const float2 *>(mono->amps), dfid, c->stream));
+    c->launches_total += 1;
+    CUDA_TRY(cudaMemcpyAsync(fidelity, dfid, b_fid, cudaMemcpyDeviceToHost, c->stream));
+    if (amps) CUDA_TRY(cudaMemcpyAsync(amps, damp, b_amp, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (counts) *counts = cnt;
     return QAOA_OK;
 }
 

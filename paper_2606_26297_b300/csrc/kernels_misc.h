@@ -92,6 +92,18 @@ cudaError_t launch_sample_weights(const SampleItem *items_dev, int count, int ma
 cudaError_t launch_sample_shots(const SampleItem *items_dev, int count, long long max_shots, bool fp64,
                                 unsigned int *status, cudaStream_t st);
 
+// One operation of the distributed (TeleGate) circuit (kernels_telegate.cu).
+enum TgKind { TG_PHASE = 0, TG_RX, TG_H, TG_X, TG_Z, TG_CNOT, TG_MEASURE, TG_XIF, TG_ZIF, TG_GPHASE, TG_RESET };
+struct TgOp {
+    int32_t kind;
+    int32_t q0, q1;  // qubit; second qubit (CNOT target) or outcome slot (MEASURE, XIF, ZIF)
+    int32_t midx;    // running index of a MEASURE (its random-number counter)
+    float c, s;      // cos and sin of the angle (PHASE, GPHASE: e^{i theta}; RX: exp(-i theta X))
+};
+int telegate_smem_bytes(int n);
+cudaError_t launch_telegate(const TgOp *ops, int nops, int n, unsigned long long seed, int traj0, int count,
+                            float2 *data_out, const float2 *mono, double *fid_out, cudaStream_t st);
+
 struct FactArgs {
     const int32_t *T;
     int n, M;

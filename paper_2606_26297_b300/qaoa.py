@@ -82,6 +82,11 @@ class qaoa_solve_result(ctypes.Structure):
                 ("metrics", qaoa_sample_metrics)]
 
 
+class qaoa_telegate_counts(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in ("ops", "local_zz", "cross_zz", "remote_cx", "measurements", "resets",
+                                              "feedforward")]
+
+
 _P = ctypes.c_void_p
 _I = ctypes.c_int
 _D = ctypes.c_double
@@ -120,6 +125,8 @@ _SIGS = {
     "qaoa_solve": ([_P, _P, ctypes.POINTER(qaoa_solve_options), _PD, _PD, _I, _PU64, _PD, _PI64,
                     ctypes.POINTER(qaoa_sample_metrics), ctypes.POINTER(qaoa_solve_result)], _I),
     "qaoa_partition": ([_I, _I, _PI32, _PI32, _PI32], _I),
+    "qaoa_telegate_simulate": ([_P, _P, _PI32, _I, _PD, _PD, _I, ctypes.c_uint64, _PD, _PF,
+                                ctypes.POINTER(qaoa_telegate_counts)], _I),
     "qaoa_partition_graph": ([ctypes.POINTER(qaoa_qubo), _I, _PI32, _PI32], _I),
     "qaoa_allocation_candidates": ([ctypes.POINTER(qaoa_qubo), _I, _PI32, _PI32, _I, _PI32, _PI32, _PI64, _PI64],
                                    _I),
@@ -483,6 +490,23 @@ def qaoa_allocation_candidates(H, f, c0: float, caps, manual=None, p: int = 1, d
     k = 3 if manual is not None else 2
     return {"qpu_of": out, "kind": kind.value, "cross": [int(v) for v in cross[:k]],
             "remote_cx": [int(v) for v in rcx[:k]]}
+
+
+def qaoa_telegate_simulate(ctx, cost, qpu_of, gamma, beta, trajectories: int = 1, seed: int = 0,
+                           want_amps: bool = False):
+    """Gate-level TeleGate simulation (Sec. 3.3).  Returns (fidelity per
+    trajectory, data states (trajectories, 2^n) complex64 or None, counts)."""
+    q = np.ascontiguousarray(np.asarray(qpu_of, dtype=np.int32))
+    g, b = _f64(gamma), _f64(beta)
+    T = int(trajectories)
+    fid = np.zeros(T)
+    n = q.size
+    amps = np.zeros((T, 1 << n), dtype=np.complex64) if want_amps else None
+    cnt = qaoa_telegate_counts()
+    _check(_lib.qaoa_telegate_simulate(ctx, cost, q.ctypes.data_as(_PI32), len(g), _dptr(g), _dptr(b), T,
+                                       int(seed) & 0xFFFFFFFFFFFFFFFF, _dptr(fid),
+                                       None if amps is None else amps.ctypes.data_as(_PF), ctypes.byref(cnt)))
+    return fid, amps, {f: getattr(cnt, f) for f, _ in qaoa_telegate_counts._fields_}
 
 
 def qaoa_classify(cost, qpu_of, p: int):
