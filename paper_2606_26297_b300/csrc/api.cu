@@ -246,7 +246,7 @@ qaoa_status enqueue_plan(qaoa_ctx c, PlanBufs &b, const PlanRun &r, const int32_
             cudaError_t e = pl.kind == 0   ? launch_fwd_pass(pl.type, a, c->stream)
                             : pl.kind == 1 ? launch_final_pass(pl.type, a, c->num_sms, stw, c->stream)
                             : pl.kind == 2 ? launch_rev_pass(pl.type, a, c->num_sms, stw, c->stream)
-                                           : launch_rev_mid(pl.type, a, c->stream);
+                                           : launch_rev_mid(pl.type, a, c->num_sms, stw, c->stream);
             if (e) return fail(QAOA_ERR_CUDA, "layer-pass launch failed: %s", cudaGetErrorString(e));
             c->launches_total += 1;
         }

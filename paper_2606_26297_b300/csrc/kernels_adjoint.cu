@@ -372,26 +372,45 @@ __global__ void __launch_bounds__(PASS_THREADS, 1)
 // return to true scale) and written, alone or interleaved with the stored
 // input state psi_in; the X-terms of the mixer are taken at the pass input
 // against psi_in, once with lambda in arrangement Y and once, after a
-// transpose, in arrangement X.  Direct loads, two CTAs per SM.  slots: 0 =
-// X-term (Y bits), 1 = X-term (X bits).
+// transpose, in arrangement X.  slots: 0 = X-term (Y bits), 1 = X-term (X
+// bits).
 // ---------------------------------------------------------------------------
 
-// sum over the mixed register bits j of sum_m Im(conj(lambda_{m ^ e_j}) psi_m),
-// psi streamed from global memory in arrangement A; PL: also write the
-// interleaved element (psi_m, lambda_m) to pl
+// A persistent TMA-pipelined kernel (one CTA per SM): the lambda block and the
+// stored psi_in block of a unit are staged in shared memory by bulk/tensor
+// copies, the next unit's copies are issued as soon as each stage has been
+// read, and both X-term sums read psi_in from the stage (one read of psi_in
+// from HBM).  A direct-load form with two CTAs per SM took 8% longer per
+// gradient evaluation at n = 30 (load latency with 16 warps per SM).
+template <int T>
+__device__ __forceinline__ void issue_block8(uint32_t u, const PassArgs &a, const CUtensorMap *map,
+                                             const float2 *arr, float2 *stage, unsigned long long *mbar) {
+    const int nbits = a.n - BLOCK_BITS;
+    const Unit un = unit_of(u, nbits);
+    mbar_expect_tx(mbar, 65536u);
+    if (T == 0) {
+        bulk_load(stage, arr + ((size_t)un.item << a.n) + ((size_t)un.b << 13), 65536u, mbar);
+    } else {
+        int c1, c3, c4;
+        tile_coords(un.b, un.item, a, &c1, &c3, &c4);
+        tma_load_5d(stage, map, c1, c3, c4, mbar);
+    }
+}
+
+// X-terms of the mixed register bits with lambda in registers (arrangement A)
+// and psi read from a staged block; PL: also write (psi, lambda) interleaved
 template <int T, int A, bool PL>
-__device__ __forceinline__ float xterm_stream(const float2 (&v)[32], const float2 *__restrict__ pp,
-                                              float4 *__restrict__ pl, uint32_t l, uint32_t w, int loA, int loB,
-                                              uint32_t mask) {
-    const size_t t = goff<T>(local_idx<T, A>(l, 0u, w), loA, loB);
-    const float2 *q = pp + t;
+__device__ __forceinline__ float xterm_staged(const float2 (&v)[32], const float2 *pst, float4 *__restrict__ pl,
+                                              uint32_t l, uint32_t w, int loA, int loB, uint32_t mask) {
+    const uint32_t ts = local_idx<T, A>(l, 0u, w);
+    const size_t t = goff<T>(ts, loA, loB);
     bool on[5];
 #pragma unroll
     for (int i = 0; i < 5; ++i) on[i] = (mask >> regbit<T, A>(i)) & 1u;
     float s0 = 0.f, s1 = 0.f;
 #pragma unroll
     for (int m = 0; m < 32; ++m) {
-        const float2 ps = __ldg(q + roff<T, A>(m, loA, loB));
+        const float2 ps = pst[ts | local_idx<T, A>(0u, (uint32_t)m, 0u)];
         if (PL) __stcs(pl + t + roff<T, A>(m, loA, loB), make_float4(ps.x, v[m].x, ps.y, v[m].y));
 #pragma unroll
         for (int i = 0; i < 5; ++i) {
@@ -405,40 +424,64 @@ __device__ __forceinline__ float xterm_stream(const float2 (&v)[32], const float
 }
 
 template <int T, bool PLOUT, bool FULL>
-__global__ void __launch_bounds__(PASS_THREADS, 2) rev_mid_kernel(const PassArgs a) {
-    extern __shared__ __align__(16) float2 sm[];
+__global__ void __launch_bounds__(PASS_THREADS, 1)
+    rev_mid_tma_kernel(const PassArgs a, const __grid_constant__ CUtensorMap mlam,
+                       const __grid_constant__ CUtensorMap mpsi, int nunits, unsigned int *status) {
+    extern __shared__ __align__(1024) unsigned char smraw[];
     const uint32_t mask = FULL ? full_mask<T>() : a.mask;
+    float2 *lst = reinterpret_cast<float2 *>(smraw);            // lambda block, 64 KB
+    float2 *pst = reinterpret_cast<float2 *>(smraw + 65536);    // stored psi_in block, 64 KB
+    float2 *xbuf = reinterpret_cast<float2 *>(smraw + 131072);  // transposes, 64 KB
+    __shared__ __align__(8) unsigned long long mbl, mbp;
     __shared__ double red[PASS_THREADS / 32][NSLOT];
     const uint32_t l = threadIdx.x & 31u, w = threadIdx.x >> 5;
     const int nbits = a.n - BLOCK_BITS;
-    const uint32_t item = blockIdx.x >> nbits, b = blockIdx.x & ((1u << nbits) - 1u);
-    const PassScal sc = a.scal[item];
-    const uint32_t fb = sc.post_flip ? mask : 0u;
-    const size_t base = block_base<T>(b, a.loA, a.loB);
-    float2 *lp = a.lam + ((size_t)item << a.n) + base;
-    const float2 *pp = a.psi_src + ((size_t)item << a.n) + base;
-    {
-        // start the stored state's journey to L1 while lambda is undone
-        const float2 *qy = pp + goff<T>(local_idx<T, 1>(l, 0u, w), a.loA, a.loB);
-#pragma unroll
-        for (int m = 0; m < 32; ++m) asm volatile("prefetch.global.L1 [%0];" ::"l"(qy + roff<T, 1>(m, a.loA, a.loB)));
+    if (threadIdx.x == 0) {
+        mbar_init(&mbl, 1);
+        mbar_init(&mbp, 1);
     }
-    float2 v[32];
-    load_arr<T, 0>(v, lp, l, w, a.loA, a.loB);
-    round_mix<T, 0>(v, -sc.post_t, mask);
-    transpose1<T, 0, 1>(v, sm, l, w, fb);
-    round_mix<T, 1>(v, -sc.post_t, mask);
+    __syncthreads();
+    uint32_t parl = 0, parp = 0;
+    if (threadIdx.x == 0 && (int)blockIdx.x < nunits) {
+        issue_block8<T>(blockIdx.x, a, &mlam, a.lam, lst, &mbl);
+        issue_block8<T>(blockIdx.x, a, &mpsi, a.psi_src, pst, &mbp);
+    }
+    for (uint32_t u = blockIdx.x; (int)u < nunits; u += gridDim.x) {
+        const Unit un = unit_of(u, nbits);
+        const PassScal sc = a.scal[un.item];
+        const uint32_t fb = sc.post_flip ? mask : 0u;
+        const size_t base = block_base<T>(un.b, a.loA, a.loB);
+        const bool more = (int)(u + gridDim.x) < nunits;
+        float2 v[32];
+        if (!stage_ready(&mbl, parl, status)) return;
+        parl ^= 1u;
+        read_stage<T, 0>(v, lst, l, w);
+        __syncthreads();
+        if (threadIdx.x == 0 && more) {
+            fence_proxy_async();
+            issue_block8<T>(u + gridDim.x, a, &mlam, a.lam, lst, &mbl);
+        }
+        round_mix<T, 0>(v, -sc.post_t, mask);
+        transpose1<T, 0, 1>(v, xbuf, l, w, fb);
+        round_mix<T, 1>(v, -sc.post_t, mask);
 #pragma unroll
-    for (int m = 0; m < 32; ++m) v[m] = cmul(v[m], sc.kend);
-    // lambda_in: interleaved with psi_in for a following reverse pass that
-    // undoes a cost layer (it uncomputes psi), else alone
-    float4 *plo = a.pl + ((size_t)item << a.n) + base;
-    const float xy = xterm_stream<T, 1, false>(v, pp, plo, l, w, a.loA, a.loB, mask);
-    if (!PLOUT) store_arr<T, 1>(v, lp, l, w, a.loA, a.loB);
-    transpose1<T, 1, 0>(v, sm, l, w, 0u);
-    const float xx = xterm_stream<T, 0, PLOUT>(v, pp, plo, l, w, a.loA, a.loB, mask);
-    double vals[NSLOT] = {(double)xy, (double)xx, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    block_sum_write(vals, red, a.partials, blockIdx.x);
+        for (int m = 0; m < 32; ++m) v[m] = cmul(v[m], sc.kend);
+        if (!stage_ready(&mbp, parp, status)) return;
+        parp ^= 1u;
+        float4 *plo = a.pl + ((size_t)un.item << a.n) + base;
+        const float xy = xterm_staged<T, 1, false>(v, pst, plo, l, w, a.loA, a.loB, mask);
+        if (!PLOUT) store_arr<T, 1>(v, a.lam + ((size_t)un.item << a.n) + base, l, w, a.loA, a.loB);
+        transpose1<T, 1, 0>(v, xbuf, l, w, 0u);
+        const float xx = xterm_staged<T, 0, PLOUT>(v, pst, plo, l, w, a.loA, a.loB, mask);
+        __syncthreads();
+        if (threadIdx.x == 0 && more) {
+            fence_proxy_async();
+            issue_block8<T>(u + gridDim.x, a, &mpsi, a.psi_src, pst, &mbp);
+        }
+        double vals[NSLOT] = {(double)xy, (double)xx, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        block_sum_write(vals, red, a.partials, u);
+        __syncthreads();
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -585,23 +628,38 @@ cudaError_t launch_rev_pass(int type, const PassArgs &a, int grid, unsigned int 
 }
 
 template <int T, bool PLOUT, bool FULL>
-static cudaError_t mid_launch_f(const PassArgs &a, cudaStream_t st) {
-    const unsigned grid = (unsigned)a.nitems << (a.n - BLOCK_BITS);
-    const int smem = 8192 * (int)sizeof(float2);
-    cudaError_t e = set_smem(rev_mid_kernel<T, PLOUT, FULL>, smem);
+static cudaError_t mid_launch_f(const PassArgs &a, const CUtensorMap &ml, const CUtensorMap &mp, int grid,
+                                int nunits, unsigned int *status, cudaStream_t st) {
+    const int smem = 3 * 65536;
+    cudaError_t e = set_smem(rev_mid_tma_kernel<T, PLOUT, FULL>, smem);
     if (e) return e;
-    rev_mid_kernel<T, PLOUT, FULL><<<grid, PASS_THREADS, smem, st>>>(a);
+    rev_mid_tma_kernel<T, PLOUT, FULL><<<grid, PASS_THREADS, smem, st>>>(a, ml, mp, nunits, status);
     return cudaGetLastError();
 }
 
 template <int T, bool PLOUT>
-static cudaError_t mid_launch(const PassArgs &a, cudaStream_t st) {
-    return a.mask == full_mask<T>() ? mid_launch_f<T, PLOUT, true>(a, st) : mid_launch_f<T, PLOUT, false>(a, st);
+static cudaError_t mid_launch(const PassArgs &a, const CUtensorMap &ml, const CUtensorMap &mp, int grid,
+                              int nunits, unsigned int *status, cudaStream_t st) {
+    return a.mask == full_mask<T>() ? mid_launch_f<T, PLOUT, true>(a, ml, mp, grid, nunits, status, st)
+                                    : mid_launch_f<T, PLOUT, false>(a, ml, mp, grid, nunits, status, st);
 }
 
-cudaError_t launch_rev_mid(int type, const PassArgs &a, cudaStream_t st) {
-    if (type == 0) return a.pl_out ? mid_launch<0, true>(a, st) : mid_launch<0, false>(a, st);
-    return a.pl_out ? mid_launch<1, true>(a, st) : mid_launch<1, false>(a, st);
+cudaError_t launch_rev_mid(int type, const PassArgs &a, int grid, unsigned int *status, cudaStream_t st) {
+    const int nunits = a.nitems << (a.n - BLOCK_BITS);
+    CUtensorMap ml, mp;
+    std::memset(&ml, 0, sizeof ml);
+    std::memset(&mp, 0, sizeof mp);
+    cudaError_t e;
+    if (type == 1) {
+        if ((e = make_block_map(&ml, a.lam, a.n, a.loA, a.loB, 8, a.nitems))) return e;
+        if ((e = make_block_map(&mp, a.psi_src, a.n, a.loA, a.loB, 8, a.nitems))) return e;
+    }
+    if (grid > nunits) grid = nunits;
+    if (type == 0)
+        return a.pl_out ? mid_launch<0, true>(a, ml, mp, grid, nunits, status, st)
+                        : mid_launch<0, false>(a, ml, mp, grid, nunits, status, st);
+    return a.pl_out ? mid_launch<1, true>(a, ml, mp, grid, nunits, status, st)
+                    : mid_launch<1, false>(a, ml, mp, grid, nunits, status, st);
 }
 
 }  // namespace qaoa
