@@ -286,3 +286,44 @@ def test_block_separable_n33_maximum_size(q):
     q.qaoa_cost_destroy(cost)
     q.qaoa_ctx_destroy(ctx)
     gc.collect()
+
+
+def test_sampling_n30_block_marginals(q):
+    """Measurement at the benchmark's size (n = 30, p = 8, 2^20 shots): on the
+    QUBO of three uncoupled dense blocks the state is a tensor product, so the
+    shots' 10-bit block marginals must follow the oracle's block
+    distributions (chi-square over the outcomes of expected count >= 20, far
+    tail at 6 sigma), the shot mean cost must be within five standard errors
+    of the oracle's E, and the costs of the shots must equal the sum of the
+    blocks' F at their block indices."""
+    ctx = q.qaoa_ctx_create(0)
+    blocks = [inst.normal_qubo(10, 1003 + k) for k in range(3)]
+    Qd, g, b = inst.workload_dense30()
+    Qb = inst.block_diagonal_qubo(blocks)
+    cost = _cost(q, ctx, Qb)
+    st = q.qaoa_forward(ctx, cost, g, b)
+    S = 1 << 20
+    idx, cs, mean = q.qaoa_sample(ctx, cost, st, S, seed=2026, stream=30, want_cost=True, want_mean=True)
+    Fs = [oracle.cost_table(oracle.canonical_of(B)) for B in blocks]
+    Ps = [oracle.probabilities(oracle.evolve(Fb, g, b)) for Fb in Fs]
+    E = sum(float(np.dot(P, Fb)) for P, Fb in zip(Ps, Fs))
+    var = sum(float(np.dot(P, (Fb - np.dot(P, Fb)) ** 2)) for P, Fb in zip(Ps, Fs))
+    assert abs(mean - E) < 5 * math.sqrt(var / S)
+    info = q.qaoa_cost_info(cost)
+    bound = (1 + 30 + 435) * 2.0 ** (-(info["shift_bits"] + 1))
+    fsum = np.zeros(S)
+    for k, (P, Fb) in enumerate(zip(Ps, Fs)):
+        xb = ((idx >> np.uint64(10 * k)) & np.uint64(1023)).astype(np.int64)
+        fsum += Fb[xb]
+        cnt = np.bincount(xb, minlength=1024).astype(np.float64)
+        exp = S * P
+        keep = exp >= 20
+        chi2 = float(np.sum((cnt[keep] - exp[keep]) ** 2 / exp[keep]))
+        dof = int(np.sum(keep)) - 1
+        assert chi2 < dof + 6 * math.sqrt(2 * dof), (k, chi2, dof)
+        assert float(np.sum(cnt[~keep])) < 5 * max(float(np.sum(exp[~keep])), 1.0) + 50
+    assert np.max(np.abs(cs - (fsum + Qb.c0 - sum(B.c0 for B in blocks)))) <= bound + 1e-9
+    q.qaoa_state_destroy(st)
+    q.qaoa_cost_destroy(cost)
+    q.qaoa_ctx_destroy(ctx)
+    gc.collect()
