@@ -282,6 +282,20 @@ def test_block_separable_n33_maximum_size(q):
     assert np.linalg.norm(got - ref) * math.sqrt(2.0 ** n / xs.size) <= 1e-5
     tk = q.qaoa_topk(ctx, cost, st, 4)
     assert np.all(np.diff(tk["prob"]) <= 0)
+    # measurement at the largest size (2^19 super-chunks): stratified random
+    # integers give non-decreasing indices from the first to the last index,
+    # and the shot mean cost lies within five standard errors of E
+    S = 8192
+    R = np.array([(s << 64) // S + (1 << 40) for s in range(S)], dtype=np.uint64)
+    R[0], R[-1] = 0, np.iinfo(np.uint64).max
+    idx, _, _ = q.qaoa_sample(ctx, None, st, S, rand=R)
+    assert np.all(np.diff(idx.astype(np.int64)) >= 0)
+    assert idx[0] == 0 and idx[-1] == (1 << n) - 1
+    _, cs, mean = q.qaoa_sample(ctx, cost, st, 1 << 16, seed=33, want_idx=False, want_cost=True, want_mean=True)
+    Ps = [np.abs(pb) ** 2 for pb in psis]
+    var = sum(float(np.dot(P, (Fb - np.dot(P, Fb)) ** 2)) for P, Fb in zip(Ps, Fs))
+    assert abs(mean - Eo) < 5 * math.sqrt(var / (1 << 16))
+    assert mean == pytest.approx(float(np.mean(cs)), rel=1e-12, abs=1e-9)
     q.qaoa_state_destroy(st)
     q.qaoa_cost_destroy(cost)
     q.qaoa_ctx_destroy(ctx)

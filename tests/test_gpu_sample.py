@@ -222,6 +222,26 @@ def test_spsa_shots_first_iteration_vs_oracle(q, ctx):
     q.qaoa_cost_destroy(cost)
 
 
+def test_spsa_averaging_passes(q, ctx):
+    """averaging = 3: J of the first iteration is the mean over three shot
+    estimates drawn on streams pass 0, 1, 2, i.e. qaoa_sample's mean cost over
+    those three streams of the same state (n = 13)."""
+    n, p, S, seed, c = 13, 2, 3000, 17, 0.12
+    Q = inst.upper_int_qubo(n, 3250)
+    g0, b0 = inst.random_angles(p, 1, 3251, gamma_scale=0.3)
+    cost = _cost(q, ctx, Q)
+    _, _, hist, _ = q.qaoa_optimize_spsa(ctx, [cost], g0, b0, 1, shots=S, averaging=3, seed=seed, c=c)
+    D = osm.spsa_signs(seed, 0, 0, 2 * p)
+    for which, sign in ((0, 1.0), (1, -1.0)):
+        x = oracle.interleave(g0[0], b0[0]) + sign * c * D
+        st = q.qaoa_forward(ctx, cost, x[0::2], x[1::2])
+        means = [q.qaoa_sample(ctx, cost, st, S, seed=seed, stream=(which << 9) | a, want_idx=False,
+                               want_mean=True)[2] for a in range(3)]
+        assert hist[0, 0, which] == pytest.approx(float(np.mean(means)), rel=1e-12, abs=1e-9)
+        q.qaoa_state_destroy(st)
+    q.qaoa_cost_destroy(cost)
+
+
 def test_spsa_shots_match_sample_api(q, ctx):
     """J+ of the first iteration equals qaoa_sample's mean cost of the state
     qaoa_forward evolves at x0 + c D with the same stream (n = 13, pass path)."""
