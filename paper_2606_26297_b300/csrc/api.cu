@@ -243,7 +243,9 @@ qaoa_status enqueue_plan(qaoa_ctx c, PlanBufs &b, const PlanRun &r, const int32_
         const double bytes = pass_bytes_per_amp(pl) * std::ldexp((double)r.nitems, n);
         {
             ProfScope ps(c, pl.kind >= 2 ? 1 : 0, bytes, profile);
-            cudaError_t e = pl.kind == 0   ? launch_fwd_pass(pl.type, a, c->stream)
+            cudaError_t e = pl.kind == 0   ? (a.has_pre && a.has_cost && a.has_post && !a.init
+                                                  ? launch_fwd_cost_tma(pl.type, a, 2 * c->num_sms, stw, c->stream)
+                                                  : launch_fwd_pass(pl.type, a, c->stream))
                             : pl.kind == 1 ? launch_final_pass(pl.type, a, c->num_sms, stw, c->stream)
                             : pl.kind == 2 ? launch_rev_pass(pl.type, a, c->num_sms, stw, c->stream)
                                            : launch_rev_mid(pl.type, a, c->num_sms, stw, c->stream);

@@ -484,6 +484,71 @@ __global__ void __launch_bounds__(PASS_THREADS, 1)
     }
 }
 
+// forward cost-layer pass (pre mixer, cost, post mixer), persistent, two CTAs
+// per SM: the psi block is staged by TMA and, once read, the same stage serves
+// as the transpose buffer; the next unit's psi copy is issued after the last
+// transpose, the next table copy as soon as the table stage has been read.
+// Against the direct-load form this cuts the forward passes of one n = 30,
+// p = 8 evaluation from 66.6 to 64.2 ms; for the mixer-only passes (already
+// near the HBM bound) the same form gains nothing, and with one CTA per SM and
+// a separate transpose buffer it was slower.
+template <int T, bool FULL>
+__global__ void __launch_bounds__(PASS_THREADS, 2)
+    fwd_cost_tma_kernel(const PassArgs a, const __grid_constant__ CUtensorMap mpsi,
+                        const __grid_constant__ CUtensorMap mcost, int nunits, unsigned int *status) {
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    const uint32_t mask = FULL ? full_mask<T>() : a.mask;
+    float2 *pst = reinterpret_cast<float2 *>(smraw);            // psi block / transposes, 64 KB
+    int32_t *cst = reinterpret_cast<int32_t *>(smraw + 65536);  // table block, 32 KB
+    __shared__ __align__(8) unsigned long long mbp, mbc;
+    const uint32_t l = threadIdx.x & 31u, w = threadIdx.x >> 5;
+    const int nbits = a.n - BLOCK_BITS;
+    if (threadIdx.x == 0) {
+        mbar_init(&mbp, 1);
+        mbar_init(&mbc, 1);
+    }
+    __syncthreads();
+    uint32_t parp = 0, parc = 0;
+    if (threadIdx.x == 0 && (int)blockIdx.x < nunits) {
+        issue_block8<T>(blockIdx.x, a, &mpsi, a.psi, pst, &mbp);
+        issue_table<T>(blockIdx.x, a, &mcost, cst, &mbc);
+    }
+    for (uint32_t u = blockIdx.x; (int)u < nunits; u += gridDim.x) {
+        const Unit un = unit_of(u, nbits);
+        const PassScal sc = a.scal[un.item];
+        const size_t base = block_base<T>(un.b, a.loA, a.loB);
+        const bool more = (int)(u + gridDim.x) < nunits;
+        float2 *po = (a.psi_out ? a.psi_out : a.psi) + ((size_t)un.item << a.n) + base;
+        float2 v[32];
+        if (!stage_ready(&mbp, parp, status)) return;
+        parp ^= 1u;
+        read_stage<T, 0>(v, pst, l, w);
+        round_mix<T, 0>(v, sc.pre_t, mask);
+        transpose1<T, 0, 1>(v, pst, l, w, sc.pre_flip ? mask : 0u);
+        round_mix<T, 1>(v, sc.pre_t, mask);
+        int32_t c[32];
+        if (!stage_ready(&mbc, parc, status)) return;
+        parc ^= 1u;
+        read_cost_stage<T, 1>(c, cst, l, w);
+        __syncthreads();
+        if (threadIdx.x == 0 && more) {
+            fence_proxy_async();
+            issue_table<T>(u + gridDim.x, a, &mcost, cst, &mbc);
+        }
+#pragma unroll
+        for (int m = 0; m < 32; ++m) v[m] = cmul(v[m], cost_phase(c[m], sc.phi, sc.off, sc.kmag, a.precise_phase));
+        round_mix<T, 1>(v, sc.post_t, mask);
+        transpose1<T, 1, 0>(v, pst, l, w, sc.post_flip ? mask : 0u);
+        __syncthreads();
+        if (threadIdx.x == 0 && more) {
+            fence_proxy_async();
+            issue_block8<T>(u + gridDim.x, a, &mpsi, a.psi, pst, &mbp);
+        }
+        round_mix<T, 0>(v, sc.post_t, mask);
+        store_arr<T, 0>(v, po, l, w, a.loA, a.loB);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // host side: tensor maps and launchers
 // ---------------------------------------------------------------------------
@@ -660,6 +725,38 @@ cudaError_t launch_rev_mid(int type, const PassArgs &a, int grid, unsigned int *
                         : mid_launch<0, false>(a, ml, mp, grid, nunits, status, st);
     return a.pl_out ? mid_launch<1, true>(a, ml, mp, grid, nunits, status, st)
                     : mid_launch<1, false>(a, ml, mp, grid, nunits, status, st);
+}
+
+template <int T, bool FULL>
+static cudaError_t fct_launch_f(const PassArgs &a, const CUtensorMap &m, const CUtensorMap &mc, int grid,
+                                int nunits, unsigned int *status, cudaStream_t st) {
+    const int smem = 65536 + 32768;
+    cudaError_t e = set_smem(fwd_cost_tma_kernel<T, FULL>, smem);
+    if (e) return e;
+    fwd_cost_tma_kernel<T, FULL><<<grid, PASS_THREADS, smem, st>>>(a, m, mc, nunits, status);
+    return cudaGetLastError();
+}
+
+template <int T>
+static cudaError_t fct_launch(const PassArgs &a, const CUtensorMap &m, const CUtensorMap &mc, int grid, int nunits,
+                              unsigned int *status, cudaStream_t st) {
+    return a.mask == full_mask<T>() ? fct_launch_f<T, true>(a, m, mc, grid, nunits, status, st)
+                                    : fct_launch_f<T, false>(a, m, mc, grid, nunits, status, st);
+}
+
+cudaError_t launch_fwd_cost_tma(int type, const PassArgs &a, int grid, unsigned int *status, cudaStream_t st) {
+    const int nunits = a.nitems << (a.n - BLOCK_BITS);
+    CUtensorMap m, mc;
+    std::memset(&m, 0, sizeof m);
+    std::memset(&mc, 0, sizeof mc);
+    cudaError_t e;
+    if (type == 1) {
+        if ((e = make_block_map(&m, a.psi, a.n, a.loA, a.loB, 8, a.nitems))) return e;
+        if ((e = make_block_map(&mc, a.C, a.n, a.loA, a.loB, 4, a.ntables))) return e;
+    }
+    if (grid > nunits) grid = nunits;
+    return type == 0 ? fct_launch<0>(a, m, mc, grid, nunits, status, st)
+                     : fct_launch<1>(a, m, mc, grid, nunits, status, st);
 }
 
 }  // namespace qaoa
