@@ -154,10 +154,11 @@ __global__ void __launch_bounds__(SAMPLE_THREADS) sample_shot_kernel(const Sampl
                                                                      unsigned int *status) {
     const SampleItem &it = items[blockIdx.y];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const long long s = (long long)blockIdx.x * (SAMPLE_THREADS / 32) + warp;
     __shared__ long long tsum[SAMPLE_THREADS / 32];
-    long long tv = 0;
-    if (s < it.shots) {
+    long long tv = 0;  // this warp's sum of table values
+    // one warp per shot, grid-strided (a launch holds at most 2^22 CTAs)
+    for (long long s = (long long)blockIdx.x * (SAMPLE_THREADS / 32) + warp; s < it.shots;
+         s += (long long)gridDim.x * (SAMPLE_THREADS / 32)) {
         const Geo g = geo_of(it.n);
         const unsigned long long Q = *it.total;
         const unsigned long long R = it.rand ? it.rand[s] : shot_random(it.seed, it.stream, (uint64_t)s);
@@ -216,8 +217,9 @@ __global__ void __launch_bounds__(SAMPLE_THREADS) sample_shot_kernel(const Sampl
         if (lane == 0) {
             if (it.idx) it.idx[s] = x;
             if (it.T) {
-                tv = it.T[x];
-                if (it.tval) it.tval[s] = (int32_t)tv;
+                const int32_t t = it.T[x];
+                tv += t;
+                if (it.tval) it.tval[s] = t;
             }
         }
     }
@@ -259,9 +261,11 @@ cudaError_t launch_sample_weights(const SampleItem *items_dev, int count, int ma
 cudaError_t launch_sample_shots(const SampleItem *items_dev, int count, long long max_shots, bool fp64,
                                 unsigned int *status, cudaStream_t st) {
     const long long per_cta = SAMPLE_THREADS / 32;
+    long long ctas = (max_shots + per_cta - 1) / per_cta;
+    if (ctas > (1ll << 22)) ctas = 1ll << 22;
     for (int o = 0; o < count; o += MAX_GRID_Y) {
         const int k = count - o < MAX_GRID_Y ? count - o : MAX_GRID_Y;
-        const dim3 grid((unsigned)((max_shots + per_cta - 1) / per_cta), (unsigned)k);
+        const dim3 grid((unsigned)ctas, (unsigned)k);
         if (fp64)
             sample_shot_kernel<double2><<<grid, SAMPLE_THREADS, 0, st>>>(items_dev + o, status);
         else

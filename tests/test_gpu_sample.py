@@ -70,6 +70,26 @@ def test_sample_bit_exact_caller_randoms(q, ctx, n):
     q.qaoa_state_destroy(st)
 
 
+def test_sample_many_shots_grid_stride(q, ctx):
+    """More shots than one launch has warps (2^25 + 1000: each warp takes
+    several shots): the first and last shots match the oracle index for index,
+    and the mean cost equals the mean of F over all returned indices."""
+    n = 10
+    amps = inst.random_state(n, 4040)
+    st = q.qaoa_state_from_host(ctx, amps)
+    Q = inst.upper_int_qubo(n, 4041)
+    cost = _cost(q, ctx, Q)
+    S = (1 << 25) + 1000
+    idx, _, mean = q.qaoa_sample(ctx, cost, st, S, seed=41, stream=42, want_mean=True)
+    for first, cnt in ((0, 200), (S - 1000, 1000), ((1 << 22) * 8 - 7, 20)):
+        ref = osm.sample(amps, osm.shot_randoms(41, 42, cnt, first=first))
+        assert np.array_equal(idx[first:first + cnt], ref)
+    F = oracle.cost_table(oracle.canonical_of(Q))
+    assert mean == pytest.approx(float(np.mean(F[idx.astype(np.int64)])), rel=1e-12, abs=1e-9)
+    q.qaoa_cost_destroy(cost)
+    q.qaoa_state_destroy(st)
+
+
 def test_sample_sparse_and_empty_regions(q, ctx):
     """Whole super-chunks and chunks of zero probability (n = 18): the search
     skips them, shots never land on a zero weight, and indices match the
