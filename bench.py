@@ -274,6 +274,8 @@ def run_gpu(args):
         achieved = d["bytes"] / (d["ms"] / 1000.0) / 1e9
         per_launch = d["bytes"] / d["launches"]
         share = {k: round(v["ms"] / sum(x["ms"] for x in kinds.values()), 4) for k, v in kinds.items()}
+        step_bytes = (prof["fwd_pass"]["bytes"] + prof["rev_pass"]["bytes"]) / args.steps
+        min_bytes = 56.0 * p * 2.0 ** n
         clocks = clk.summary()
         cpu = cpu_baseline(24) if (rank == 0 and not args.no_cpu) else None
         E, dg, db, ti, tp, mism, cls = res
@@ -294,6 +296,15 @@ def run_gpu(args):
                          "alg_bytes_per_launch": per_launch,
                          "traffic": _traffic(dom, per_launch)},
             "kernel_time_share": share,
+            # the whole step against HBM: the bytes this design moves per step (every layer
+            # pass, forward and reverse) and the method's minimum (20 B forward + 36 B
+            # reverse per amplitude per layer), over the device time of the whole step
+            # (table build and factorisation check included)
+            "step_roofline": {
+                "design_bytes_per_step": step_bytes,
+                "method_min_bytes_per_step": min_bytes,
+                "frac_design": step_bytes / (ms / args.steps / 1000.0) / 1e9 / peak,
+                "frac_method_min": min_bytes / (ms / args.steps / 1000.0) / 1e9 / peak},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
