@@ -350,6 +350,8 @@ def run_workload(args):
       telegate gate-level distributed circuit (Sec. 3.3) of a dense integer
                n=12 QUBO on three QPUs of four, p=2: 1184 trajectories, time
                per trajectory and fidelity against the monolithic state;
+      peaks    sustained FP32 FMA, f32x2 FMA, FP64 FMA and sin/cos rates of this
+               GPU (the denominators of arithmetic-bound kernels);
       solve    Algorithm 1 (Sec. 3.5) on the n=20 integer QUBO: depths 1..3,
                4 random starts + lifted + 2 perturbed per depth, SPSA-Adam with
                1024 shots, `--iters` iterations, 8192 final shots."""
@@ -523,6 +525,11 @@ def run_workload(args):
                     "op_passes_per_s": cnt["ops"] * T / t, "counts": cnt,
                     "min_fidelity": float(np.min(fid)), "monolithic_forward_ms": 1e3 * tm})
         q.qaoa_cost_destroy(cost)
+    elif args.workload == "peaks":
+        names = ["fp32_fma", "f32x2_fma", "fp64_fma", "sincos"]
+        for k, name in enumerate(names):
+            ops, flops = q.qaoa_peak_probe(ctx, k)
+            res[name] = {"ops_per_s": ops, "flop_per_s": flops}
     elif args.workload == "solve":
         Q, _, _ = inst.workload_batch20()
         cost = q.qaoa_build_cost(ctx, Q.H, Q.f, Q.c0, "i32")
@@ -555,7 +562,7 @@ def main():
     ap.add_argument("--p", type=int, default=DEPTH, help="depth (default 8)")
     ap.add_argument("--workload", default="",
                     choices=["", "fd", "batch20", "ragged", "uc32", "autotune", "sample", "spsa", "solve",
-                             "telegate"],
+                             "telegate", "peaks"],
                     help="a secondary measurement instead of the headline step")
     ap.add_argument("--iters", type=int, default=200, help="optimiser steps for --workload batch20/uc32/spsa/solve")
     ap.add_argument("--shots", type=int, default=1 << 20, help="shots per request for --workload sample")

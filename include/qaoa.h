@@ -507,6 +507,17 @@ qaoa_status qaoa_expect_noalloc(const void *amps, const int32_t *table, int n, i
 qaoa_status qaoa_profile_read(qaoa_ctx ctx, int kind, int64_t *launches, double *ms,
                               double *bytes, int reset);
 
+/* Sustained rate of one arithmetic pipe of this GPU, the denominator for
+ * kernels bound by plain arithmetic rather than by memory (the paper has no
+ * counterpart: this is measurement support).  kind: 0 = FP32 FMA, 1 = packed
+ * f32x2 FMA, 2 = FP64 FMA, 3 = fast sin/cos pairs.  Runs 8 CTAs per SM of
+ * independent FMA (or sin/cos) chains on the context stream, timed with CUDA
+ * events after a warm-up launch.  *ops_per_s: instructions' lane operations
+ * per second (one FMA, one f32x2 FMA lane pair, or one sin/cos pair);
+ * *flops_per_s: 2 per FMA, 4 per f32x2 FMA, 1 per sin/cos pair.  Either may be
+ * NULL. */
+qaoa_status qaoa_peak_probe(qaoa_ctx ctx, int kind, double *ops_per_s, double *flops_per_s);
+
 #ifdef __cplusplus
 }
 #endif

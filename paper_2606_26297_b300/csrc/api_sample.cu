@@ -717,4 +717,32 @@ qaoa_status qaoa_telegate_simulate(qaoa_ctx c, qaoa_cost cost, const int32_t *qp
     return QAOA_OK;
 }
 
+qaoa_status qaoa_peak_probe(qaoa_ctx c, int kind, double *ops_per_s, double *flops_per_s) {
+    if (!c || kind < 0 || kind > 3) return fail(QAOA_ERR_INVALID_ARG, "bad context or kind %d", kind);
+    CUDA_TRY(cudaSetDevice(c->device));
+    QAOA_TRY(c->misc.ensure(4096, &c->held, c->opt.memory_budget));
+    const int blocks = c->num_sms * 8;
+    const int iters = kind == 2 ? 2048 : kind == 3 ? 8192 : 32768;
+    float *out = c->misc.as<float>();
+    CUDA_TRY(launch_peak(kind, blocks, iters, out, c->stream));  // warm-up
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    const int reps = 3;
+    cudaError_t err = cudaEventRecord(e0, c->stream);
+    for (int r = 0; r < reps && !err; ++r) err = launch_peak(kind, blocks, iters, out, c->stream);
+    if (!err) err = cudaEventRecord(e1, c->stream);
+    if (!err) err = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (!err) err = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CUDA_TRY(err);
+    c->launches_total += 1 + reps;
+    const double ops = peak_ops_per_launch(blocks, iters) * reps / (ms / 1e3);
+    if (ops_per_s) *ops_per_s = ops;
+    if (flops_per_s) *flops_per_s = kind == 1 ? 4.0 * ops : kind == 3 ? ops : 2.0 * ops;
+    return QAOA_OK;
+}
+
 }  // extern "C"

@@ -104,6 +104,10 @@ int telegate_smem_bytes(int n);
 cudaError_t launch_telegate(const TgOp *ops, int nops, int n, unsigned long long seed, int traj0, int count,
                             float2 *data_out, const float2 *mono, double *fid_out, cudaStream_t st);
 
+// arithmetic-pipe micro-benchmarks (kernels_peak.cu)
+cudaError_t launch_peak(int kind, int blocks, int iters, float *out, cudaStream_t st);
+double peak_ops_per_launch(int blocks, int iters);
+
 struct FactArgs {
     const int32_t *T;
     int n, M;

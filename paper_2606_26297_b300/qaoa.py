@@ -133,6 +133,7 @@ _SIGS = {
     "qaoa_classify": ([_P, _PI32, _I, _PI64, _PI64, _PI64, _PI64], _I),
     "qaoa_check_factorisation": ([_P, _P, _PI32, _D, _PI64, _PD], _I),
     "qaoa_profile_read": ([_P, _I, _PI64, _PD, _PD, _I], _I),
+    "qaoa_peak_probe": ([_P, _I, _PD, _PD], _I),
     "qaoa_expect_noalloc": ([_P, _P, _I, ctypes.c_int32, ctypes.c_int64, _P, _PD], _I),
 }
 for _name, (_args, _res) in _SIGS.items():
@@ -541,6 +542,14 @@ def qaoa_profile_read(ctx, kind: int, reset: bool = False):
     ms, by = ctypes.c_double(), ctypes.c_double()
     _check(_lib.qaoa_profile_read(ctx, int(kind), ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by), int(reset)))
     return {"launches": n.value, "ms": ms.value, "bytes": by.value}
+
+
+def qaoa_peak_probe(ctx, kind: int):
+    """Sustained (ops/s, flop/s) of one arithmetic pipe: 0 FP32 FMA, 1 f32x2
+    FMA, 2 FP64 FMA, 3 sin/cos pairs."""
+    o, f = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.qaoa_peak_probe(ctx, int(kind), ctypes.byref(o), ctypes.byref(f)))
+    return o.value, f.value
 
 
 PROFILE_KINDS = {"fwd_pass": 0, "rev_pass": 1, "cost_build": 2, "small_resident": 3, "factorisation": 4,

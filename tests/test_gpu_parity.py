@@ -476,3 +476,17 @@ def test_factorisation_noncontiguous(q, ctx):
     mism, perr = q.qaoa_check_factorisation(ctx, cost, qpu_of, 1.3)
     assert mism == 0 and perr < 1e-5
     q.qaoa_cost_destroy(cost)
+
+
+def test_peak_probe_rates(q):
+    """The arithmetic-pipe probe returns finite positive rates for every kind
+    and rejects an unknown kind; FP32 FMA runs far faster than FP64 FMA on this
+    part."""
+    ctx = q.qaoa_ctx_create(0)
+    rates = [q.qaoa_peak_probe(ctx, k) for k in range(4)]
+    for ops, flops in rates:
+        assert np.isfinite(ops) and ops > 0 and flops >= ops
+    assert rates[0][1] > 4 * rates[2][1]
+    with pytest.raises(q.QaoaError):
+        q.qaoa_peak_probe(ctx, 4)
+    q.qaoa_ctx_destroy(ctx)
