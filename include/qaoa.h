@@ -507,6 +507,15 @@ qaoa_status qaoa_expect_noalloc(const void *amps, const int32_t *table, int n, i
 qaoa_status qaoa_profile_read(qaoa_ctx ctx, int kind, int64_t *launches, double *ms,
                               double *bytes, int reset);
 
+/* Diagnostic of the failure path of the device-side waits (the paper has no
+ * counterpart).  Every TMA-pipelined pass kernel waits for its copies with a
+ * bounded wait: after about 2 s it records QAOA_ERR_TIMEOUT in the context's
+ * status word and returns, instead of hanging the GPU.  This call launches one
+ * CTA that waits on a copy that is never issued, so the wait must expire: it
+ * returns QAOA_ERR_TIMEOUT (the expected result, after about 4 s) and leaves
+ * the context usable; QAOA_OK would mean the wait did not give up. */
+qaoa_status qaoa_wait_probe(qaoa_ctx ctx);
+
 /* Sustained rate of one arithmetic pipe of this GPU, the denominator for
  * kernels bound by plain arithmetic rather than by memory (the paper has no
  * counterpart: this is measurement support).  kind: 0 = FP32 FMA, 1 = packed

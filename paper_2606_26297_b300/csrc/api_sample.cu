@@ -745,4 +745,20 @@ qaoa_status qaoa_peak_probe(qaoa_ctx c, int kind, double *ops_per_s, double *flo
     return QAOA_OK;
 }
 
+qaoa_status qaoa_wait_probe(qaoa_ctx c) {
+    if (!c) return fail(QAOA_ERR_INVALID_ARG, "null context");
+    CUDA_TRY(cudaSetDevice(c->device));
+    QAOA_TRY(c->status.ensure(16, &c->held, c->opt.memory_budget));
+    CUDA_TRY(cudaMemsetAsync(c->status.p, 0, 4, c->stream));
+    CUDA_TRY(launch_wait_probe(c->status.as<unsigned int>(), c->stream));
+    c->launches_total += 1;
+    unsigned int hs = 0;
+    CUDA_TRY(cudaMemcpyAsync(&hs, c->status.p, 4, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    CUDA_TRY(cudaMemsetAsync(c->status.p, 0, 4, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (hs) return fail(QAOA_ERR_TIMEOUT, "the probe's bounded wait expired, as it must");
+    return QAOA_OK;
+}
+
 }  // extern "C"

@@ -549,6 +549,19 @@ __global__ void __launch_bounds__(PASS_THREADS, 2)
     }
 }
 
+// Diagnostic of the bounded waits every TMA-pipelined kernel uses: one CTA
+// announces a 16-byte transaction on an mbarrier and issues no copy, so the
+// phase never completes; stage_ready() gives up after its limit (about 2 s of
+// clock, then a second bounded wait), records the timeout in the status word
+// and the CTA returns.  Nothing is left in flight.
+__global__ void wait_probe_kernel(unsigned int *status) {
+    __shared__ __align__(8) unsigned long long mbar;
+    if (threadIdx.x == 0) mbar_init(&mbar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_expect_tx(&mbar, 16u);
+    if (!stage_ready(&mbar, 0u, status)) return;
+}
+
 // ---------------------------------------------------------------------------
 // host side: tensor maps and launchers
 // ---------------------------------------------------------------------------
@@ -757,6 +770,11 @@ cudaError_t launch_fwd_cost_tma(int type, const PassArgs &a, int grid, unsigned 
     if (grid > nunits) grid = nunits;
     return type == 0 ? fct_launch<0>(a, m, mc, grid, nunits, status, st)
                      : fct_launch<1>(a, m, mc, grid, nunits, status, st);
+}
+
+cudaError_t launch_wait_probe(unsigned int *status, cudaStream_t st) {
+    wait_probe_kernel<<<1, 128, 0, st>>>(status);
+    return cudaGetLastError();
 }
 
 }  // namespace qaoa

@@ -101,6 +101,7 @@ cudaError_t launch_fwd_pass(int type, const PassArgs &a, cudaStream_t st);
 cudaError_t launch_final_pass(int type, const PassArgs &a, int grid, unsigned int *status, cudaStream_t st);
 cudaError_t launch_rev_pass(int type, const PassArgs &a, int grid, unsigned int *status, cudaStream_t st);
 cudaError_t launch_rev_mid(int type, const PassArgs &a, int grid, unsigned int *status, cudaStream_t st);
+cudaError_t launch_wait_probe(unsigned int *status, cudaStream_t st);
 cudaError_t launch_fwd_cost_tma(int type, const PassArgs &a, int grid, unsigned int *status, cudaStream_t st);
 cudaError_t launch_reduce_partials(const double *partials, int nitems, int nblocks, double *out,
                                    cudaStream_t st);

@@ -134,6 +134,7 @@ _SIGS = {
     "qaoa_check_factorisation": ([_P, _P, _PI32, _D, _PI64, _PD], _I),
     "qaoa_profile_read": ([_P, _I, _PI64, _PD, _PD, _I], _I),
     "qaoa_peak_probe": ([_P, _I, _PD, _PD], _I),
+    "qaoa_wait_probe": ([_P], _I),
     "qaoa_expect_noalloc": ([_P, _P, _I, ctypes.c_int32, ctypes.c_int64, _P, _PD], _I),
 }
 for _name, (_args, _res) in _SIGS.items():
@@ -550,6 +551,12 @@ def qaoa_peak_probe(ctx, kind: int):
     o, f = ctypes.c_double(), ctypes.c_double()
     _check(_lib.qaoa_peak_probe(ctx, int(kind), ctypes.byref(o), ctypes.byref(f)))
     return o.value, f.value
+
+
+def qaoa_wait_probe(ctx) -> None:
+    """Make one bounded device wait expire; raises QaoaError with status
+    QAOA_ERR_TIMEOUT, which is the expected outcome."""
+    _check(_lib.qaoa_wait_probe(ctx))
 
 
 PROFILE_KINDS = {"fwd_pass": 0, "rev_pass": 1, "cost_build": 2, "small_resident": 3, "factorisation": 4,

@@ -490,3 +490,22 @@ def test_peak_probe_rates(q):
     with pytest.raises(q.QaoaError):
         q.qaoa_peak_probe(ctx, 4)
     q.qaoa_ctx_destroy(ctx)
+
+
+def test_bounded_wait_expires_and_context_survives(q):
+    """Failure path of the device waits without a GPU fault: a wait on a copy
+    that is never issued runs out (QAOA_ERR_TIMEOUT from the status word), and
+    the same context then evaluates a gradient that matches the oracle."""
+    ctx = q.qaoa_ctx_create(0)
+    with pytest.raises(q.QaoaError) as ei:
+        q.qaoa_wait_probe(ctx)
+    assert ei.value.status == q.QAOA_ERR_TIMEOUT
+    Q = inst.upper_int_qubo(14, 9090)
+    cost = q.qaoa_build_cost(ctx, Q.H, Q.f, Q.c0, "i32")
+    g, b = inst.ramp_angles(2, gamma_scale=0.2)
+    E, dg, db = q.qaoa_grad(ctx, cost, g, b)
+    F = oracle.cost_table(oracle.canonical_of(Q))
+    Eo, dgo, dbo = oracle.grad_adjoint(F, g, b)
+    assert abs(E - Eo) / np.max(np.abs(F)) <= 1e-5
+    q.qaoa_cost_destroy(cost)
+    q.qaoa_ctx_destroy(ctx)
