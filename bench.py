@@ -450,9 +450,10 @@ def run_workload(args):
     elif args.workload == "autotune":
         Q, g, b = inst.workload_dense30(args.n, args.p)
         cost = q.qaoa_build_cost(ctx, Q.H, Q.f, Q.c0, "f32")
-        best, ms = q.qaoa_autotune(ctx, cost, 2)
+        best, ms, modes = q.qaoa_autotune(ctx, cost, 2, with_modes=True)
         res.update({"n": args.n, "p_timed": 2, "best_fusion_width": best,
-                    "ms_fwd_adjoint_by_width": {str(k): v for k, v in sorted(ms.items(), reverse=True)}})
+                    "ms_fwd_adjoint_by_width": {str(k): v for k, v in sorted(ms.items(), reverse=True)},
+                    "ms_fwd_adjoint_by_adjoint_form": modes})
         q.qaoa_cost_destroy(cost)
     elif args.workload == "uc32":
         Q, g, b = inst.workload_uc32()

@@ -375,10 +375,15 @@ qaoa_status qaoa_solve(qaoa_ctx ctx, qaoa_cost cost, const qaoa_solve_options *o
  * each width in {10, 9, 8, 7, 6, 5} (<= n) with CUDA events on the context
  * stream.  The fastest width is returned in *best_k and kept by the context
  * for that n (used when options.autotune = 1 and max_fused_qubits = 0).
- * ms_by_k (host, 8 doubles, may be NULL): ms_by_k[k - 3] = time for width k,
- * NaN where not timed.  n <= 12 is rejected (the shared-memory kernel has no
- * passes).  Sec. 4.1 compiles a circuit once and reuses it; this is the
- * counterpart for the pass plan. */
+ * At the chosen width it then times the adjoint with stored forward states
+ * (the AUTO choice: uncompute where they do not fit) against the uncompute
+ * sweep and keeps the faster form for that n (used when options.autotune = 1
+ * and adjoint_mode = AUTO).  ms_by_k (host, 8 doubles, may be NULL):
+ * ms_by_k[k - 3] = time for width k (k = 5..10), NaN where not timed; the
+ * slots of widths 3 and 4, which are never tuned, receive the times of the
+ * two adjoint forms: ms_by_k[0] stored (AUTO), ms_by_k[1] uncompute.  n <= 12
+ * is rejected (the shared-memory kernel has no passes).  Sec. 4.1 compiles a
+ * circuit once and reuses it; this is the counterpart for the pass plan. */
 qaoa_status qaoa_autotune(qaoa_ctx ctx, qaoa_cost cost, int p, int32_t *best_k, double *ms_by_k);
 
 /* ---- DQAOA bookkeeping (host) and the GPU factorisation invariant ------- */

@@ -8,6 +8,8 @@
 #include <memory>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "kernels_misc.h"
 #include "qaoa_internal.h"
 #include "schedule.cuh"
@@ -129,7 +131,12 @@ qaoa_status make_run_plan(qaoa_ctx c, PlanRun &r, const PlanBufs &b) {
     const int maxq = maxq_for(c, r.n);
     r.stored = false;
     r.nslots = 0;
-    if (r.grad && c->opt.adjoint_mode != QAOA_ADJ_UNCOMPUTE) {
+    bool tuned_unc = false;
+    if (c->opt.autotune && c->opt.adjoint_mode == QAOA_ADJ_AUTO) {
+        auto it = c->tuned_uncompute.find(r.n);
+        tuned_unc = it != c->tuned_uncompute.end() && it->second;
+    }
+    if (r.grad && c->opt.adjoint_mode != QAOA_ADJ_UNCOMPUTE && !tuned_unc) {
         int ns = 0;
         std::vector<PassPlan> sp = make_plan(r.n, r.p, true, maxq, true, &ns);
         const double N8 = std::ldexp(8.0 * r.nitems, r.n);
@@ -243,12 +250,17 @@ qaoa_status enqueue_plan(qaoa_ctx c, PlanBufs &b, const PlanRun &r, const int32_
         const double bytes = pass_bytes_per_amp(pl) * std::ldexp((double)r.nitems, n);
         {
             ProfScope ps(c, pl.kind >= 2 ? 1 : 0, bytes, profile);
+            // a named range per pass for timeline tools (no cost when no tool is attached)
+            static const char *const pass_names[4] = {"qaoa forward pass", "qaoa final pass",
+                                                      "qaoa reverse pass (psi, lambda)", "qaoa reverse pass (lambda)"};
+            nvtxRangePushA(pass_names[pl.kind & 3]);
             cudaError_t e = pl.kind == 0   ? (a.has_pre && a.has_cost && a.has_post && !a.init
                                                   ? launch_fwd_cost_tma(pl.type, a, 2 * c->num_sms, stw, c->stream)
                                                   : launch_fwd_pass(pl.type, a, c->stream))
                             : pl.kind == 1 ? launch_final_pass(pl.type, a, c->num_sms, stw, c->stream)
                             : pl.kind == 2 ? launch_rev_pass(pl.type, a, c->num_sms, stw, c->stream)
                                            : launch_rev_mid(pl.type, a, c->num_sms, stw, c->stream);
+            nvtxRangePop();
             if (e) return fail(QAOA_ERR_CUDA, "layer-pass launch failed: %s", cudaGetErrorString(e));
             c->launches_total += 1;
         }
@@ -419,10 +431,37 @@ qaoa_status tune_width(qaoa_ctx c, const qaoa_cost_s *cost, int p, int *best_k, 
             bk = k;
         }
     }
+    // at the chosen width, time the adjoint with stored forward states (when
+    // they fit) against the uncompute sweep and keep the faster for this n
+    double ms_mode[2] = {1e300, 1e300};
+    const int saved_mode = c->opt.adjoint_mode;
+    c->opt.max_fused_qubits = bk;
+    for (int m = 0; m < 2 && st == QAOA_OK; ++m) {
+        c->opt.adjoint_mode = m == 0 ? QAOA_ADJ_AUTO : QAOA_ADJ_UNCOMPUTE;
+        double E = 0.0;
+        st = run_single(c, cost, p, g.data(), b.data(), true, nullptr, &E, dg.data(), db.data(), 0, nullptr, nullptr);
+        if (st != QAOA_OK) break;
+        cudaEvent_t e0 = get_event(c), e1 = get_event(c);
+        cudaEventRecord(e0, c->stream);
+        st = run_single(c, cost, p, g.data(), b.data(), true, nullptr, &E, dg.data(), db.data(), 0, nullptr, nullptr);
+        cudaEventRecord(e1, c->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        c->ev_free.push_back(e0);
+        c->ev_free.push_back(e1);
+        ms_mode[m] = ms;
+    }
+    c->opt.adjoint_mode = saved_mode;
     c->opt.max_fused_qubits = saved;
     c->opt.profile = saved_prof;
     QAOA_TRY(st);
     c->tuned_k[n] = bk;
+    c->tuned_uncompute[n] = ms_mode[1] < ms_mode[0] ? 1 : 0;
+    if (ms_by_k) {
+        ms_by_k[0] = ms_mode[0];  // widths 3 and 4 are never timed: their slots carry the adjoint forms
+        ms_by_k[1] = ms_mode[1];
+    }
     if (best_k) *best_k = bk;
     return QAOA_OK;
 }

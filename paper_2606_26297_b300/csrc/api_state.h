@@ -108,6 +108,7 @@ struct qaoa_ctx_s {
     int64_t launches_total = 0;  // every kernel launched by this context
     cudaStream_t aux_stream = nullptr;  // owned; runs captured optimisation loops
     std::map<int, int> tuned_k;         // fusion width picked by the autotuner, by n
+    std::map<int, int> tuned_uncompute; // 1: the autotuner found the uncompute sweep faster, by n
     DevBuf sample_items, sample_scratch, sample_out, small_states;  // measurement by shots
 };
 

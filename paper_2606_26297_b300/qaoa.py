@@ -333,12 +333,17 @@ def qaoa_optimize_adam(ctx, costs, gamma, beta, iterations: int, item_cost=None,
     return g, b, hist, E
 
 
-def qaoa_autotune(ctx, cost, p: int = 2):
-    """Time every fusion width; returns (best width, {width: ms})."""
+def qaoa_autotune(ctx, cost, p: int = 2, with_modes: bool = False):
+    """Time every fusion width; returns (best width, {width: ms}), and with
+    with_modes also {"stored": ms, "uncompute": ms} of the two adjoint forms
+    at that width."""
     k = ctypes.c_int32()
     ms = np.zeros(8)
     _check(_lib.qaoa_autotune(ctx, cost, int(p), ctypes.byref(k), _dptr(ms)))
-    return k.value, {w: float(ms[w - 3]) for w in range(3, 11) if not np.isnan(ms[w - 3])}
+    widths = {w: float(ms[w - 3]) for w in range(5, 11) if not np.isnan(ms[w - 3])}
+    if with_modes:
+        return k.value, widths, {"stored": float(ms[0]), "uncompute": float(ms[1])}
+    return k.value, widths
 
 
 # ---- measurement by shots and SPSA ----------------------------------------------------------

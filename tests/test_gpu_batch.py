@@ -185,6 +185,27 @@ def test_autotune_fusion_width(q, ctx):
         q.qaoa_ctx_destroy(c)
 
 
+def test_autotune_adjoint_form(q, ctx):
+    """At n = 24 (three qubit groups, so stored forward states apply) the tuner
+    also times the two adjoint forms; a context with autotune on then
+    evaluates bit for bit like a context fixed to the chosen width and form."""
+    Q = inst.upper_int_qubo(24, 4650)
+    g, b = inst.ramp_angles(4, gamma_scale=0.1)
+    ca = q.qaoa_ctx_create(0, autotune=True)
+    ka = _cost(q, ca, Q)
+    best, ms, modes = q.qaoa_autotune(ca, ka, 2, with_modes=True)
+    assert modes["stored"] > 0 and modes["uncompute"] > 0
+    mode = q.QAOA_ADJ_UNCOMPUTE if modes["uncompute"] < modes["stored"] else q.QAOA_ADJ_AUTO
+    cf = q.qaoa_ctx_create(0, max_fused_qubits=best, adjoint_mode=mode)
+    kf = _cost(q, cf, Q)
+    ra = q.qaoa_grad(ca, ka, g, b)
+    rf = q.qaoa_grad(cf, kf, g, b)
+    assert ra[0] == rf[0] and np.array_equal(ra[1], rf[1]) and np.array_equal(ra[2], rf[2])
+    for c, k in ((ca, ka), (cf, kf)):
+        q.qaoa_cost_destroy(k)
+        q.qaoa_ctx_destroy(c)
+
+
 def test_autograd_functions(q, ctx):
     """torch.autograd.Function wrappers: backward of E (single and batched)
     against the oracle's gradient and against central differences of the
