@@ -368,6 +368,21 @@ qaoa_status qaoa_solve(qaoa_ctx ctx, qaoa_cost cost, const qaoa_solve_options *o
                        double *beta, int elite, uint64_t *elite_idx, double *elite_cost, int64_t *elite_count,
                        qaoa_sample_metrics *depth_metrics, qaoa_solve_result *out);
 
+/* qaoa_optimize_adam continuing an earlier run, for checkpointed optimisation
+ * (the paper records the optimiser history, Sec. 3.4; the state needed to
+ * resume it is the moments and the step count).  m, v: host, B*2p doubles
+ * each, in/out: m[b*2p + l] and m[b*2p + p + l] are the first moments of
+ * gamma_l and beta_l of item b (v the second moments); zeros start a fresh
+ * run.  step: host, in/out: Adam steps taken before this call (the bias
+ * correction continues from it); it is advanced by `iterations`.  Running
+ * k1 iterations and then k2 more with the returned gamma, beta, m, v and step
+ * equals k1 + k2 iterations in one call.  history[t*B + b] counts the
+ * iterations of this call. */
+qaoa_status qaoa_optimize_adam_resume(qaoa_ctx ctx, int nq, const qaoa_cost *costs, const int32_t *item_cost,
+                                      int B, int p, double *gamma, double *beta, const qaoa_adam_options *opt,
+                                      double *history, double *final_expect, double *m, double *v,
+                                      int32_t *step);
+
 /* ---- autotuning ---------------------------------------------------------- */
 
 /* Pick the fusion width (qubits per mixer pass) for states of cost's n by

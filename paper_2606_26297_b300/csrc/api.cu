@@ -1138,11 +1138,24 @@ qaoa_status qaoa_grad_batch(qaoa_ctx c, int nq, const qaoa_cost *costs, const in
     return run_batch(c, nq, costs, item_cost, B, p, gamma, beta, expect, dgamma, dbeta, nullptr);
 }
 
-qaoa_status qaoa_optimize_adam(qaoa_ctx c, int nq, const qaoa_cost *costs, const int32_t *item_cost, int B, int p,
-                               double *gamma, double *beta, const qaoa_adam_options *aopt, double *history,
-                               double *final_expect) {
+}  // extern "C"
+
+namespace {
+
+// Adam state of a run that continues an earlier one (host, caller-owned):
+// m, v as [B][2p] (gamma then beta of each item), step = steps already taken.
+struct AdamResume {
+    double *m = nullptr, *v = nullptr;
+    int32_t *step = nullptr;
+};
+
+qaoa_status optimize_adam(qaoa_ctx c, int nq, const qaoa_cost *costs, const int32_t *item_cost, int B, int p,
+                          double *gamma, double *beta, const qaoa_adam_options *aopt, double *history,
+                          double *final_expect, const AdamResume &rs) {
     if (!c || !costs || nq < 1 || B < 1 || !gamma || !beta || !aopt)
         return fail(QAOA_ERR_INVALID_ARG, "bad optimiser arguments");
+    const int step0 = rs.step ? *rs.step : 0;
+    if (step0 < 0) return fail(QAOA_ERR_INVALID_ARG, "step=%d < 0", step0);
     if (p < 1 || p > SMALL_MAXP) return fail(QAOA_ERR_INVALID_ARG, "p=%d not in [1, %d]", p, SMALL_MAXP);
     if (aopt->iterations < 1) return fail(QAOA_ERR_INVALID_ARG, "iterations=%d < 1", aopt->iterations);
     if (c->opt.state_fp64) return fail(QAOA_ERR_INVALID_ARG, "the optimiser runs in complex64 only");
@@ -1176,9 +1189,27 @@ qaoa_status qaoa_optimize_adam(qaoa_ctx c, int nq, const qaoa_cost *costs, const
         QAOA_TRY(b->adam_v.ensure(2 * K * p * 8, &c->held, c->opt.memory_budget));
         QAOA_TRY(b->adam_step.ensure(16, &c->held, c->opt.memory_budget));
         QAOA_TRY(b->history.ensure((size_t)iters * K * 8, &c->held, c->opt.memory_budget));
-        CUDA_TRY(cudaMemsetAsync(b->adam_m.p, 0, 2 * K * p * 8, c->stream));
-        CUDA_TRY(cudaMemsetAsync(b->adam_v.p, 0, 2 * K * p * 8, c->stream));
-        CUDA_TRY(cudaMemsetAsync(b->adam_step.p, 0, 16, c->stream));
+        if (rs.m) {
+            // device moments are [gamma | beta][item][l]
+            std::vector<double> hm(2 * K * p), hv(2 * K * p);
+            for (size_t i = 0; i < K; ++i)
+                for (int l = 0; l < p; ++l)
+                    for (int h = 0; h < 2; ++h) {
+                        const size_t src = (size_t)items[i] * 2 * p + (size_t)h * p + l;
+                        const size_t dst = (size_t)h * K * p + i * p + l;
+                        hm[dst] = rs.m[src];
+                        hv[dst] = rs.v[src];
+                    }
+            CUDA_TRY(cudaMemcpyAsync(b->adam_m.p, hm.data(), hm.size() * 8, cudaMemcpyHostToDevice, c->stream));
+            CUDA_TRY(cudaMemcpyAsync(b->adam_v.p, hv.data(), hv.size() * 8, cudaMemcpyHostToDevice, c->stream));
+            CUDA_TRY(cudaStreamSynchronize(c->stream));
+        } else {
+            CUDA_TRY(cudaMemsetAsync(b->adam_m.p, 0, 2 * K * p * 8, c->stream));
+            CUDA_TRY(cudaMemsetAsync(b->adam_v.p, 0, 2 * K * p * 8, c->stream));
+        }
+        const int st0[4] = {step0, 0, 0, 0};
+        CUDA_TRY(cudaMemcpyAsync(b->adam_step.p, st0, sizeof st0, cudaMemcpyHostToDevice, c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
         AdamArgs a{};
         a.gamma = b->gamma.as<double>();
         a.beta = b->beta.as<double>();
@@ -1192,6 +1223,7 @@ qaoa_status qaoa_optimize_adam(qaoa_ctx c, int nq, const qaoa_cost *costs, const
         a.estride = estride;
         a.history = b->history.as<double>();
         a.max_steps = iters;
+        a.step0 = step0;
         a.nitems = (int)K;
         a.p = p;
         a.lr = lr;
@@ -1288,13 +1320,49 @@ qaoa_status qaoa_optimize_adam(qaoa_ctx c, int nq, const qaoa_cost *costs, const
                 for (int t = 0; t < iters; ++t) history[(size_t)t * B + b] = hist[(size_t)t * K + i];
             if (final_expect) final_expect[b] = E[i];
         }
+        if (rs.m) {
+            std::vector<double> hm(2 * K * p), hv(2 * K * p);
+            CUDA_TRY(cudaMemcpyAsync(hm.data(), o.a.m, hm.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+            CUDA_TRY(cudaMemcpyAsync(hv.data(), o.a.v, hv.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+            CUDA_TRY(cudaStreamSynchronize(c->stream));
+            for (size_t i = 0; i < K; ++i)
+                for (int l = 0; l < p; ++l)
+                    for (int h = 0; h < 2; ++h) {
+                        const size_t dst = (size_t)items[i] * 2 * p + (size_t)h * p + l;
+                        const size_t src = (size_t)h * K * p + i * p + l;
+                        rs.m[dst] = hm[src];
+                        rs.v[dst] = hv[src];
+                    }
+        }
     }
+    if (rs.step) *rs.step = step0 + iters;
     // order the caller's stream after the loop
     cudaEvent_t done = get_event(c);
     CUDA_TRY(cudaEventRecord(done, c->aux_stream));
     CUDA_TRY(cudaStreamWaitEvent(user, done, 0));
     c->ev_free.push_back(done);
     return QAOA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+qaoa_status qaoa_optimize_adam(qaoa_ctx c, int nq, const qaoa_cost *costs, const int32_t *item_cost, int B, int p,
+                               double *gamma, double *beta, const qaoa_adam_options *aopt, double *history,
+                               double *final_expect) {
+    return optimize_adam(c, nq, costs, item_cost, B, p, gamma, beta, aopt, history, final_expect, AdamResume{});
+}
+
+qaoa_status qaoa_optimize_adam_resume(qaoa_ctx c, int nq, const qaoa_cost *costs, const int32_t *item_cost, int B,
+                                      int p, double *gamma, double *beta, const qaoa_adam_options *aopt,
+                                      double *history, double *final_expect, double *m, double *v, int32_t *step) {
+    if (!m || !v || !step) return fail(QAOA_ERR_INVALID_ARG, "m, v and step are required");
+    AdamResume rs;
+    rs.m = m;
+    rs.v = v;
+    rs.step = step;
+    return optimize_adam(c, nq, costs, item_cost, B, p, gamma, beta, aopt, history, final_expect, rs);
 }
 
 qaoa_status qaoa_autotune(qaoa_ctx c, qaoa_cost cost, int p, int32_t *best_k, double *ms_by_k) {

@@ -82,8 +82,9 @@ __global__ void adam_kernel(AdamArgs a) {
         const double vh = v / (1.0 - pow(a.beta2, (double)t));
         th[k] -= a.lr * mh / (sqrt(vh) + a.eps);
     }
-    if (a.history && idx < a.nitems && t - 1 < a.max_steps)
-        a.history[(size_t)(t - 1) * a.nitems + idx] = a.E[(size_t)idx * a.estride];
+    const int row = t - 1 - a.step0;
+    if (a.history && idx < a.nitems && row >= 0 && row < a.max_steps)
+        a.history[(size_t)row * a.nitems + idx] = a.E[(size_t)idx * a.estride];
 }
 
 __global__ void adam_step_kernel(int *step) { *step += 1; }

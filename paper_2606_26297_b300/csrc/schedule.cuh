@@ -453,6 +453,7 @@ struct AdamArgs {
     int estride;
     double *history;             // [max_steps][nitems] or null
     int max_steps, nitems, p;
+    int step0;                   // steps taken before this run (history rows count from it)
     double lr, beta1, beta2, eps;
 };
 cudaError_t launch_adam(const AdamArgs &a, cudaStream_t st);

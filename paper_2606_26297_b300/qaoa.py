@@ -116,6 +116,8 @@ _SIGS = {
     "qaoa_optimize_adam": ([_P, _I, ctypes.POINTER(_P), _PI32, _I, _I, _PD, _PD,
                             ctypes.POINTER(qaoa_adam_options), _PD, _PD], _I),
     "qaoa_autotune": ([_P, _P, _I, _PI32, _PD], _I),
+    "qaoa_optimize_adam_resume": ([_P, _I, ctypes.POINTER(_P), _PI32, _I, _I, _PD, _PD,
+                                   ctypes.POINTER(qaoa_adam_options), _PD, _PD, _PD, _PD, _PI32], _I),
     "qaoa_state_from_host": ([_P, _I, _I, _P, ctypes.POINTER(_P)], _I),
     "qaoa_sample": ([_P, _P, _P, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint64, _PU64, _PU64, _PD, _PD], _I),
     "qaoa_sample_stats": ([ctypes.c_int64, _PU64, _PD, _D, _I, _PU64, _PD, _PI64, _I, _D, ctypes.c_uint64, _D,
@@ -331,6 +333,34 @@ def qaoa_optimize_adam(ctx, costs, gamma, beta, iterations: int, item_cost=None,
     _check(_lib.qaoa_optimize_adam(ctx, len(costs), arr, None if ic is None else ic.ctypes.data_as(_PI32), B, p,
                                    _dptr(g), _dptr(b), ctypes.byref(opt), _dptr(hist), _dptr(E)))
     return g, b, hist, E
+
+
+def qaoa_optimize_adam_resume(ctx, costs, gamma, beta, iterations: int, state=None, item_cost=None,
+                              lr: float = 0.0, beta1: float = 0.0, beta2: float = 0.0, eps: float = 0.0,
+                              use_graph: bool = True):
+    """qaoa_optimize_adam from a saved state (None: a fresh run).  Returns
+    (gamma, beta, history, final E, state) with state = {"m", "v", "step"}
+    to pass to the next call."""
+    g = np.array(np.asarray(gamma, dtype=np.float64), order="C", copy=True)
+    b = np.array(np.asarray(beta, dtype=np.float64), order="C", copy=True)
+    B, p = g.shape
+    if state is None:
+        state = {"m": np.zeros((B, 2 * p)), "v": np.zeros((B, 2 * p)), "step": 0}
+    m = np.array(state["m"], dtype=np.float64, order="C", copy=True)
+    v = np.array(state["v"], dtype=np.float64, order="C", copy=True)
+    step = ctypes.c_int32(int(state["step"]))
+    arr = (_P * len(costs))(*[c.value if isinstance(c, _P) else c for c in costs])
+    ic = None if item_cost is None else np.ascontiguousarray(np.asarray(item_cost, dtype=np.int32))
+    opt = qaoa_adam_options()
+    opt.lr, opt.beta1, opt.beta2, opt.eps = float(lr), float(beta1), float(beta2), float(eps)
+    opt.iterations = int(iterations)
+    opt.disable_graph = 0 if use_graph else 1
+    hist = np.zeros((int(iterations), B))
+    E = np.zeros(B)
+    _check(_lib.qaoa_optimize_adam_resume(ctx, len(costs), arr, None if ic is None else ic.ctypes.data_as(_PI32), B,
+                                          p, _dptr(g), _dptr(b), ctypes.byref(opt), _dptr(hist), _dptr(E), _dptr(m),
+                                          _dptr(v), ctypes.byref(step)))
+    return g, b, hist, E, {"m": m, "v": v, "step": step.value}
 
 
 def qaoa_autotune(ctx, cost, p: int = 2, with_modes: bool = False):

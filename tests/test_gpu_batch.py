@@ -206,6 +206,26 @@ def test_autotune_adjoint_form(q, ctx):
         q.qaoa_ctx_destroy(c)
 
 
+def test_adam_resume_equals_one_run(q, ctx):
+    """Checkpointed optimisation: 6 Adam iterations and then 5 more from the
+    returned angles, moments and step count give the same angles and history,
+    bit for bit, as 11 iterations in one call (a mixed batch: n = 10 items on
+    the shared-memory path and n = 14 items on the pass path)."""
+    Qa, Qb = inst.upper_int_qubo(10, 4800), inst.upper_int_qubo(14, 4801)
+    ca, cb = _cost(q, ctx, Qa), _cost(q, ctx, Qb)
+    g0, b0 = inst.random_angles(2, 4, 4802, gamma_scale=0.2)
+    ic = [0, 1, 0, 1]
+    g1, b1, h1, E1, st = q.qaoa_optimize_adam_resume(ctx, [ca, cb], g0, b0, 6, item_cost=ic, lr=0.02)
+    assert st["step"] == 6 and np.any(st["m"] != 0)
+    g2, b2, h2, E2, st2 = q.qaoa_optimize_adam_resume(ctx, [ca, cb], g1, b1, 5, state=st, item_cost=ic, lr=0.02)
+    assert st2["step"] == 11
+    gf, bf, hf, Ef = q.qaoa_optimize_adam(ctx, [ca, cb], g0, b0, 11, item_cost=ic, lr=0.02)
+    assert np.array_equal(g2, gf) and np.array_equal(b2, bf)
+    assert np.array_equal(np.concatenate([h1, h2]), hf) and np.array_equal(E2, Ef)
+    q.qaoa_cost_destroy(ca)
+    q.qaoa_cost_destroy(cb)
+
+
 def test_autograd_functions(q, ctx):
     """torch.autograd.Function wrappers: backward of E (single and batched)
     against the oracle's gradient and against central differences of the
