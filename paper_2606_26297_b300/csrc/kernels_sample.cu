@@ -42,15 +42,18 @@ __host__ __device__ inline Geo geo_of(int n) {
 }
 
 // floor(v^2 2^60) for |v| < 2 (larger or non-finite values saturate at 2^62):
-// v = M 2^e2 with an integer mantissa M, so v^2 2^60 = M^2 2^(2 e2 + 60).
+// v = M 2^(E - 150) with the 24-bit mantissa M, so v^2 2^60 = M^2 2^(2E - 240).
+// Below |v| = 2^-30 (E <= 96, zeros and subnormals included) the result is 0,
+// since M^2 < 2^48; above, the shift lies in [-46, 14].
 __device__ __forceinline__ unsigned long long sq60(float v) {
     const uint32_t u = __float_as_uint(v) & 0x7FFFFFFFu;
     const int E = (int)(u >> 23);
-    const unsigned long long M = E ? ((u & 0x7FFFFFu) | 0x800000u) : (u & 0x7FFFFFu);
-    const int sh = 2 * (E ? E - 150 : -149) + 60;
+    const unsigned long long M = (u & 0x7FFFFFu) | 0x800000u;
     const unsigned long long m2 = M * M;
-    if (sh >= 0) return sh > 14 ? (1ull << 62) : (m2 << sh);
-    return sh <= -64 ? 0ull : (m2 >> -sh);
+    const int sh = 2 * E - 240;
+    if (E <= 96) return 0ull;
+    if (E > 127) return 1ull << 62;
+    return sh >= 0 ? (m2 << sh) : (m2 >> -sh);
 }
 
 __device__ __forceinline__ unsigned long long sq60(double v) {
