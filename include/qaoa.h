@@ -245,7 +245,8 @@ qaoa_status qaoa_state_from_host(qaoa_ctx ctx, int n, int fp64, const void *amps
  * Outputs (host, each may be NULL): idx[s] = x_s; cost_out[s] = F(x_s) from
  * the cost table (needs `cost`, of the same n); *mean_cost = mean of F over
  * the shots (needs `cost`), summed exactly in integers.  QAOA_ERR_RANGE if
- * the state's total probability is outside [0.25, 4].  Device scratch: about
+ * the state's total probability is outside [0.25, 4] or a component has
+ * magnitude >= 2 or is infinite or NaN.  Device scratch: about
  * 2^n / 32 bytes plus 8 bytes per shot for each output kept. */
 qaoa_status qaoa_sample(qaoa_ctx ctx, qaoa_cost cost, qaoa_state state, int64_t shots, uint64_t seed,
                         uint64_t stream, const uint64_t *rand, uint64_t *idx, double *cost_out,

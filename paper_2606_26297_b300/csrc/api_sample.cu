@@ -62,6 +62,8 @@ qaoa_status measure(qaoa_ctx c, const std::vector<ItemState> &st, bool fp64, con
     std::vector<size_t> off(K + 1, 0);
     int max_n = 1;
     for (size_t i = 0; i < K; ++i) {
+        if (reinterpret_cast<uintptr_t>(st[i].amps) % 16)  // the weights pass reads 16-byte vectors
+            return fail(QAOA_ERR_INVALID_ARG, "measure: state not 16-byte aligned");
         off[i + 1] = off[i] + (size_t)(sample_chunk_count(st[i].n) + sample_super_count(st[i].n) + 1);
         max_n = std::max(max_n, st[i].n);
     }
@@ -99,14 +101,19 @@ qaoa_status measure(qaoa_ctx c, const std::vector<ItemState> &st, bool fp64, con
     {
         double wb = 0;
         for (size_t i = 0; i < K; ++i) wb += std::ldexp(fp64 ? 16.0 : 8.0, st[i].n);
+        QAOA_TRY(c->status.ensure(16, &c->held, c->opt.memory_budget));
+        CUDA_TRY(cudaMemsetAsync(c->status.p, 0, 4, c->stream));
         SampleProf prof(c, 6, wb);
-        CUDA_TRY(launch_sample_weights(dev, (int)K, max_n, fp64, c->stream));
+        CUDA_TRY(launch_sample_weights(dev, (int)K, max_n, fp64, c->status.as<unsigned int>(), c->stream));
     }
     c->launches_total += 2;
     std::vector<unsigned long long> Q(K);
+    unsigned int ws = 0;
     for (size_t i = 0; i < K; ++i)
         CUDA_TRY(cudaMemcpyAsync(&Q[i], items[i].total, 8, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(&ws, c->status.p, 4, cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (ws & 4u) return fail(QAOA_ERR_RANGE, "a state holds a component of magnitude >= 2, infinite or NaN");
     for (size_t i = 0; i < K; ++i)
         if (Q[i] < (1ull << 58) || Q[i] > (1ull << 62))
             return fail(QAOA_ERR_RANGE, "state %zu: total probability %.6g outside [0.25, 4]", i,

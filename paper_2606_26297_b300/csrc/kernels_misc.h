@@ -87,8 +87,10 @@ struct SampleItem {
 };
 long long sample_chunk_count(int n);
 long long sample_super_count(int n);
-// weights + per-item scan; then the caller checks Q and launches the shots
-cudaError_t launch_sample_weights(const SampleItem *items_dev, int count, int max_n, bool fp64, cudaStream_t st);
+// weights + per-item scan; then the caller checks Q and the status (bit 4: a
+// component with |v| >= 2, infinite or NaN) and launches the shots
+cudaError_t launch_sample_weights(const SampleItem *items_dev, int count, int max_n, bool fp64,
+                                  unsigned int *status, cudaStream_t st);
 cudaError_t launch_sample_shots(const SampleItem *items_dev, int count, long long max_shots, bool fp64,
                                 unsigned int *status, cudaStream_t st);
 

@@ -41,19 +41,33 @@ __host__ __device__ inline Geo geo_of(int n) {
     return g;
 }
 
-// floor(v^2 2^60) for |v| < 2 (larger or non-finite values saturate at 2^62):
-// v = M 2^(E - 150) with the 24-bit mantissa M, so v^2 2^60 = M^2 2^(2E - 240).
-// Below |v| = 2^-30 (E <= 96, zeros and subnormals included) the result is 0,
-// since M^2 < 2^48; above, the shift lies in [-46, 14].
+// Logical right shift of a 32-bit word; shifts of 32 or more give 0.
+__device__ __forceinline__ uint32_t shr_clamped(uint32_t x, uint32_t n) {
+    uint32_t r;
+    asm("shr.b32 %0, %1, %2;" : "=r"(r) : "r"(x), "r"(n));
+    return r;
+}
+
+// floor(v^2 2^60) for |v| < 2.  With the exponent field E and the 24-bit
+// mantissa M (leading 1 included), v = M 2^(E - 150); m8 = M 2^8 < 2^32 is
+// the value's bits shifted left by 8 with the top bit set (the shift drops the
+// sign and all but the lowest exponent bit, which the top bit overwrites), so
+// v^2 2^60 = m8^2 / 2^s with s = 256 - 2E in [2, 256] for E <= 127: one
+// 32 x 32 -> 64-bit square and one right shift on its 32-bit halves, where a
+// shift of 32 or more clears a word (so |v| < 2^-30, E <= 96, s >= 64, zeros
+// and subnormals included, gives 0).  |v| >= 2 and non-finite values
+// (E >= 128) lie outside the domain and give an unspecified value: the
+// weights pass reports them through top_word instead.
 __device__ __forceinline__ unsigned long long sq60(float v) {
-    const uint32_t u = __float_as_uint(v) & 0x7FFFFFFFu;
-    const int E = (int)(u >> 23);
-    const unsigned long long M = (u & 0x7FFFFFu) | 0x800000u;
-    const unsigned long long m2 = M * M;
-    const int sh = 2 * E - 240;
-    if (E <= 96) return 0ull;
-    if (E > 127) return 1ull << 62;
-    return sh >= 0 ? (m2 << sh) : (m2 >> -sh);
+    const uint32_t b = __float_as_uint(v);
+    const uint32_t m8 = (b << 8) | 0x80000000u;
+    const uint32_t E = (b << 1) >> 24;
+    const uint32_t s = 256u - 2u * E;
+    const unsigned long long w = (unsigned long long)m8 * m8;
+    const uint32_t lo = (uint32_t)w, hi = (uint32_t)(w >> 32);
+    const uint32_t rlo = s >= 32u ? shr_clamped(hi, s - 32u) : __funnelshift_r(lo, hi, s);
+    const uint32_t rhi = shr_clamped(hi, s);
+    return ((unsigned long long)rhi << 32) | rlo;
 }
 
 __device__ __forceinline__ unsigned long long sq60(double v) {
@@ -74,6 +88,13 @@ __device__ __forceinline__ unsigned long long weight_of(const E &a) {
     return sq60(a.x) + sq60(a.y);
 }
 
+// The 32-bit word that holds the top exponent bit of a component, at bit 30:
+// it is set exactly when |v| >= 2, v infinite or NaN (float: the value's bits;
+// double: their high word).
+__device__ __forceinline__ uint32_t top_word(float v) { return __float_as_uint(v); }
+__device__ __forceinline__ uint32_t top_word(double v) { return (uint32_t)(__double_as_longlong(v) >> 32); }
+constexpr uint32_t TOP_EXPONENT_BIT = 0x40000000u;
+
 __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
 #pragma unroll
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -89,8 +110,44 @@ __device__ __forceinline__ unsigned long long warp_incl_scan(unsigned long long 
     return v;
 }
 
+// This lane's part of the weight sum of one chunk of ch amplitudes (a warp
+// covers the chunk); ORs the components' top words into *top.
 template <typename E>
-__global__ void __launch_bounds__(SAMPLE_THREADS) sample_weights_kernel(const SampleItem *__restrict__ items) {
+__device__ __forceinline__ unsigned long long lane_chunk_sum(const E *p, int ch, int lane, uint32_t *top) {
+    unsigned long long s = 0;
+    uint32_t t = 0;
+    if constexpr (sizeof(E) == 8) {
+        if (ch == 256) {  // complex64: two amplitudes per 16-byte load
+            const float4 *p4 = reinterpret_cast<const float4 *>(p);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float4 v = p4[lane + 32 * j];
+                s += (sq60(v.x) + sq60(v.y)) + (sq60(v.z) + sq60(v.w));
+                t |= (top_word(v.x) | top_word(v.y)) | (top_word(v.z) | top_word(v.w));
+            }
+            *top |= t;
+            return s;
+        }
+    }
+    if (ch >= 32) {
+#pragma unroll 8
+        for (int j = 0; j < ch / 32; ++j) {
+            const E a = p[lane + 32 * j];
+            s += weight_of(a);
+            t |= top_word(a.x) | top_word(a.y);
+        }
+    } else if (lane < ch) {
+        const E a = p[lane];
+        s = weight_of(a);
+        t = top_word(a.x) | top_word(a.y);
+    }
+    *top |= t;
+    return s;
+}
+
+template <typename E>
+__global__ void __launch_bounds__(SAMPLE_THREADS) sample_weights_kernel(const SampleItem *__restrict__ items,
+                                                                        unsigned int *status) {
     const SampleItem &it = items[blockIdx.y];
     const Geo g = geo_of(it.n);
     if ((long long)blockIdx.x >= g.nsuper) return;
@@ -98,18 +155,13 @@ __global__ void __launch_bounds__(SAMPLE_THREADS) sample_weights_kernel(const Sa
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const E *amps = static_cast<const E *>(it.amps);
     const unsigned long long sbase = (unsigned long long)blockIdx.x * g.cps * g.ch;
+    uint32_t top = 0;
     for (int c = warp; c < g.cps; c += SAMPLE_THREADS / 32) {
         const E *p = amps + sbase + (unsigned long long)c * g.ch;
-        unsigned long long s = 0;
-        if (g.ch >= 32) {
-#pragma unroll 8
-            for (int j = 0; j < g.ch / 32; ++j) s += weight_of(p[lane + 32 * j]);
-        } else if (lane < g.ch) {
-            s = weight_of(p[lane]);
-        }
-        s = warp_sum(s);
+        const unsigned long long s = warp_sum(lane_chunk_sum(p, g.ch, lane, &top));
         if (lane == 0) cs[c] = s;
     }
+    if (top & TOP_EXPONENT_BIT) atomicOr(status, 4u);  // a component outside |v| < 2
     __syncthreads();
     if (warp == 0) {
         const unsigned long long a = 2 * lane < g.cps ? cs[2 * lane] : 0ull;
@@ -246,14 +298,15 @@ long long sample_super_count(int n) { return geo_of(n).nsuper; }
 
 constexpr int MAX_GRID_Y = 65535;
 
-cudaError_t launch_sample_weights(const SampleItem *items_dev, int count, int max_n, bool fp64, cudaStream_t st) {
+cudaError_t launch_sample_weights(const SampleItem *items_dev, int count, int max_n, bool fp64,
+                                  unsigned int *status, cudaStream_t st) {
     for (int o = 0; o < count; o += MAX_GRID_Y) {
         const int k = count - o < MAX_GRID_Y ? count - o : MAX_GRID_Y;
         const dim3 grid((unsigned)sample_super_count(max_n), (unsigned)k);
         if (fp64)
-            sample_weights_kernel<double2><<<grid, SAMPLE_THREADS, 0, st>>>(items_dev + o);
+            sample_weights_kernel<double2><<<grid, SAMPLE_THREADS, 0, st>>>(items_dev + o, status);
         else
-            sample_weights_kernel<float2><<<grid, SAMPLE_THREADS, 0, st>>>(items_dev + o);
+            sample_weights_kernel<float2><<<grid, SAMPLE_THREADS, 0, st>>>(items_dev + o, status);
         cudaError_t e = cudaGetLastError();
         if (e) return e;
     }

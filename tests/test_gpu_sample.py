@@ -114,6 +114,50 @@ def test_sample_sparse_and_empty_regions(q, ctx):
     q.qaoa_state_destroy(st)
 
 
+def _exponent_sweep_state(n, seed):
+    """complex64 components of every binary exponent from 2^-8 to 2^-51, with
+    zeros, subnormals, the 2^-30 edge of the weights (the largest float below
+    it has weight 0, 2^-30 itself weight 1) and a few large components that
+    carry most of the probability."""
+    rng = np.random.default_rng(seed)
+    N = 1 << n
+    v = (rng.choice([-1.0, 1.0], 2 * N) * (1.0 + rng.random(2 * N)) * 2.0 ** -rng.integers(8, 52, 2 * N))
+    v = v.astype(np.float32)
+    edge = np.float32(2.0 ** -30)
+    special = [0.0, -0.0, 1e-40, -1e-45, edge, np.nextafter(edge, np.float32(0)), -edge, 2.0 ** -16, 1.5 * 2.0 ** -16,
+               2.0 ** -15, -(2.0 ** -8), 2.0 ** -7, 0.75, -0.5, 1.0, 0.3]
+    pos = rng.choice(2 * N, len(special), replace=False)
+    v[pos] = np.array(special, dtype=np.float32)
+    return (v[0::2] + 1j * v[1::2]).astype(np.complex64)
+
+
+@pytest.mark.parametrize("n", [8, 12])
+def test_sample_weight_boundaries(q, ctx, n):
+    """Shots aimed at both sides of every prefix-sum boundary: for each x of
+    non-zero weight, caller randoms with T = q_0 + ... + q_x - 1 and with
+    T = q_0 + ... + q_x (R = ceil(T 2^64 / Q)).  Any weight that differs from
+    the exact floor(v^2 2^60), at any exponent, moves a boundary and changes
+    one of these indices."""
+    amps = _exponent_sweep_state(n, 7000 + n)
+    w = osm.weights(amps)
+    cum = np.cumsum(w, dtype=np.uint64)
+    Q = int(cum[-1])
+    R, want = [], []
+    for x in np.flatnonzero(w):
+        for T in (int(cum[x]) - 1, int(cum[x])):
+            if T >= Q:
+                continue
+            r = -(-(T << 64) // Q)
+            assert r < 1 << 64 and (r * Q) >> 64 == T
+            R.append(r)
+    R = np.array(R, dtype=np.uint64)
+    st = q.qaoa_state_from_host(ctx, amps)
+    idx, _, _ = q.qaoa_sample(ctx, None, st, len(R), rand=R)
+    ref = osm.sample(amps, [int(r) for r in R])
+    assert np.array_equal(idx, ref)
+    q.qaoa_state_destroy(st)
+
+
 def test_sample_complex128_state(q, ctx):
     """A complex128 state (n <= 12): weights from FP64 amplitudes, both
     products rounded, match the oracle bit for bit."""
@@ -126,11 +170,28 @@ def test_sample_complex128_state(q, ctx):
 
 
 def test_sample_rejects_bad_input(q, ctx):
-    """Zero states (total probability outside [0.25, 4]), shots < 1, costs
+    """Zero states (total probability outside [0.25, 4]), states holding a
+    component of magnitude >= 2, infinite or NaN (in complex64 on both load
+    paths and in complex128, even when the rest sums to 1), shots < 1, costs
     without a cost handle, and a cost of another n are refused."""
     st = q.qaoa_state_from_host(ctx, np.zeros(1 << 6, dtype=np.complex64))
     with pytest.raises(q.QaoaError):
         q.qaoa_sample(ctx, None, st, 10)
+    q.qaoa_state_destroy(st)
+    for n, dt in ((6, np.complex64), (10, np.complex64), (6, np.complex128)):
+        for bad in (2.0, -3.5, np.inf, np.nan):
+            a = np.zeros(1 << n, dtype=dt)
+            a[1] = 1.0
+            a[(1 << n) - 3] = complex(0.0, bad)
+            st = q.qaoa_state_from_host(ctx, a)
+            with pytest.raises(q.QaoaError):
+                q.qaoa_sample(ctx, None, st, 10)
+            q.qaoa_state_destroy(st)
+    a = np.zeros(1 << 10, dtype=np.complex64)
+    a[5] = np.float32(np.nextafter(np.float32(2), np.float32(0)))  # largest float below 2: in the domain
+    st = q.qaoa_state_from_host(ctx, a)
+    idx, _, _ = q.qaoa_sample(ctx, None, st, 10)
+    assert set(idx.tolist()) == {5}
     q.qaoa_state_destroy(st)
     st = q.qaoa_state_from_host(ctx, inst.random_state(6, 1))
     with pytest.raises(q.QaoaError):
