@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(PASS_THREADS, 1)
     int32_t *cstage = reinterpret_cast<int32_t *>(smraw + 65536);      // table block, 32 KB
     float2 *xbuf = reinterpret_cast<float2 *>(smraw + 65536 + 32768);  // transposes, 64 KB
     __shared__ __align__(8) unsigned long long mbar, mbarc;
-    __shared__ double red[PASS_THREADS / 32][NSLOT];
+    __shared__ float2 red[PASS_THREADS / 32][NSLOT];
     __shared__ unsigned long long tk_list[8 * 16], tk_scr[8 * 32];
     const uint32_t l = threadIdx.x & 31u, w = threadIdx.x >> 5;
     const int nbits = a.n - BLOCK_BITS;
@@ -282,8 +282,8 @@ __global__ void __launch_bounds__(PASS_THREADS, 1)
             store_lam<T, 0>(P, Q, a.lam + ((size_t)un.item << a.n) + base, l, w, a.loA, a.loB);
         else
             store_pq<T, 0>(P, Q, a.pl + ((size_t)un.item << a.n) + base, l, w, a.loA, a.loB);
-        double vals[NSLOT] = {(double)e0, (double)e1, (double)x1, (double)x0, 0.0, 0.0, 0.0, 0.0};
-        block_sum_write(vals, red, a.partials, u);
+        const float vals[4] = {e0, e1, x1, x0};
+        block_sum_write_pairs<4>(vals, red, a.partials, u);
         __syncthreads();
     }
     // one top-K list per warp: topk_keys[(CTA * 8 + warp) * K ..]
@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(PASS_THREADS, 1)
     int32_t *cstage = reinterpret_cast<int32_t *>(smraw + 131072);      // table block, 32 KB
     float2 *xbuf = reinterpret_cast<float2 *>(smraw + 131072 + 32768);  // transposes, 64 KB
     __shared__ __align__(8) unsigned long long mbar, mbarc;
-    __shared__ double red[PASS_THREADS / 32][NSLOT];
+    __shared__ float2 red[PASS_THREADS / 32][NSLOT];
     const uint32_t l = threadIdx.x & 31u, w = threadIdx.x >> 5;
     const int nbits = a.n - BLOCK_BITS;
     constexpr bool pre = PRE, post = POST;
@@ -389,10 +389,14 @@ __global__ void __launch_bounds__(PASS_THREADS, 1)
             if (SPLIT) store_lam<T, 1>(P, Q, a.lam + ((size_t)un.item << a.n) + base, l, w, a.loA, a.loB);
             else store_pq<T, 1>(P, Q, dst, l, w, a.loA, a.loB);
         }
-        double vals[NSLOT];
+        if constexpr (FULL || !(PRE && COST && POST)) {
+            block_sum_write_pairs<5>(acc, red, a.partials, u);
+        } else {  // the FP64 tree: the pair form spills in these register-bound forms
+            double vals[NSLOT];
 #pragma unroll
-        for (int s = 0; s < NSLOT; ++s) vals[s] = (double)acc[s];
-        block_sum_write(vals, red, a.partials, u);
+            for (int s = 0; s < NSLOT; ++s) vals[s] = (double)acc[s];
+            block_sum_write(vals, reinterpret_cast<double(*)[NSLOT]>(red), a.partials, u);
+        }
         __syncthreads();
     }
 }
@@ -464,7 +468,7 @@ __global__ void __launch_bounds__(PASS_THREADS, 1)
     float2 *pst = reinterpret_cast<float2 *>(smraw + 65536);    // stored psi_in block, 64 KB
     float2 *xbuf = reinterpret_cast<float2 *>(smraw + 131072);  // transposes, 64 KB
     __shared__ __align__(8) unsigned long long mbl, mbp;
-    __shared__ double red[PASS_THREADS / 32][NSLOT];
+    __shared__ float2 red[PASS_THREADS / 32][NSLOT];
     const uint32_t l = threadIdx.x & 31u, w = threadIdx.x >> 5;
     const int nbits = a.n - BLOCK_BITS;
     if (threadIdx.x == 0) {
@@ -509,8 +513,8 @@ __global__ void __launch_bounds__(PASS_THREADS, 1)
             fence_proxy_async();
             issue_block8<T>(u + gridDim.x, a, &mpsi, a.psi_src, pst, &mbp);
         }
-        double vals[NSLOT] = {(double)xy, (double)xx, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-        block_sum_write(vals, red, a.partials, u);
+        const float vals[2] = {xy, xx};
+        block_sum_write_pairs<2>(vals, red, a.partials, u);
         __syncthreads();
     }
 }

@@ -150,6 +150,56 @@ __device__ __forceinline__ float2 cost_phase(int32_t tq, unsigned long long phi,
     return make_float2(c * kmag, -s * kmag);
 }
 
+static_assert(sizeof(float2) == sizeof(double), "a pair slot holds one FP64 slot");
+
+// Sum of x over the warp as an unevaluated pair hi + lo: Knuth's TwoSum at
+// every level of the butterfly keeps each addition's rounding error, so the
+// pair carries the warp sum to about 2^-48 relative without FP64 instructions
+// (the FP64 rate of this GPU is a small fraction of its FP32 rate).  TwoSum's
+// error term is exact whatever the operand order, so every lane ends with the
+// same pair.
+__device__ __forceinline__ float2 warp_sum_pair(float x) {
+    float hi = x, lo = 0.f;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+        const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+        const float s = __fadd_rn(hi, h2);
+        const float bv = __fsub_rn(s, hi);
+        const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bv)), __fsub_rn(h2, bv));
+        hi = s;
+        lo = __fadd_rn(__fadd_rn(lo, l2), e);
+    }
+    return make_float2(hi, lo);
+}
+
+// Deterministic block sum of the first K of NSLOT FP32 values (the other
+// slots are written as 0): warp sums as FP32 pairs (fixed shuffle tree), then
+// the warps' pairs in FP64 in index order.  red: shared [8][NSLOT] pairs.
+// Writes out[blk*NSLOT+s].
+template <int K>
+__device__ __forceinline__ void block_sum_write_pairs(const float *val, float2 (*red)[NSLOT], double *out,
+                                                      uint32_t blk) {
+    const int l = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int s = 0; s < K; ++s) {
+        const float2 p = warp_sum_pair(val[s]);
+        if (l == 0) red[w][s] = p;
+    }
+    __syncthreads();
+    if (threadIdx.x < NSLOT) {
+        double t = 0.0;
+        if ((int)threadIdx.x < K) {
+#pragma unroll
+            for (int k = 0; k < PASS_THREADS / 32; ++k) {
+                const float2 p = red[k][threadIdx.x];
+                t += (double)p.x + (double)p.y;
+            }
+        }
+        out[(size_t)blk * NSLOT + threadIdx.x] = t;
+    }
+}
+
 // Deterministic block sum of NSLOT FP64 values (fixed shuffle tree, then warps
 // in index order).  red: shared [8][NSLOT].  Writes out[blockIdx.x*NSLOT+s].
 __device__ __forceinline__ void block_sum_write(double (&val)[NSLOT], double (*red)[NSLOT], double *out,
