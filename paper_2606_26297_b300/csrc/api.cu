@@ -178,6 +178,7 @@ qaoa_status ensure_plan_bufs(qaoa_ctx c, PlanBufs &b, const PlanRun &r) {
         b.lam.release(h);
     }
     QAOA_TRY(b.partials.ensure(B * nb * NSLOT * sizeof(double), h, bud));
+    QAOA_TRY(b.partials2.ensure(std::max<size_t>((size_t)B * reduce_chunk_count(nb) * NSLOT * sizeof(double), 64), h, bud));
     QAOA_TRY(b.sums.ensure((size_t)std::max(r.rows, 1) * B * NSLOT * sizeof(double), h, bud));
     QAOA_TRY(b.scal.ensure(r.plan.size() * B * sizeof(PassScal), h, bud));
     QAOA_TRY(b.slot_scale.ensure(r.plan.size() * B * NSLOT * sizeof(double), h, bud));
@@ -265,9 +266,11 @@ qaoa_status enqueue_plan(qaoa_ctx c, PlanBufs &b, const PlanRun &r, const int32_
             c->launches_total += 1;
         }
         if (pl.sum_index >= 0) {
-            CUDA_TRY(launch_reduce_partials(a.partials, r.nitems, nb,
-                                            b.sums.as<double>() + (size_t)pl.sum_index * r.nitems * NSLOT, c->stream));
-            c->launches_total += 1;
+            int nl = 0;
+            CUDA_TRY(launch_reduce_partials_chunked(a.partials, r.nitems, nb, b.partials2.as<double>(),
+                                                    b.sums.as<double>() + (size_t)pl.sum_index * r.nitems * NSLOT,
+                                                    &nl, c->stream));
+            c->launches_total += nl;
         }
     }
     return QAOA_OK;

@@ -80,7 +80,7 @@ struct ProfRec {
 
 // Device buffers of one plan execution (one n, a batch of items).
 struct PlanBufs {
-    DevBuf psi, pl, states, lam, partials, sums, scal, slot_scale, plan, gamma, beta, item_s, item_kc, item_table, tables,
+    DevBuf psi, pl, states, lam, partials, partials2, sums, scal, slot_scale, plan, gamma, beta, item_s, item_kc, item_table, tables,
         out_E, out_dg, out_db, topk_a, topk_b, adam_m, adam_v, adam_step, history, small_items, small_out;
 };
 

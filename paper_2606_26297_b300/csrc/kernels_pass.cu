@@ -81,6 +81,26 @@ __global__ void reduce_partials_kernel(const double *__restrict__ in, int nblock
     if (threadIdx.x == 0) out[(size_t)item * NSLOT + s] = sh[0];
 }
 
+// First stage of the per-pass partial sums when an item has many units: CTA
+// (c, item) sums units [256 c, 256 c + 256) of the item for every slot; warp s
+// takes slot s, its lanes the units lane, lane + 32, ... in order, then a
+// fixed shuffle tree.  out[(item * nchunks + c) * NSLOT + s].  The chunking is
+// fixed, so the sums do not depend on the GPU's size.
+constexpr int REDUCE_CHUNK = 256;
+static_assert(NSLOT * 32 == 256, "one warp per slot");
+__global__ void __launch_bounds__(256) reduce_chunks_kernel(const double *__restrict__ in, int nblocks, int nchunks,
+                                                            double *__restrict__ out) {
+    const int item = blockIdx.y, c = blockIdx.x;
+    const int l = threadIdx.x & 31, s = threadIdx.x >> 5;
+    const double *src = in + ((size_t)item * nblocks + (size_t)c * REDUCE_CHUNK) * NSLOT + s;
+    const int rows = min(REDUCE_CHUNK, nblocks - c * REDUCE_CHUNK);
+    double t = 0.0;
+    for (int r = l; r < rows; r += 32) t += src[(size_t)r * NSLOT];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (l == 0) out[((size_t)item * nchunks + c) * NSLOT + s] = t;
+}
+
 // K-way merge of sorted (descending) key lists of length K.  CTA c merges
 // lists [c*LPC, (c+1)*LPC) and writes its K best keys to out[c*K ...].
 __global__ void topk_merge_kernel(const unsigned long long *__restrict__ in, int nlists, int K,
@@ -169,6 +189,25 @@ cudaError_t launch_fwd_pass(int type, const PassArgs &a, cudaStream_t st) {
 cudaError_t launch_reduce_partials(const double *partials, int nitems, int nblocks, double *out, cudaStream_t st) {
     reduce_partials_kernel<<<nitems * NSLOT, 256, 0, st>>>(partials, nblocks, out);
     return cudaGetLastError();
+}
+
+int reduce_chunk_count(int nblocks) {
+    const int nchunks = (nblocks + REDUCE_CHUNK - 1) / REDUCE_CHUNK;
+    return nchunks >= 64 ? nchunks : 0;  // from 2^14 units (n >= 27): below, the one-stage sum is as fast
+}
+
+cudaError_t launch_reduce_partials_chunked(const double *partials, int nitems, int nblocks, double *scratch,
+                                           double *out, int *launches, cudaStream_t st) {
+    const int nchunks = reduce_chunk_count(nblocks);
+    if (nchunks == 0 || nitems > 65535 || !scratch) {
+        *launches = 1;
+        return launch_reduce_partials(partials, nitems, nblocks, out, st);
+    }
+    reduce_chunks_kernel<<<dim3((unsigned)nchunks, (unsigned)nitems), 256, 0, st>>>(partials, nblocks, nchunks, scratch);
+    cudaError_t e = cudaGetLastError();
+    if (e) return e;
+    *launches = 2;
+    return launch_reduce_partials(scratch, nitems, nchunks, out, st);
 }
 
 // Repeatedly merge until one list remains.  `in` holds nlists lists of K keys;

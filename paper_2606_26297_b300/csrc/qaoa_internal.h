@@ -105,6 +105,12 @@ cudaError_t launch_wait_probe(unsigned int *status, cudaStream_t st);
 cudaError_t launch_fwd_cost_tma(int type, const PassArgs &a, int grid, unsigned int *status, cudaStream_t st);
 cudaError_t launch_reduce_partials(const double *partials, int nitems, int nblocks, double *out,
                                    cudaStream_t st);
+// Two stages when an item has at least 64 chunks of 256 units (scratch holds
+// nitems * reduce_chunk_count(nblocks) * NSLOT doubles), else the one-stage
+// sum; *launches = kernels launched.
+int reduce_chunk_count(int nblocks);
+cudaError_t launch_reduce_partials_chunked(const double *partials, int nitems, int nblocks, double *scratch,
+                                           double *out, int *launches, cudaStream_t st);
 cudaError_t launch_topk_merge(const unsigned long long *in, int nlists, int k,
                               unsigned long long *out, int *nout, int *nlaunch, cudaStream_t st);
 
