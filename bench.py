@@ -339,7 +339,7 @@ def run_workload(args):
       fd       adjoint gradient vs central finite differences from forward-only
                evaluations (one parameter set: MaxCut n=26 p=4; a batch: 256
                sets on the n=20 integer QUBO, p=4), time and error vs adjoint;
-      batch20  256 multi-start sets, n=20, p=4: batched fwd+adjoint, and Adam
+      batch20  256 (`--sets`) multi-start sets, n=20, p=4: batched fwd+adjoint, and Adam
                steps replayed from a CUDA graph;
       ragged   64 integer QUBOs with n in [10, 22], p=4, one request;
       uc32     unit-commitment QUBO n=32, p=6: `--iters` Adam steps on the
@@ -419,7 +419,7 @@ def run_workload(args):
                                 "fd_rel_err_vs_adjoint": err}})
         q.qaoa_cost_destroy(cost)
     elif args.workload == "batch20":
-        Q, G0, B0 = inst.workload_batch20()
+        Q, G0, B0 = inst.workload_batch20(batch=args.sets)
         cost = q.qaoa_build_cost(ctx, Q.H, Q.f, Q.c0, "i32")
         nb, p = G0.shape
         q.qaoa_grad_batch(ctx, [cost], G0, B0)
@@ -570,6 +570,7 @@ def main():
                     help="a secondary measurement instead of the headline step")
     ap.add_argument("--iters", type=int, default=200, help="optimiser steps for --workload batch20/uc32/spsa/solve")
     ap.add_argument("--shots", type=int, default=1 << 20, help="shots per request for --workload sample")
+    ap.add_argument("--sets", type=int, default=256, help="angle sets for --workload batch20")
     args = ap.parse_args()
     if args.workload:
         return run_workload(args)
