@@ -63,16 +63,30 @@ __device__ __forceinline__ void load_cost(int32_t (&c)[32], const int32_t *__res
     }
 }
 
+// Barrier of a shared-memory transpose.  Type 0 keeps the warp bits (local
+// bits 10..12) in both arrangements, and the swizzle and the flip touch bits
+// 0..9 only, so each warp writes and reads only its own 1024 slots: a warp
+// barrier suffices (the kernels that hand the buffer to a TMA copy afterwards
+// synchronise the block themselves).  Type 1 moves amplitudes between warps.
+template <int T>
+__device__ __forceinline__ void xpose_barrier() {
+    if constexpr (T == 0) {
+        __syncwarp();
+    } else {
+        __syncthreads();
+    }
+}
+
 // Transpose one state from arrangement A to arrangement B through shared
 // memory.  fm: local-bit mask of a bit flip X applied on the way (the
 // amplitude of local index e lands at e ^ fm).
 template <int T, int A, int B>
 __device__ __forceinline__ void transpose1(float2 (&v)[32], float2 *sm, uint32_t l, uint32_t w, uint32_t fm) {
-    __syncthreads();
+    xpose_barrier<T>();
     const uint32_t ta = swz<T>(local_idx<T, A>(l, 0u, w) ^ fm);
 #pragma unroll
     for (int m = 0; m < 32; ++m) sm[ta ^ swz<T>(local_idx<T, A>(0u, (uint32_t)m, 0u))] = v[m];
-    __syncthreads();
+    xpose_barrier<T>();
     const uint32_t tb = swz<T>(local_idx<T, B>(l, 0u, w));
 #pragma unroll
     for (int m = 0; m < 32; ++m) v[m] = sm[tb ^ swz<T>(local_idx<T, B>(0u, (uint32_t)m, 0u))];
