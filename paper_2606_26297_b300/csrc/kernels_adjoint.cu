@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(PASS_THREADS, 1)
             store_pq<T, 0>(P, Q, a.pl + ((size_t)un.item << a.n) + base, l, w, a.loA, a.loB);
         const float vals[4] = {e0, e1, x1, x0};
         block_sum_write_pairs<4>(vals, red, a.partials, u);
-        __syncthreads();
+        // no barrier here: the next unit passes one (after its stage read) before it writes red
     }
     // one top-K list per warp: topk_keys[(CTA * 8 + warp) * K ..]
     if (TOPK && (int)l < a.ktop)
@@ -397,7 +397,7 @@ __global__ void __launch_bounds__(PASS_THREADS, 1)
             for (int s = 0; s < NSLOT; ++s) vals[s] = (double)acc[s];
             block_sum_write(vals, reinterpret_cast<double(*)[NSLOT]>(red), a.partials, u);
         }
-        __syncthreads();
+        // no barrier here: the next unit passes one (after its stage read) before it writes red
     }
 }
 
@@ -515,7 +515,7 @@ __global__ void __launch_bounds__(PASS_THREADS, 1)
         }
         const float vals[2] = {xy, xx};
         block_sum_write_pairs<2>(vals, red, a.partials, u);
-        __syncthreads();
+        // no barrier here: the next unit passes one (after its stage read) before it writes red
     }
 }
 
