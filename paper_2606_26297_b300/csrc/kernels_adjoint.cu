@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(PASS_THREADS, 1)
             issue_amps<T, false>(u + gridDim.x, a, &mpsi, stage, &mbar);
         }
         round_mix<T, 0>(v, sc.pre_t, mask);
-        transpose1<T, 0, 1>(v, xbuf, l, w, fm);
+        transpose1<T, 0, 1, false>(v, xbuf, l, w, fm);  // after the stage-read barrier
         round_mix<T, 1>(v, sc.pre_t, mask);
         int32_t c[32];
         if (!stage_ready(&mbarc, parc, status)) return;
@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(PASS_THREADS, 1)
         }
         const float x1 = xterm_form<T, 1, FULL && T == 0>(P, Q, mask);
         round_mix_pq<T, 1>(P, Q, -sc.pre_t, mask);
-        transpose1<T, 1, 0>(P, xbuf, l, w, fm);
+        transpose1<T, 1, 0, false>(P, xbuf, l, w, fm);  // after the table barrier
         transpose1<T, 1, 0>(Q, xbuf, l, w, fm);
         const float x0 = xterm_form<T, 0, FULL && T == 0>(P, Q, mask);
         round_mix_pq<T, 0>(P, Q, -sc.pre_t, mask);
@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(PASS_THREADS, 1)
         if (post) {
             acc[0] = xterm_form<T, 0, FULL && PRE && COST && POST>(P, Q, mask);
             round_mix_pq<T, 0>(P, Q, -sc.post_t, mask);
-            transpose1<T, 0, 1>(P, xbuf, l, w, fb);
+            transpose1<T, 0, 1, false>(P, xbuf, l, w, fb);  // after the stage-read barrier
             transpose1<T, 0, 1>(Q, xbuf, l, w, fb);
             acc[1] = xterm_form<T, 1, FULL && PRE && COST && POST>(P, Q, mask);
             round_mix_pq<T, 1>(P, Q, -sc.post_t, mask);
@@ -369,7 +369,9 @@ __global__ void __launch_bounds__(PASS_THREADS, 1)
         if (pre) {
             acc[3] = xterm_form<T, 1, FULL && PRE && COST && POST>(P, Q, mask);
             round_mix_pq<T, 1>(P, Q, -sc.pre_t, mask);
-            transpose1<T, 1, 0>(P, xbuf, l, w, fa);
+            // with a cost layer the table barrier, without a post mixer the stage-read
+            // barrier, lies between the last use of xbuf and this transpose
+            transpose1<T, 1, 0, !COST && POST>(P, xbuf, l, w, fa);
             transpose1<T, 1, 0>(Q, xbuf, l, w, fa);
             acc[4] = xterm_form<T, 0, FULL && PRE && COST && POST>(P, Q, mask);
             round_mix_pq<T, 0>(P, Q, -sc.pre_t, mask);
@@ -497,7 +499,7 @@ __global__ void __launch_bounds__(PASS_THREADS, 1)
             issue_block8<T>(u + gridDim.x, a, &mlam, a.lam, lst, &mbl);
         }
         round_mix<T, 0>(v, -sc.post_t, mask);
-        transpose1<T, 0, 1>(v, xbuf, l, w, fb);
+        transpose1<T, 0, 1, false>(v, xbuf, l, w, fb);  // after the stage-read barrier
         round_mix<T, 1>(v, -sc.post_t, mask);
 #pragma unroll
         for (int m = 0; m < 32; ++m) v[m] = cmul(v[m], sc.kend);

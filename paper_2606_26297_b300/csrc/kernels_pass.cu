@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(PASS_THREADS, 2) fwd_pass_kernel(const PassArg
     }
     if (PRE) {
         round_mix<T, 0>(v, sc.pre_t, mask);
-        transpose1<T, 0, 1>(v, sm, l, w, sc.pre_flip ? mask : 0u);
+        transpose1<T, 0, 1, false>(v, sm, l, w, sc.pre_flip ? mask : 0u);  // first use of sm
         round_mix<T, 1>(v, sc.pre_t, mask);
     }
     // arrangement Y
@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(PASS_THREADS, 2) fwd_pass_kernel(const PassArg
     }
     if (POST) {
         round_mix<T, 1>(v, sc.post_t, mask);
-        transpose1<T, 1, 0>(v, sm, l, w, sc.post_flip ? mask : 0u);
+        transpose1<T, 1, 0, PRE>(v, sm, l, w, sc.post_flip ? mask : 0u);  // first use of sm without PRE
         round_mix<T, 0>(v, sc.post_t, mask);
         if (!COST) {
 #pragma unroll

@@ -79,10 +79,13 @@ __device__ __forceinline__ void xpose_barrier() {
 
 // Transpose one state from arrangement A to arrangement B through shared
 // memory.  fm: local-bit mask of a bit flip X applied on the way (the
-// amplitude of local index e lands at e ^ fm).
-template <int T, int A, int B>
+// amplitude of local index e lands at e ^ fm).  LEAD = false drops the
+// barrier that keeps the writes from overtaking the previous transpose's
+// reads, for call sites where a block barrier already lies between the two
+// (or where the buffer has not been used yet).
+template <int T, int A, int B, bool LEAD = true>
 __device__ __forceinline__ void transpose1(float2 (&v)[32], float2 *sm, uint32_t l, uint32_t w, uint32_t fm) {
-    xpose_barrier<T>();
+    if constexpr (LEAD) xpose_barrier<T>();
     const uint32_t ta = swz<T>(local_idx<T, A>(l, 0u, w) ^ fm);
 #pragma unroll
     for (int m = 0; m < 32; ++m) sm[ta ^ swz<T>(local_idx<T, A>(0u, (uint32_t)m, 0u))] = v[m];
