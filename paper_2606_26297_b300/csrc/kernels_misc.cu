@@ -592,7 +592,7 @@ __global__ void fact_check_kernel(FactArgs a) {
 // Contiguous allocation (QPU m owns bits [s_m, s_m + c_m)).  x = u0 + 2^c0 hi
 // with u0 the field of QPU 0.  The part of the split that does not depend on
 // u0 (the local tables of QPUs 1..M-1 and their mutual cross terms) is formed
-// once per hi by fact_hi_kernel; a CTA of the check fixes hi, forms
+// once per hi by fact_hi_kernel; for each row hi the check forms
 // W[q] = sum_{m >= 1} V_{0,m}[u_m][q] (QPU 0 variable q's cross coupling to
 // the other QPUs' set variables) and two subset-sum tables of W over the low
 // and high 8 bits of u0, so that the cross term of x is two table reads.
@@ -616,53 +616,69 @@ __global__ void fact_hi_kernel(FactArgs a, long long *Hhi) {
     Hhi[hi] = h;
 }
 
-__global__ void fact_check_contig_kernel(FactArgs a, const long long *__restrict__ Hhi) {
+// A CTA checks rows hi = blockIdx.x, blockIdx.x + gridDim.x, ... (the bits
+// above QPU 0); per row it forms W[q] and the subset-sum tables of W over the
+// low and high 8 bits of u0, the latter from four 16-entry tables over 4 bits
+// each (one add per entry).  Counts and the error bound are reduced once per
+// CTA; every sum is an exact integer and the bound a maximum, so the result
+// does not depend on the grid.
+__global__ void __launch_bounds__(256) fact_check_contig_kernel(FactArgs a, const long long *__restrict__ Hhi,
+                                                                long long nhi) {
     __shared__ long long wrow[16];
+    __shared__ long long nib[4][16];
     __shared__ long long tlo[256], thi[256];
     __shared__ unsigned long long cnt_sh;
     __shared__ unsigned int err_sh;
     const int c0 = a.c0;
-    const unsigned long long hi = blockIdx.x;  // bits c0..n-1 of x
+    const int klo = c0 < 8 ? c0 : 8;
     if (threadIdx.x == 0) {
         cnt_sh = 0;
         err_sh = 0;
     }
-    if (threadIdx.x < (unsigned)c0) {
-        const int q = threadIdx.x;
-        long long w = 0;
-        for (int m2 = 1; m2 < a.M; ++m2) {
-            const int s2 = a.q_start[m2], c2 = a.q_start[m2 + 1] - s2;
-            const unsigned u2 = (unsigned)((hi >> (s2 - c0)) & ((1u << c2) - 1u));
-            w += a.V[a.V_off[m2] + (size_t)u2 * c0 + q];
-        }
-        wrow[q] = w;
-    }
-    const long long H = Hhi[hi];
-    __syncthreads();
-    const int klo = c0 < 8 ? c0 : 8, khi = c0 - klo;
-    for (int k = threadIdx.x; k < 256; k += blockDim.x) {
-        long long sl = 0, sh = 0;
-        for (int q = 0; q < klo; ++q)
-            if ((k >> q) & 1) sl += wrow[q];
-        for (int q = 0; q < khi; ++q)
-            if ((k >> q) & 1) sh += wrow[klo + q];
-        tlo[k] = sl;
-        thi[k] = sh;
-    }
-    __syncthreads();
     unsigned long long bad = 0;
     float maxerr = 0.f;
-    const int32_t *Tr = a.T + (hi << c0);
-    for (unsigned u0 = threadIdx.x; u0 < (1u << c0); u0 += blockDim.x) {
-        const long long cross = tlo[u0 & ((1u << klo) - 1u)] + thi[u0 >> klo];
-        const long long loc = H + a.Ltab[u0];
-        const int32_t tx = Tr[u0];
-        if ((long long)tx != loc + cross) ++bad;
-        const float2 pf = phase_ll((long long)tx + a.k_c, a.phi, 0ull);
-        const float2 pl = phase_ll(loc + a.k_c, a.phi, 0ull);
-        const float2 pc = phase_ll(cross, a.phi, 0ull);
-        const float2 pp = cmul(pl, pc);
-        maxerr = fmaxf(maxerr, fmaxf(fabsf(pf.x - pp.x), fabsf(pf.y - pp.y)));
+    for (long long hi = blockIdx.x; hi < nhi; hi += gridDim.x) {
+        __syncthreads();  // the previous row's table readers are done
+        if (threadIdx.x < 16) {
+            const int q = threadIdx.x;
+            long long w = 0;
+            if (q < c0)
+                for (int m2 = 1; m2 < a.M; ++m2) {
+                    const int s2 = a.q_start[m2], c2 = a.q_start[m2 + 1] - s2;
+                    const unsigned u2 = (unsigned)((hi >> (s2 - c0)) & ((1u << c2) - 1u));
+                    w += a.V[a.V_off[m2] + (size_t)u2 * c0 + q];
+                }
+            wrow[q] = w;  // 0 beyond QPU 0's c0 variables
+        }
+        __syncthreads();
+        if (threadIdx.x < 64) {
+            const int j = threadIdx.x >> 4, k = threadIdx.x & 15;
+            long long t = 0;
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+                if ((k >> b) & 1) t += wrow[4 * j + b];
+            nib[j][k] = t;
+        }
+        __syncthreads();
+        {
+            const int k = threadIdx.x;  // 256 threads: one entry of each table
+            tlo[k] = nib[0][k & 15] + nib[1][k >> 4];
+            thi[k] = nib[2][k & 15] + nib[3][k >> 4];
+        }
+        __syncthreads();
+        const long long H = Hhi[hi];
+        const int32_t *Tr = a.T + (hi << c0);
+        for (unsigned u0 = threadIdx.x; u0 < (1u << c0); u0 += blockDim.x) {
+            const long long cross = tlo[u0 & ((1u << klo) - 1u)] + thi[u0 >> klo];
+            const long long loc = H + a.Ltab[u0];
+            const int32_t tx = Tr[u0];
+            if ((long long)tx != loc + cross) ++bad;
+            const float2 pf = phase_ll((long long)tx + a.k_c, a.phi, 0ull);
+            const float2 pl = phase_ll(loc + a.k_c, a.phi, 0ull);
+            const float2 pc = phase_ll(cross, a.phi, 0ull);
+            const float2 pp = cmul(pl, pc);
+            maxerr = fmaxf(maxerr, fmaxf(fabsf(pf.x - pp.x), fabsf(pf.y - pp.y)));
+        }
     }
     // warp then CTA reduction of the counts and the error bound
 #pragma unroll
@@ -685,7 +701,8 @@ cudaError_t launch_fact_check(const FactArgs &a, cudaStream_t st) {
     if (a.contiguous) {
         const unsigned long long nhi = 1ull << (a.n - a.c0);
         fact_hi_kernel<<<(unsigned)((nhi + 255) / 256), 256, 0, st>>>(a, a.hhi);
-        fact_check_contig_kernel<<<(unsigned)nhi, 256, 0, st>>>(a, a.hhi);
+        const long long grid = nhi < 2048 ? (long long)nhi : 2048;  // rows per CTA: nhi / 2048 from n - c0 = 11
+        fact_check_contig_kernel<<<(unsigned)grid, 256, 0, st>>>(a, a.hhi, (long long)nhi);
     } else {
         fact_check_kernel<<<148 * 8, 256, 0, st>>>(a);
     }
