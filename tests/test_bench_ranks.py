@@ -68,3 +68,28 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
         gpus, steps, warmup = 2, 1, 0
     assert b.run_reference(A()) == 0
     assert capsys.readouterr().out == ""
+
+
+def test_traffic_record_follows_kernel_sources(tmp_path, monkeypatch):
+    """A DRAM-traffic record is scaled to a launch only while its source hash
+    matches the reverse-pass sources; an edit to any of them, an unknown
+    kernel or a missing record reports no traffic rather than a stale
+    figure.  Checked on a copy of the sources, with a record written for it."""
+    import json
+    b = _bench()
+    d = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    assert 0.9 < d["rev_pass"]["dram_bytes"] / d["rev_pass"]["alg_bytes"] < 1.1
+    root = tmp_path / "repo"
+    src = root / "paper_2606_26297_b300" / "csrc"
+    src.mkdir(parents=True)
+    for name in ("kernels_adjoint.cu", "pass_body.cuh", "pass_common.cuh", "tma_util.cuh", "qaoa_internal.h"):
+        (src / name).write_bytes(open(os.path.join(ROOT, "paper_2606_26297_b300", "csrc", name), "rb").read())
+    monkeypatch.setattr(b, "ROOT", str(root))
+    assert b._traffic("rev_pass", 1000.0) is None  # no record
+    (root / "profiles").mkdir()
+    rec = {"rev_pass": {"dram_bytes": 980.0, "alg_bytes": 1000, "source_hash": b._kernel_source_hash()}}
+    (root / "profiles" / "traffic.json").write_text(json.dumps(rec))
+    assert b._traffic("rev_pass", 5000.0) == pytest.approx(4900.0)
+    assert b._traffic("no_such_kernel", 5000.0) is None
+    (src / "pass_body.cuh").write_bytes((src / "pass_body.cuh").read_bytes() + b"\n")
+    assert b._traffic("rev_pass", 5000.0) is None
