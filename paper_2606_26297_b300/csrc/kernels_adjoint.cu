@@ -575,7 +575,7 @@ __global__ void __launch_bounds__(PASS_THREADS, 2)
 #pragma unroll
         for (int m = 0; m < 32; ++m) v[m] = cmul(v[m], cost_phase(c[m], sc.phi, sc.off, sc.kmag, a.precise_phase));
         round_mix<T, 1>(v, sc.post_t, mask);
-        transpose1<T, 1, 0>(v, pst, l, w, sc.post_flip ? mask : 0u);
+        transpose1<T, 1, 0, false>(v, pst, l, w, sc.post_flip ? mask : 0u);  // after the table barrier
         __syncthreads();
         if (threadIdx.x == 0 && more) {
             fence_proxy_async();
