@@ -151,11 +151,77 @@ def cpu_baseline(n_sample: int, p: int = DEPTH, reps: int = 1):
                       f"scaled to n={N_QUBITS} by n*2^n"}
 
 
+# ---- error against the FP64 oracle, per result ----------------------------------------------
+
+def _tie_groups_match(ti, Po, k):
+    """Top-k indices from the GPU against the oracle's probabilities: every
+    GPU entry must be at least the oracle's k-th probability up to the tie
+    tolerance 1e-6 max P (entries within it are interchangeable)."""
+    kth = np.sort(Po)[::-1][k - 1]
+    return bool(all(Po[int(x)] >= kth - 1e-6 * Po.max() for x in ti))
+
+
+def error_report(q, ctx):
+    """Errors of the GPU path against the FP64 oracle on the benchmark's
+    instance generators, each at the largest size the oracle evaluates in a
+    few seconds on the host cores: |dE|/max|F|, amplitude L2 (complex64 state
+    against the complex128 oracle state), gradient max|dg|/max|g|, top-K as
+    tie groups, brute-force argmin.  Bounds: 1e-5, 1e-5, 1e-4; integer
+    results exact."""
+    import oracle
+    from paper_2606_26297_b300 import instances as inst
+    rep = {}
+
+    def one(label, Q, g, b, dtype, k_top):
+        t0 = time.perf_counter()
+        cost = q.qaoa_build_cost(ctx, Q.H, Q.f, Q.c0, dtype)
+        E, dg, db, ti, tp = q.qaoa_grad(ctx, cost, g, b, k_top=k_top)
+        st = q.qaoa_forward(ctx, cost, g, b)
+        psi = q.qaoa_state_copy_to_host(ctx, st, Q.n).astype(np.complex128)
+        info = q.qaoa_cost_info(cost)
+        q.qaoa_state_destroy(st)
+        q.qaoa_cost_destroy(cost)
+        F = oracle.cost_table(oracle.canonical_of(Q))
+        Eo, dgo, dbo = oracle.grad_adjoint(F, g, b)
+        po = oracle.evolve(F, g, b)
+        go = np.concatenate([dgo, dbo])
+        rep[label] = {
+            "E_abs_err_over_max_abs_F": abs(E - Eo) / float(np.abs(F).max()),
+            "amp_l2_err": float(np.linalg.norm(psi - po)),
+            "grad_rel_err": float(np.max(np.abs(np.concatenate([dg, db]) - go)) / max(np.max(np.abs(go)), 1e-12)),
+            f"top{k_top}_tie_groups_match": _tie_groups_match(ti, oracle.probabilities(po), k_top),
+            "argmin_exact": int(info["argmin"]) == int(oracle.argmin(F)),
+            "oracle_s": round(time.perf_counter() - t0, 2)}
+
+    Q, g, b = inst.workload_small_int()
+    one("dense integer n=12 p=2 (brute-force minimum over 4096 states)", Q, g, b, "i32", 8)
+    Q, g, b = inst.workload_maxcut26()
+    one("MaxCut 3-regular n=26 p=4", Q, g, b, "i32", 10)
+    Q, g, b = inst.workload_dense30(24, DEPTH)
+    one(f"dense N(0,1) n=24 p={DEPTH} (the n=30 workload's generator at n=24)", Q, g, b, "f32", 10)
+    Q, G, B = inst.workload_batch20()
+    cost = q.qaoa_build_cost(ctx, Q.H, Q.f, Q.c0, "i32")
+    sel = np.arange(0, G.shape[0], 32)
+    E, dg, db = q.qaoa_grad_batch(ctx, [cost], G, B)
+    q.qaoa_cost_destroy(cost)
+    F = oracle.cost_table(oracle.canonical_of(Q))
+    eerr = gerr = 0.0
+    for i in sel:
+        Eo, dgo, dbo = oracle.grad_adjoint(F, G[i], B[i])
+        go = np.concatenate([dgo, dbo])
+        eerr = max(eerr, abs(E[i] - Eo) / float(np.abs(F).max()))
+        gerr = max(gerr, float(np.max(np.abs(np.concatenate([dg[i], db[i]]) - go)) / max(np.max(np.abs(go)), 1e-12)))
+    rep[f"multi-start n=20 p=4, {len(sel)} of {G.shape[0]} sets (batched request)"] = {
+        "E_abs_err_over_max_abs_F": eerr, "grad_rel_err": gerr}
+    rep["bounds"] = {"E_abs_err_over_max_abs_F": 1e-5, "amp_l2_err": 1e-5, "grad_rel_err": 1e-4}
+    return rep
+
+
 def run_reference(args):
     rank, ws = _dist()
     if rank != 0:
         return 0
-    n_s = 22
+    n_s = 24
     for _ in range(args.warmup):
         cpu_baseline(n_s, reps=1)
     vals = []
@@ -211,7 +277,7 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     stream = torch.cuda.current_stream()
-    ctx = q.qaoa_ctx_create(local, stream.cuda_stream, profile=True)
+    ctx = q.qaoa_ctx_create(local, stream.cuda_stream, profile=True, reverse_blocks=args.reverse_blocks)
 
     Q, gamma, beta = inst.workload_dense30(args.n, args.p)
     n, p = Q.n, args.p
@@ -254,6 +320,9 @@ def run_gpu(args):
         barrier()
     ms = ev0.elapsed_time(ev1)
     prof = {name: q.qaoa_profile_read(ctx, k) for name, k in q.PROFILE_KINDS.items()}
+    kprof = {name: q.qaoa_profile_read(ctx, k) for name, k in q.PROFILE_KERNEL_KINDS.items()}
+    kprof["table_build"] = prof["cost_build"]
+    kprof["factorisation_check"] = prof["factorisation"]
     launches = q.qaoa_profile_read(ctx, 5)["launches"]
 
     # end-to-end region: host wall clock around the same API calls, inputs from
@@ -271,16 +340,18 @@ def run_gpu(args):
 
     if rank == 0:
         peak, peak_src = _peaks()
-        kinds = {k: v for k, v in prof.items() if v["launches"] > 0}
+        kinds = {k: v for k, v in kprof.items() if v["launches"] > 0}
         dom = max(kinds, key=lambda k: kinds[k]["ms"])
         d = kinds[dom]
         achieved = d["bytes"] / (d["ms"] / 1000.0) / 1e9
         per_launch = d["bytes"] / d["launches"]
         share = {k: round(v["ms"] / sum(x["ms"] for x in kinds.values()), 4) for k, v in kinds.items()}
+        kernel_frac = {k: round(v["bytes"] / (v["ms"] / 1000.0) / 1e9 / peak, 4) for k, v in kinds.items()}
         step_bytes = (prof["fwd_pass"]["bytes"] + prof["rev_pass"]["bytes"]) / args.steps
         min_bytes = 56.0 * p * 2.0 ** n
         clocks = clk.summary()
-        cpu = cpu_baseline(24) if (rank == 0 and not args.no_cpu) else None
+        cpu = cpu_baseline(26) if (rank == 0 and not args.no_cpu) else None
+        errors = error_report(q, ctx) if (rank == 0 and not args.no_errors) else None
         E, dg, db, ti, tp, mism, cls = res
         h2d = H.numel() * 4 + f.numel() * 4 + g_h.numel() * 8 + b_h.numel() * 8
         d2h = 8 + 16 * p + KTOP * 12 + 8 + 8 + 8
@@ -299,6 +370,9 @@ def run_gpu(args):
                          "alg_bytes_per_launch": per_launch,
                          "traffic": _traffic(dom, per_launch)},
             "kernel_time_share": share,
+            # algorithmic bytes / CUDA-event time of every kernel, over the measured HBM peak
+            "kernel_hbm_frac": kernel_frac,
+            "errors": errors,
             # the whole step against HBM: the bytes this design moves per step (every layer
             # pass, forward and reverse) and the method's minimum (20 B forward + 36 B
             # reverse per amplitude per layer), over the device time of the whole step
@@ -338,7 +412,8 @@ def run_workload(args):
     """Secondary measurements, one JSON line each:
       fd       adjoint gradient vs central finite differences from forward-only
                evaluations (one parameter set: MaxCut n=26 p=4; a batch: 256
-               sets on the n=20 integer QUBO, p=4), time and error vs adjoint;
+               sets on the n=20 integer QUBO, p=4), both against the FP64
+               oracle gradient, h swept, speed-up at equal accuracy;
       batch20  256 (`--sets`) multi-start sets, n=20, p=4: batched fwd+adjoint, and Adam
                steps replayed from a CUDA graph;
       ragged   64 integer QUBOs with n in [10, 22], p=4, one request;
@@ -368,56 +443,62 @@ def run_workload(args):
     ctx = q.qaoa_ctx_create(0, stream.cuda_stream)
     res = {"workload": args.workload}
     if args.workload == "fd":
-        Q, g, b = inst.workload_maxcut26()
-        cost = q.qaoa_build_cost(ctx, Q.H, Q.f, Q.c0, "i32")
-        p = len(g)
-        q.qaoa_grad(ctx, cost, g, b)
-        t_adj, (E, dg, db) = _event_time(torch, stream, lambda: q.qaoa_grad(ctx, cost, g, b), args.steps)
-        ref = np.concatenate([dg, db])
-        sc = np.max(np.abs(ref))
-        sweep = {}
-        t_fd = None
-        for h in (1e-2, 3e-3, 1e-3, 3e-4, 1e-4):
+        # Equal accuracy: the adjoint gradient and central differences of
+        # forward-only evaluations (4p per gradient) are both measured against
+        # the FP64 oracle gradient on the same instance; the step h is swept and
+        # the speed-up is reported at the fastest h whose error meets the
+        # gradient bound 1e-4 (relative to max|g|).
+        import oracle
+        BOUND = 1e-4
+        H_SWEEP = (1e-2, 3e-3, 1e-3, 3e-4, 1e-4)
+
+        def fd_sets(G0, B0, h):
             G, B = [], []
-            for k in range(2 * p):
-                for sgn in (1, -1):
-                    gg, bb = np.array(g, float), np.array(b, float)
-                    (gg if k < p else bb)[k % p] += sgn * h
-                    G.append(gg)
-                    B.append(bb)
-            G, B = np.array(G), np.array(B)
-            t, Ef = _event_time(torch, stream, lambda: q.qaoa_grad_batch(ctx, [cost], G, B, grad=False), args.steps)
-            d = (Ef[0::2] - Ef[1::2]) / (2 * h)
-            sweep[f"{h:g}"] = float(np.max(np.abs(d - ref)) / sc)
-            t_fd = t
-        res.update({"single": {"n": 26, "p": p, "adjoint_ms": 1e3 * t_adj, "fd_ms": 1e3 * t_fd,
-                               "fd_evals": 4 * p, "speedup": t_fd / t_adj,
-                               "fd_rel_err_vs_adjoint_by_h": sweep}})
-        q.qaoa_cost_destroy(cost)
-        # batched: 256 sets on n=20
+            for i in range(G0.shape[0]):
+                for k in range(2 * G0.shape[1]):
+                    for sgn in (1, -1):
+                        gg, bb = G0[i].copy(), B0[i].copy()
+                        (gg if k < G0.shape[1] else bb)[k % G0.shape[1]] += sgn * h
+                        G.append(gg)
+                        B.append(bb)
+            return np.array(G), np.array(B)
+
+        def compare(label, Q, G0, B0, sel, reps):
+            cost = q.qaoa_build_cost(ctx, Q.H, Q.f, Q.c0, "i32")
+            nb, p = G0.shape
+            F = oracle.cost_table(oracle.canonical_of(Q))
+            ref = np.array([np.concatenate(oracle.grad_adjoint(F, G0[i], B0[i])[1:]) for i in sel])
+            sc = np.max(np.abs(ref), axis=1)
+            q.qaoa_grad_batch(ctx, [cost], G0, B0)
+            t_adj, (E, dg, db) = _event_time(torch, stream, lambda: q.qaoa_grad_batch(ctx, [cost], G0, B0), reps)
+            adj = np.concatenate([dg, db], axis=1)[sel]
+            adj_err = float(np.max(np.max(np.abs(adj - ref), axis=1) / sc))
+            sweep = {}
+            for h in H_SWEEP:
+                G, B = fd_sets(G0, B0, h)
+                q.qaoa_grad_batch(ctx, [cost], G, B, grad=False)
+                t, Ef = _event_time(torch, stream, lambda: q.qaoa_grad_batch(ctx, [cost], G, B, grad=False), reps)
+                d = ((Ef[0::2] - Ef[1::2]) / (2 * h)).reshape(nb, 2 * p)[sel]
+                sweep[f"{h:g}"] = {"fd_ms": 1e3 * t, "fd_rel_err_vs_oracle": float(np.max(np.max(np.abs(d - ref), axis=1) / sc))}
+            ok = {h: v for h, v in sweep.items() if v["fd_rel_err_vs_oracle"] <= BOUND}
+            best = min(ok, key=lambda h: ok[h]["fd_ms"]) if ok else None
+            most = min(sweep, key=lambda h: sweep[h]["fd_rel_err_vs_oracle"])
+            res[label] = {"n": Q.n, "p": p, "sets": nb, "adjoint_ms": 1e3 * t_adj,
+                          "adjoint_rel_err_vs_oracle": adj_err, "fd_evals": 4 * p * nb, "fd_by_h": sweep,
+                          "bound": BOUND, "oracle_checked_sets": len(sel),
+                          "fd_meets_bound_at_h": best,
+                          "speedup_at_equal_accuracy": (ok[best]["fd_ms"] / (1e3 * t_adj)) if best else None,
+                          # when no h meets the bound, FD never reaches the adjoint's accuracy; the
+                          # speed-up is then quoted at FD's most accurate h, where FD is still less accurate
+                          "fd_most_accurate_h": most,
+                          "fd_most_accurate_rel_err": sweep[most]["fd_rel_err_vs_oracle"],
+                          "speedup_at_fd_most_accurate_h": sweep[most]["fd_ms"] / (1e3 * t_adj)}
+            q.qaoa_cost_destroy(cost)
+
+        Q, g, b = inst.workload_maxcut26()
+        compare("single", Q, np.asarray(g)[None, :], np.asarray(b)[None, :], np.arange(1), args.steps)
         Q, G0, B0 = inst.workload_batch20()
-        cost = q.qaoa_build_cost(ctx, Q.H, Q.f, Q.c0, "i32")
-        nb, p = G0.shape
-        q.qaoa_grad_batch(ctx, [cost], G0, B0)
-        t_adj, (E, dg, db) = _event_time(torch, stream, lambda: q.qaoa_grad_batch(ctx, [cost], G0, B0), args.steps)
-        h = 1e-3
-        G, B = [], []
-        for i in range(nb):
-            for k in range(2 * p):
-                for sgn in (1, -1):
-                    gg, bb = G0[i].copy(), B0[i].copy()
-                    (gg if k < p else bb)[k % p] += sgn * h
-                    G.append(gg)
-                    B.append(bb)
-        G, B = np.array(G), np.array(B)
-        t_fd, Ef = _event_time(torch, stream, lambda: q.qaoa_grad_batch(ctx, [cost], G, B, grad=False), 1)
-        d = ((Ef[0::2] - Ef[1::2]) / (2 * h)).reshape(nb, 2 * p)
-        refb = np.concatenate([dg, db], axis=1)
-        err = float(np.max(np.abs(d - refb)) / np.max(np.abs(refb)))
-        res.update({"batched": {"n": 20, "p": p, "sets": nb, "adjoint_ms": 1e3 * t_adj, "fd_ms": 1e3 * t_fd,
-                                "fd_evals": 4 * p * nb, "speedup": t_fd / t_adj, "h": h,
-                                "fd_rel_err_vs_adjoint": err}})
-        q.qaoa_cost_destroy(cost)
+        compare("batched", Q, G0, B0, np.arange(0, G0.shape[0], 16), 1)
     elif args.workload == "batch20":
         Q, G0, B0 = inst.workload_batch20(batch=args.sets)
         cost = q.qaoa_build_cost(ctx, Q.H, Q.f, Q.c0, "i32")
@@ -562,6 +643,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-errors", action="store_true", help="skip the per-result errors against the oracle")
+    ap.add_argument("--reverse-blocks", type=int, default=0, choices=[0, 1, 2],
+                    help="final and reverse cost-layer passes: half blocks of 2^12 for the low group (0, "
+                         "default), blocks of 2^13 everywhere (1), half blocks everywhere (2)")
     ap.add_argument("--n", type=int, default=N_QUBITS, help="qubits (default: the n=30 workload)")
     ap.add_argument("--p", type=int, default=DEPTH, help="depth (default 8)")
     ap.add_argument("--workload", default="",

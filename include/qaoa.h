@@ -95,7 +95,13 @@ typedef struct {
     int32_t autotune;       /* 1: the first evaluation of each state size n >= 13 times every
                                fusion width (qaoa_autotune) and the context keeps the fastest;
                                ignored when max_fused_qubits is set */
-    int32_t reserved[4];    /* must be zero */
+    int32_t reverse_blocks; /* final forward pass and reverse passes of cost-layer passes:
+                               0 = half blocks of 2^12 amplitudes (two 128-thread CTAs per SM)
+                               for the low qubit group, blocks of 2^13 (one 256-thread CTA per
+                               SM) for the others; 1 = blocks of 2^13 for every group; 2 = half
+                               blocks for every group.  The same results up to the rounding of
+                               the partial sums. */
+    int32_t reserved[3];    /* must be zero */
 } qaoa_options;
 
 typedef struct qaoa_ctx_s *qaoa_ctx;     /* device, stream, options, scratch, plan cache */
@@ -134,6 +140,14 @@ qaoa_status qaoa_cost_info(qaoa_cost cost, int32_t *n, int32_t *shift_bits, int6
 
 /* Copy the int32 table T (2^n entries) into host memory `table`. */
 qaoa_status qaoa_cost_copy_to_host(qaoa_ctx ctx, qaoa_cost cost, int32_t *table);
+
+/* Device address of the int32 table T (2^n entries, index order) and its
+ * entry count.  The table stays owned by the cost handle and is meant to be
+ * read (for example handed to qaoa_expect_noalloc); every call that takes the
+ * handle reads it as it then stands, so a caller that writes through this
+ * pointer changes the objective of every later call (the factorisation check
+ * reports such an edit as mismatching entries). */
+qaoa_status qaoa_cost_device_ptr(qaoa_cost cost, const int32_t **table, int64_t *count);
 
 /* ---- forward evolution -------------------------------------------------- */
 
@@ -446,9 +460,12 @@ qaoa_status qaoa_classify(qaoa_cost cost, const int32_t *qpu_of, int p, int64_t 
  * with L_m the objective of QPU m's own variables and local couplings and X
  * the sum of the cross-QPU couplings (Sec. 3.2), i.e. that the cost phase
  * factorises into local and cross-QPU parts.  All in exact integer arithmetic
- * on the fixed-point coefficients.  *mismatches = number of x that differ;
- * *max_phase_err = max over x of |e^{-i g F} - e^{-i g F_local} e^{-i g F_cross}|
- * at g = gamma_probe, evaluated with the library's own phase routine. */
+ * on the fixed-point coefficients.  *mismatches = number of x that differ.
+ * The phase routine works on the turn count (T + k_c) phi mod 2^64, which is
+ * additive, so wherever the integers split the phases split too, up to the
+ * routine's own rounding; *max_phase_err (may be NULL) measures that rounding,
+ * max |e^{-i g F} - e^{-i g F_local} e^{-i g F_cross}| at g = gamma_probe over
+ * the sampled x (the first of every 1024 consecutive indices). */
 qaoa_status qaoa_check_factorisation(qaoa_ctx ctx, qaoa_cost cost, const int32_t *qpu_of,
                                      double gamma_probe, int64_t *mismatches, double *max_phase_err);
 
@@ -497,7 +514,7 @@ qaoa_status qaoa_telegate_simulate(qaoa_ctx ctx, qaoa_cost cost, const int32_t *
  * sum_x |psi_x|^2 (T[x] + k_c) 2^-shift_bits.
  *   amps:        device pointer, 2^n complex64 amplitudes (caller-owned)
  *   table:       device pointer, the 2^n int32 table T of a qaoa_cost
- *                (qaoa_cost_copy_to_host / qaoa_cost_info give T, s and k_c)
+ *                (qaoa_cost_device_ptr / qaoa_cost_info give T, s and k_c)
  *   n:           1 <= n <= 30; larger n is rejected with QAOA_ERR_INVALID_ARG
  *   shift_bits, k_c: the fixed-point parameters s and k_c of that table
  *   cuda_stream: cudaStream_t the work is ordered on (NULL = default stream);
@@ -509,9 +526,13 @@ qaoa_status qaoa_telegate_simulate(qaoa_ctx ctx, qaoa_cost cost, const int32_t *
  * array, so calls that overlap on the GPU (two host threads, or two streams
  * without ordering between them) race and may return wrong values; order them.
  * The array keeps the previous call's contents, but every value a call reads
- * is written earlier in the same call.  The first call on each device looks
- * up the array's device address with that device current; make that first
- * call before any stream capture begins. */
+ * is written earlier in the same call.  Every call looks up the array's
+ * device address in the context current at the call (cudaGetSymbolAddress;
+ * the lookup allocates nothing), so a caller that works in a context of its
+ * own gets that context's copy of the array; amps and table must be device
+ * (or managed) memory of the current device, else QAOA_ERR_INVALID_ARG.
+ * The call copies its result to the host and synchronises cuda_stream, so it
+ * cannot be issued on a stream that is being captured into a CUDA graph. */
 qaoa_status qaoa_expect_noalloc(const void *amps, const int32_t *table, int n, int32_t shift_bits,
                                 int64_t k_c, void *cuda_stream, double *out_expect);
 
@@ -522,7 +543,11 @@ qaoa_status qaoa_expect_noalloc(const void *amps, const int32_t *table, int n, i
  * 1 = reverse (adjoint) pass, 2 = objective table build, 3 = small-n resident
  * kernel, 4 = factorisation check, 6 = measurement weights and prefix scan,
  * 7 = measurement shots; kind 5 counts every kernel the context launched
- * (timed or not; ms and bytes are 0).  Returns launches, summed
+ * (timed or not; ms and bytes are 0).  Every layer pass is also counted under
+ * the kind of the one kernel that ran it: 8 = direct-load forward pass,
+ * 9 = TMA-staged forward pass with a cost layer, 10 = final forward pass,
+ * 11 = reverse pass of a cost-layer pass, 12 = reverse pass of a mixer-only
+ * pass (kinds 0 and 1 are the sums of 8-10 and 11-12).  Returns launches, summed
  * milliseconds and summed algorithmic bytes (bytes the method must move) since
  * the last reset; reset = 1 clears the counters after reading. */
 qaoa_status qaoa_profile_read(qaoa_ctx ctx, int kind, int64_t *launches, double *ms,

@@ -35,7 +35,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     headers = glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) + \
         glob.glob(os.path.join(ROOT, "include", "*.h"))
-    objs = []
+    objs, cmds = [], []
     for src in sources():
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
         objs.append(obj)
@@ -45,8 +45,19 @@ def build(force: bool = False, verbose: bool = False) -> str:
                 cmd = [NVCC, *FLAGS, "-x", "c++", "-c", src, "-o", obj]
             if verbose:
                 cmd.insert(1, "-Xptxas=-v")
-            print(" ".join(cmd), flush=True)
-            subprocess.check_call(cmd)
+            cmds.append(cmd)
+    # translation units compile independently: run them side by side
+    jobs = max(1, min(len(cmds), os.cpu_count() or 1))
+    running = []
+    for cmd in cmds:
+        print(" ".join(cmd), flush=True)
+        running.append(subprocess.Popen(cmd))
+        if len(running) >= jobs:
+            if running.pop(0).wait() != 0:
+                raise subprocess.CalledProcessError(1, "nvcc")
+    failed = [r for r in running if r.wait() != 0]
+    if failed:
+        raise subprocess.CalledProcessError(1, "nvcc")
     if force or not os.path.exists(LIB) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
         tmp = LIB + f".tmp{os.getpid()}"
         subprocess.check_call([NVCC, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs])

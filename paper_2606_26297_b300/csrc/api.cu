@@ -36,12 +36,12 @@ cudaEvent_t get_event(qaoa_ctx c) {
 
 struct ProfScope {
     qaoa_ctx c;
-    int kind;
+    int kind, kind2;
     double bytes;
     bool on;
     cudaEvent_t a = nullptr;
-    ProfScope(qaoa_ctx c_, int kind_, double bytes_, bool allow = true)
-        : c(c_), kind(kind_), bytes(bytes_), on(c_->opt.profile != 0 && allow) {
+    ProfScope(qaoa_ctx c_, int kind_, double bytes_, bool allow = true, int kind2_ = -1)
+        : c(c_), kind(kind_), kind2(kind2_), bytes(bytes_), on(c_->opt.profile != 0 && allow) {
         if (on) {
             a = get_event(c);
             cudaEventRecord(a, c->stream);
@@ -51,7 +51,7 @@ struct ProfScope {
         if (on) {
             cudaEvent_t b = get_event(c);
             cudaEventRecord(b, c->stream);
-            c->pending.push_back({kind, a, b, bytes});
+            c->pending.push_back({kind, kind2, a, b, bytes});
         }
     }
 };
@@ -62,9 +62,12 @@ void drain_profile(qaoa_ctx c) {
     for (auto &r : c->pending) {
         float ms = 0.f;
         cudaEventElapsedTime(&ms, r.a, r.b);
-        c->prof_launches[r.kind] += 1;
-        c->prof_ms[r.kind] += ms;
-        c->prof_bytes[r.kind] += r.bytes;
+        for (int k : {r.kind, r.kind2}) {
+            if (k < 0) continue;
+            c->prof_launches[k] += 1;
+            c->prof_ms[k] += ms;
+            c->prof_bytes[k] += r.bytes;
+        }
         c->ev_free.push_back(r.a);
         c->ev_free.push_back(r.b);
     }
@@ -157,6 +160,7 @@ qaoa_status make_run_plan(qaoa_ctx c, PlanRun &r, const PlanBufs &b) {
     }
     if (!r.stored) r.plan = make_plan(r.n, r.p, r.grad, maxq);
     if (r.plan.empty()) return fail(QAOA_ERR_INVALID_ARG, "no pass layout for n=%d", r.n);
+    if (c->opt.reverse_blocks == 2) use_half_block_counts(r.plan);
     r.rows = plan_rows(r.plan);
     return QAOA_OK;
 }
@@ -177,8 +181,10 @@ qaoa_status ensure_plan_bufs(qaoa_ctx c, PlanBufs &b, const PlanRun &r) {
         b.states.release(h);
         b.lam.release(h);
     }
-    QAOA_TRY(b.partials.ensure(B * nb * NSLOT * sizeof(double), h, bud));
-    QAOA_TRY(b.partials2.ensure(std::max<size_t>((size_t)B * reduce_chunk_count(nb) * NSLOT * sizeof(double), 64), h, bud));
+    // the half-block reverse passes write one partial-sum row per 2^12 amplitudes
+    const int nunit = 2 * nb;
+    QAOA_TRY(b.partials.ensure(B * nunit * NSLOT * sizeof(double), h, bud));
+    QAOA_TRY(b.partials2.ensure(std::max<size_t>((size_t)B * reduce_chunk_count(nunit) * NSLOT * sizeof(double), 64), h, bud));
     QAOA_TRY(b.sums.ensure((size_t)std::max(r.rows, 1) * B * NSLOT * sizeof(double), h, bud));
     QAOA_TRY(b.scal.ensure(r.plan.size() * B * sizeof(PassScal), h, bud));
     QAOA_TRY(b.slot_scale.ensure(r.plan.size() * B * NSLOT * sizeof(double), h, bud));
@@ -249,17 +255,26 @@ qaoa_status enqueue_plan(qaoa_ctx c, PlanBufs &b, const PlanRun &r, const int32_
         a.ktop = pl.kind == 1 ? r.ktop : 0;
         a.amp0 = (float)std::pow(2.0, -0.5 * n);
         const double bytes = pass_bytes_per_amp(pl) * std::ldexp((double)r.nitems, n);
+        const bool fwd_tma = pl.kind == 0 && a.has_pre && a.has_cost && a.has_post && !a.init;
+        // kernel-level kinds: 8 direct-load forward, 9 TMA forward cost layer, 10 final,
+        // 11 cost-layer reverse, 12 mixer-only reverse
+        const int kernel_kind = pl.kind == 0 ? (fwd_tma ? 9 : 8) : pl.kind == 1 ? 10 : pl.kind == 2 ? 11 : 12;
+        // final and cost-layer reverse passes on half blocks (two CTAs per SM)
+        const bool half = (pl.kind == 1 || pl.kind == 2) &&
+                          ((c->opt.reverse_blocks == 0 && pl.type == 0) || c->opt.reverse_blocks == 2);
         {
-            ProfScope ps(c, pl.kind >= 2 ? 1 : 0, bytes, profile);
+            ProfScope ps(c, pl.kind >= 2 ? 1 : 0, bytes, profile, kernel_kind);
             // a named range per pass for timeline tools (no cost when no tool is attached)
             static const char *const pass_names[4] = {"qaoa forward pass", "qaoa final pass",
                                                       "qaoa reverse pass (psi, lambda)", "qaoa reverse pass (lambda)"};
             nvtxRangePushA(pass_names[pl.kind & 3]);
-            cudaError_t e = pl.kind == 0   ? (a.has_pre && a.has_cost && a.has_post && !a.init
+            cudaError_t e = pl.kind == 0   ? (fwd_tma
                                                   ? launch_fwd_cost_tma(pl.type, a, 2 * c->num_sms, stw, c->stream)
                                                   : launch_fwd_pass(pl.type, a, c->stream))
-                            : pl.kind == 1 ? launch_final_pass(pl.type, a, c->num_sms, stw, c->stream)
-                            : pl.kind == 2 ? launch_rev_pass(pl.type, a, c->num_sms, stw, c->stream)
+                            : pl.kind == 1 ? (half ? launch_final_pass_half(pl.type, a, 2 * c->num_sms, stw, c->stream)
+                                                   : launch_final_pass(pl.type, a, c->num_sms, stw, c->stream))
+                            : pl.kind == 2 ? (half ? launch_rev_pass_half(pl.type, a, 2 * c->num_sms, stw, c->stream)
+                                                   : launch_rev_pass(pl.type, a, c->num_sms, stw, c->stream))
                                            : launch_rev_mid(pl.type, a, c->num_sms, stw, c->stream);
             nvtxRangePop();
             if (e) return fail(QAOA_ERR_CUDA, "layer-pass launch failed: %s", cudaGetErrorString(e));
@@ -267,7 +282,7 @@ qaoa_status enqueue_plan(qaoa_ctx c, PlanBufs &b, const PlanRun &r, const int32_
         }
         if (pl.sum_index >= 0) {
             int nl = 0;
-            CUDA_TRY(launch_reduce_partials_chunked(a.partials, r.nitems, nb, b.partials2.as<double>(),
+            CUDA_TRY(launch_reduce_partials_chunked(a.partials, r.nitems, half ? 2 * nb : nb, b.partials2.as<double>(),
                                                     b.sums.as<double>() + (size_t)pl.sum_index * r.nitems * NSLOT,
                                                     &nl, c->stream));
             c->launches_total += nl;
@@ -677,7 +692,8 @@ qaoa_status qaoa_ctx_create(int device, void *cuda_stream, const qaoa_options *o
     if (o.table_build < 0 || o.table_build > 1) return fail(QAOA_ERR_INVALID_ARG, "table_build must be 0 or 1");
     if (o.autotune < 0 || o.autotune > 1) return fail(QAOA_ERR_INVALID_ARG, "autotune must be 0 or 1");
     if (o.adjoint_mode < 0 || o.adjoint_mode > 2) return fail(QAOA_ERR_INVALID_ARG, "adjoint_mode must be 0, 1 or 2");
-    for (int k = 0; k < 4; ++k)
+    if (o.reverse_blocks < 0 || o.reverse_blocks > 2) return fail(QAOA_ERR_INVALID_ARG, "reverse_blocks must be 0, 1 or 2");
+    for (int k = 0; k < 3; ++k)
         if (o.reserved[k]) return fail(QAOA_ERR_INVALID_ARG, "options.reserved[%d] must be zero", k);
     auto *c = new qaoa_ctx_s();
     c->device = device;
@@ -834,6 +850,13 @@ qaoa_status qaoa_cost_copy_to_host(qaoa_ctx c, qaoa_cost cost, int32_t *table) {
     QAOA_TRY(set_device(c->device));
     CUDA_TRY(cudaMemcpyAsync(table, cost->T, ((size_t)1 << cost->n) * 4, cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return QAOA_OK;
+}
+
+qaoa_status qaoa_cost_device_ptr(qaoa_cost cost, const int32_t **table, int64_t *count) {
+    if (!cost) return fail(QAOA_ERR_INVALID_ARG, "cost is null");
+    if (table) *table = cost->T;
+    if (count) *count = (int64_t)1 << cost->n;
     return QAOA_OK;
 }
 
@@ -1519,7 +1542,7 @@ qaoa_status qaoa_check_factorisation(qaoa_ctx c, qaoa_cost cost, const int32_t *
 }
 
 qaoa_status qaoa_profile_read(qaoa_ctx c, int kind, int64_t *launches, double *ms, double *bytes, int reset) {
-    if (!c || kind < 0 || kind > 7) return fail(QAOA_ERR_INVALID_ARG, "bad context or kind");
+    if (!c || kind < 0 || kind >= QAOA_PROF_KINDS) return fail(QAOA_ERR_INVALID_ARG, "bad context or kind");
     QAOA_TRY(set_device(c->device));
     if (kind == 5) {
         if (launches) *launches = c->launches_total;

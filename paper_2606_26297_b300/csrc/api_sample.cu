@@ -51,7 +51,7 @@ struct SampleProf {
         if (a) {
             cudaEvent_t b = event(c);
             cudaEventRecord(b, c->stream);
-            c->pending.push_back({kind, a, b, bytes});
+            c->pending.push_back({kind, -1, a, b, bytes});
         }
     }
 };

@@ -29,6 +29,8 @@ const char *last_error();
         if (s__ != QAOA_OK) return s__; \
     } while (0)
 
+constexpr int QAOA_PROF_KINDS = 13;
+
 namespace qaoa {
 namespace api {
 
@@ -73,7 +75,7 @@ struct DevBuf {
 };
 
 struct ProfRec {
-    int kind;
+    int kind, kind2;  // kind2: the kernel-level kind of a layer pass, or -1
     cudaEvent_t a, b;
     double bytes;
 };
@@ -102,9 +104,10 @@ struct qaoa_ctx_s {
     DevBuf partials_e, sums_e, topk_a, topk_b, small_items, small_out, misc, status;
     std::vector<ProfRec> pending;
     std::vector<cudaEvent_t> ev_free;
-    int64_t prof_launches[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // by profile kind; 5 is unused (launch count)
-    double prof_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    double prof_bytes[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    // by profile kind (QAOA_PROF_KINDS of them; 5 is unused: it reads the launch count)
+    int64_t prof_launches[QAOA_PROF_KINDS] = {};
+    double prof_ms[QAOA_PROF_KINDS] = {};
+    double prof_bytes[QAOA_PROF_KINDS] = {};
     int64_t launches_total = 0;  // every kernel launched by this context
     cudaStream_t aux_stream = nullptr;  // owned; runs captured optimisation loops
     std::map<int, int> tuned_k;         // fusion width picked by the autotuner, by n

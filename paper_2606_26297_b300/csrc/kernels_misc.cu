@@ -513,7 +513,12 @@ cudaError_t launch_small(const SmallItem *items_dev, int count, int max_n, bool 
 // ---------------------------------------------------------------------------
 // DQAOA factorisation check (Sec. 3.2): for every x,
 //   T[x] == c_off + sum_m L_m[u_m(x)] + sum_{m<m'} sum_{a in m} z_a V_{m,m'}[u_m'(x)][a]
-// with u_m(x) the bits of QPU m's variables.  Also the phase-product error.
+// with u_m(x) the bits of QPU m's variables (exact integers).  The phase
+// factors then agree as well: the library's phase is the turn count
+// (T + k_c) phi mod 2^64, which is additive, so the integer identity implies
+// e^{-i g F} = e^{-i g F_local} e^{-i g F_cross} up to the rounding of the
+// phase routine itself.  That rounding is measured on a sample (the first x
+// of every 1024) instead of at every x.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float2 phase_ll(long long v, unsigned long long phi, unsigned long long off) {
     const unsigned long long t = (unsigned long long)v * phi + off;
@@ -521,6 +526,16 @@ __device__ __forceinline__ float2 phase_ll(long long v, unsigned long long phi, 
     float s, c;
     __sincosf((float)hi * 1.4629180792671596e-09f, &s, &c);
     return make_float2(c, -s);
+}
+
+// |e^{-i g (T + k_c)} - e^{-i g (loc + k_c)} e^{-i g cross}| (max norm) with the
+// library's phase routine, for one sampled entry
+__device__ __forceinline__ float phase_split_err(long long tx, long long loc, long long cross, const FactArgs &a) {
+    const float2 pf = phase_ll(tx + a.k_c, a.phi, 0ull);
+    const float2 pl = phase_ll(loc + a.k_c, a.phi, 0ull);
+    const float2 pc = phase_ll(cross, a.phi, 0ull);
+    const float2 pp = cmul(pl, pc);
+    return fmaxf(fabsf(pf.x - pp.x), fabsf(pf.y - pp.y));
 }
 
 __global__ void fact_check_kernel(FactArgs a) {
@@ -573,12 +588,7 @@ __global__ void fact_check_kernel(FactArgs a) {
         }
         const int32_t tx = a.T[x];
         if ((long long)tx != loc + cross) ++bad;
-        const float2 pf = phase_ll((long long)tx + a.k_c, a.phi, 0ull);
-        const float2 pl = phase_ll(loc + a.k_c, a.phi, 0ull);
-        const float2 pc = phase_ll(cross, a.phi, 0ull);
-        const float2 pp = cmul(pl, pc);
-        const float err = fmaxf(fabsf(pf.x - pp.x), fabsf(pf.y - pp.y));
-        maxerr = fmaxf(maxerr, err);
+        if ((x & 1023) == 0) maxerr = fmaxf(maxerr, phase_split_err(tx, loc, cross, a));
     }
     atomicAdd(&cnt_sh, bad);
     atomicMax(&err_sh, __float_as_uint(maxerr));
@@ -673,11 +683,7 @@ __global__ void __launch_bounds__(256) fact_check_contig_kernel(FactArgs a, cons
             const long long loc = H + a.Ltab[u0];
             const int32_t tx = Tr[u0];
             if ((long long)tx != loc + cross) ++bad;
-            const float2 pf = phase_ll((long long)tx + a.k_c, a.phi, 0ull);
-            const float2 pl = phase_ll(loc + a.k_c, a.phi, 0ull);
-            const float2 pc = phase_ll(cross, a.phi, 0ull);
-            const float2 pp = cmul(pl, pc);
-            maxerr = fmaxf(maxerr, fmaxf(fabsf(pf.x - pp.x), fabsf(pf.y - pp.y)));
+            if (((((unsigned long long)hi << c0) | u0) & 1023ull) == 0) maxerr = fmaxf(maxerr, phase_split_err(tx, loc, cross, a));
         }
     }
     // warp then CTA reduction of the counts and the error bound
@@ -697,12 +703,96 @@ __global__ void __launch_bounds__(256) fact_check_contig_kernel(FactArgs a, cons
     }
 }
 
+// Contiguous allocation with QPU 0 of at least 10 variables: a CTA checks
+// tiles of 1024 consecutive x, each inside one row hi (bits 0..9 of u0 vary,
+// its bits 10..c0-1 are fixed).  Thread t owns x = 4t .. 4t+3 of the tile, so
+// its cross term is one per-thread sum over bits 2..9 of 4t (plus the tile's
+// bits >= 10) and then 0, W0, W1, W0 + W1 for the four entries; the table is
+// read as one 16-byte load per thread, the next tile's load issued before
+// the current one is checked.  One block barrier per tile (W double-buffered).
+__device__ __forceinline__ long long fact_w(const FactArgs &a, long long hi, int q) {
+    long long w = 0;
+    const int c0 = a.c0;
+    for (int m2 = 1; m2 < a.M; ++m2) {
+        const int s2 = a.q_start[m2], c2 = a.q_start[m2 + 1] - s2;
+        const unsigned u2 = (unsigned)((hi >> (s2 - c0)) & ((1u << c2) - 1u));
+        w += a.V[a.V_off[m2] + (size_t)u2 * c0 + q];
+    }
+    return w;
+}
+
+__global__ void __launch_bounds__(256) fact_check_tiles_kernel(FactArgs a, const long long *__restrict__ Hhi,
+                                                               long long ntiles) {
+    __shared__ long long wsh[2][16];
+    __shared__ unsigned long long cnt_sh;
+    __shared__ unsigned int err_sh;
+    const int c0 = a.c0;
+    const unsigned j = 4u * threadIdx.x;
+    if (threadIdx.x == 0) {
+        cnt_sh = 0;
+        err_sh = 0;
+    }
+    unsigned long long bad = 0;
+    float maxerr = 0.f;
+    long long tile = blockIdx.x;
+    int4 tv = make_int4(0, 0, 0, 0);
+    if (tile < ntiles) tv = __ldcs(reinterpret_cast<const int4 *>(a.T + (tile << 10) + j));
+    for (int it = 0; tile < ntiles; tile += gridDim.x, ++it) {
+        const long long x0 = tile << 10;
+        const long long hi = x0 >> c0;
+        const unsigned uc = (unsigned)(x0 & ((1ll << c0) - 1));
+        long long *W = wsh[it & 1];
+        if (threadIdx.x < 16) W[threadIdx.x] = (int)threadIdx.x < c0 ? fact_w(a, hi, threadIdx.x) : 0ll;
+        __syncthreads();
+        const int4 cur = tv;
+        if (tile + gridDim.x < ntiles) tv = __ldcs(reinterpret_cast<const int4 *>(a.T + ((tile + gridDim.x) << 10) + j));
+        long long cr = 0;
+#pragma unroll
+        for (int q = 2; q < 10; ++q)
+            if ((j >> q) & 1u) cr += W[q];
+        for (int q = 10; q < c0; ++q)
+            if ((uc >> q) & 1u) cr += W[q];
+        const long long H = Hhi[hi];
+        const longlong2 l01 = *reinterpret_cast<const longlong2 *>(a.Ltab + uc + j);
+        const longlong2 l23 = *reinterpret_cast<const longlong2 *>(a.Ltab + uc + j + 2);
+        const long long w0 = W[0], w1 = W[1];
+        bad += (long long)cur.x != H + l01.x + cr;
+        bad += (long long)cur.y != H + l01.y + cr + w0;
+        bad += (long long)cur.z != H + l23.x + cr + w1;
+        bad += (long long)cur.w != H + l23.y + cr + w0 + w1;
+        if (threadIdx.x == 0) maxerr = fmaxf(maxerr, phase_split_err(cur.x, H + l01.x, cr, a));
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        bad += __shfl_xor_sync(0xffffffffu, bad, o);
+        maxerr = fmaxf(maxerr, __shfl_xor_sync(0xffffffffu, maxerr, o));
+    }
+    __syncthreads();  // cnt_sh / err_sh initialised before the first atomic
+    if ((threadIdx.x & 31u) == 0) {
+        if (bad) atomicAdd(&cnt_sh, bad);
+        atomicMax(&err_sh, __float_as_uint(maxerr));
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (cnt_sh) atomicAdd(a.mismatches, cnt_sh);
+        atomicMax(a.max_err_bits, err_sh);
+    }
+}
+
+bool fact_check_uses_tiles(const FactArgs &a) { return a.contiguous && a.c0 >= 10 && a.n - a.c0 >= 1; }
+
 cudaError_t launch_fact_check(const FactArgs &a, cudaStream_t st) {
     if (a.contiguous) {
         const unsigned long long nhi = 1ull << (a.n - a.c0);
         fact_hi_kernel<<<(unsigned)((nhi + 255) / 256), 256, 0, st>>>(a, a.hhi);
-        const long long grid = nhi < 2048 ? (long long)nhi : 2048;  // rows per CTA: nhi / 2048 from n - c0 = 11
-        fact_check_contig_kernel<<<(unsigned)grid, 256, 0, st>>>(a, a.hhi, (long long)nhi);
+        if (fact_check_uses_tiles(a)) {
+            const long long ntiles = 1ll << (a.n - 10);
+            const long long grid = ntiles < 148 * 8 ? ntiles : 148 * 8;
+            fact_check_tiles_kernel<<<(unsigned)grid, 256, 0, st>>>(a, a.hhi, ntiles);
+        } else {
+            const long long grid = nhi < 2048 ? (long long)nhi : 2048;  // rows per CTA: nhi / 2048 from n - c0 = 11
+            fact_check_contig_kernel<<<(unsigned)grid, 256, 0, st>>>(a, a.hhi, (long long)nhi);
+        }
     } else {
         fact_check_kernel<<<148 * 8, 256, 0, st>>>(a);
     }

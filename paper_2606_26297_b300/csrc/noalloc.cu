@@ -14,21 +14,16 @@
 // whether or not the entry point is used; and every call shares it.
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "qaoa_internal.h"
 
 namespace {
 
 constexpr int kNoallocMaxN = 30;                           // largest supported state: 2^30 amplitudes
 constexpr int kNoallocMaxChunks = 1 << (kNoallocMaxN - 13);  // chunks of 8192 amplitudes
-constexpr int kNoallocMaxDevices = 64;
 
 // Two FP64 partial sums per chunk, then the two final sums.
 __device__ __align__(256) double g_noalloc_scratch[2 * kNoallocMaxChunks + 2];
 
-std::mutex g_noalloc_mu;
-double *g_noalloc_ptr[kNoallocMaxDevices] = {nullptr};
 
 // Per chunk of 8192 amplitudes: sum |psi|^2 T and sum |psi|^2, FP32 per thread
 // over 32 amplitudes, then an FP64 fixed-order block sum (the same order as
@@ -81,6 +76,23 @@ __global__ void noalloc_final_kernel(const double *__restrict__ part, int nchunk
     if (threadIdx.x == 0) out[s] = sh[0];
 }
 
+// amps / table must live on the current device (or be managed memory):
+// cudaPointerGetAttributes allocates nothing
+qaoa_status check_device_pointer(const void *p, int dev, const char *what) {
+    cudaPointerAttributes at{};
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return qaoa::fail(QAOA_ERR_INVALID_ARG, "qaoa_expect_noalloc: %s is not a device pointer (%s)", what,
+                          cudaGetErrorString(e));
+    }
+    if (at.type == cudaMemoryTypeManaged) return QAOA_OK;
+    if (at.type != cudaMemoryTypeDevice || at.device != dev)
+        return qaoa::fail(QAOA_ERR_INVALID_ARG, "qaoa_expect_noalloc: %s is not memory of the current device %d", what,
+                          dev);
+    return QAOA_OK;
+}
+
 }  // namespace
 
 extern "C" qaoa_status qaoa_expect_noalloc(const void *amps, const int32_t *table, int n, int32_t shift_bits,
@@ -94,21 +106,18 @@ extern "C" qaoa_status qaoa_expect_noalloc(const void *amps, const int32_t *tabl
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return fail(QAOA_ERR_CUDA, "qaoa_expect_noalloc: cudaGetDevice: %s", cudaGetErrorString(e));
-    if (dev < 0 || dev >= kNoallocMaxDevices) return fail(QAOA_ERR_INVALID_ARG, "qaoa_expect_noalloc: device %d", dev);
-    double *scratch = nullptr;
-    {
-        // once per device, with that device current: the device address of the
-        // array (host code cannot use the symbol itself as a device pointer)
-        std::lock_guard<std::mutex> lock(g_noalloc_mu);
-        if (!g_noalloc_ptr[dev]) {
-            void *p = nullptr;
-            e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-            if (e != cudaSuccess || !p)
-                return fail(QAOA_ERR_CUDA, "qaoa_expect_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-            g_noalloc_ptr[dev] = static_cast<double *>(p);
-        }
-        scratch = g_noalloc_ptr[dev];
-    }
+    qaoa_status ps = check_device_pointer(amps, dev, "amps");
+    if (ps == QAOA_OK) ps = check_device_pointer(table, dev, "table");
+    if (ps != QAOA_OK) return ps;
+    // The device address of the array in the context current now (host code
+    // cannot use the symbol itself as a device pointer).  Looked up on every
+    // call: a cache keyed by device would hand a caller working in another
+    // context of the same device the primary context's address.
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+        return fail(QAOA_ERR_CUDA, "qaoa_expect_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+    double *scratch = static_cast<double *>(p);
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     const long long N = 1ll << n;
     const int nchunks = (int)((N + 8191) / 8192);

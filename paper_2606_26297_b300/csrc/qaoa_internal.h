@@ -100,6 +100,10 @@ struct PassArgs {
 cudaError_t launch_fwd_pass(int type, const PassArgs &a, cudaStream_t st);
 cudaError_t launch_final_pass(int type, const PassArgs &a, int grid, unsigned int *status, cudaStream_t st);
 cudaError_t launch_rev_pass(int type, const PassArgs &a, int grid, unsigned int *status, cudaStream_t st);
+// the same pass on half blocks of 2^12 amplitudes (two CTAs per SM; grid =
+// 2 x SMs); one partial-sum row per half block
+cudaError_t launch_rev_pass_half(int type, const PassArgs &a, int grid, unsigned int *status, cudaStream_t st);
+cudaError_t launch_final_pass_half(int type, const PassArgs &a, int grid, unsigned int *status, cudaStream_t st);
 cudaError_t launch_rev_mid(int type, const PassArgs &a, int grid, unsigned int *status, cudaStream_t st);
 cudaError_t launch_wait_probe(unsigned int *status, cudaStream_t st);
 cudaError_t launch_fwd_cost_tma(int type, const PassArgs &a, int grid, unsigned int *status, cudaStream_t st);

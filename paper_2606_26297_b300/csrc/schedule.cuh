@@ -216,6 +216,21 @@ inline std::vector<PassPlan> make_plan(int n, int p, bool grad, int maxq, bool s
     return plan;
 }
 
+// The final pass and the reverse passes of cost-layer passes run on half
+// blocks of 2^12 amplitudes when the context asks for it for every group.  The
+// low group keeps its arrangements there, but in a high group the register
+// bits of arrangement X are window B and those of Y window A (13-bit local
+// bits 8..12 and 3..7), so a group that does not fill its block splits its
+// mixed bits between X and Y differently; the scalars of those passes count
+// them this way.
+inline void use_half_block_counts(std::vector<PassPlan> &plan) {
+    for (PassPlan &pl : plan)
+        if ((pl.kind == 1 || pl.kind == 2) && pl.type == 1) {
+            pl.kX = __builtin_popcount(pl.mask & 0x1F00u);
+            pl.kY = __builtin_popcount(pl.mask & 0x00F8u);
+        }
+}
+
 inline int plan_rows(const std::vector<PassPlan> &plan) {
     int r = 0;
     for (const auto &pl : plan) r += pl.sum_index >= 0;

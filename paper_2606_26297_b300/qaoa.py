@@ -42,7 +42,7 @@ class qaoa_options(ctypes.Structure):
     _fields_ = [("adjoint_mode", ctypes.c_int32), ("profile", ctypes.c_int32),
                 ("memory_budget", ctypes.c_int64), ("max_fused_qubits", ctypes.c_int32),
                 ("state_fp64", ctypes.c_int32), ("table_build", ctypes.c_int32),
-                ("autotune", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("autotune", ctypes.c_int32), ("reverse_blocks", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class qaoa_adam_options(ctypes.Structure):
@@ -104,6 +104,7 @@ _SIGS = {
     "qaoa_cost_destroy": ([_P], None),
     "qaoa_cost_info": ([_P, _PI32, _PI32, _PI64, _PU64, _PD], _I),
     "qaoa_cost_copy_to_host": ([_P, _P, _P], _I),
+    "qaoa_cost_device_ptr": ([_P, ctypes.POINTER(_P), _PI64], _I),
     "qaoa_forward": ([_P, _P, _I, _PD, _PD, ctypes.POINTER(_P)], _I),
     "qaoa_state_destroy": ([_P], None),
     "qaoa_state_copy_to_host": ([_P, _P, _P], _I),
@@ -166,7 +167,8 @@ def qaoa_last_error() -> str:
 
 def qaoa_ctx_create(device: int = 0, stream: int | None = None, profile: bool = False,
                     memory_budget: int = 0, max_fused_qubits: int = 0, state_fp64: bool = False,
-                    table_build: int = 0, autotune: bool = False, adjoint_mode: int = 0):
+                    table_build: int = 0, autotune: bool = False, adjoint_mode: int = 0,
+                    reverse_blocks: int = 0):
     """Create a context; `stream` is a raw cudaStream_t (e.g. torch's
     `torch.cuda.current_stream().cuda_stream`), None for the default stream."""
     opt = qaoa_options()
@@ -177,6 +179,7 @@ def qaoa_ctx_create(device: int = 0, stream: int | None = None, profile: bool = 
     opt.table_build = int(table_build)
     opt.autotune = int(autotune)
     opt.adjoint_mode = int(adjoint_mode)
+    opt.reverse_blocks = int(reverse_blocks)
     out = _P()
     _check(_lib.qaoa_ctx_create(int(device), _P(stream or 0), ctypes.byref(opt), ctypes.byref(out)))
     return out
@@ -225,6 +228,14 @@ def qaoa_cost_copy_to_host(ctx, cost, n: int) -> np.ndarray:
     out = np.empty(1 << n, dtype=np.int32)
     _check(_lib.qaoa_cost_copy_to_host(ctx, cost, out.ctypes.data))
     return out
+
+
+def qaoa_cost_device_ptr(cost):
+    """Device address of the cost handle's int32 table and its entry count."""
+    p = _P()
+    cnt = ctypes.c_int64()
+    _check(_lib.qaoa_cost_device_ptr(cost, ctypes.byref(p), ctypes.byref(cnt)))
+    return p.value, cnt.value
 
 
 # ---- forward --------------------------------------------------------------------------
@@ -596,6 +607,9 @@ def qaoa_wait_probe(ctx) -> None:
 
 PROFILE_KINDS = {"fwd_pass": 0, "rev_pass": 1, "cost_build": 2, "small_resident": 3, "factorisation": 4,
                  "sample_weights": 6, "sample_shots": 7}
+# one kernel each (a layer pass is counted in its aggregate kind above and here)
+PROFILE_KERNEL_KINDS = {"fwd_pass_kernel": 8, "fwd_cost_tma_kernel": 9, "final_pass_kernel": 10,
+                        "rev_pass_kernel": 11, "rev_mid_tma_kernel": 12}
 PROFILE_ALL_LAUNCHES = 5
 
 

@@ -5,6 +5,8 @@ configuration the benchmark times.
     8-parameter gradient against the FP64 oracle (which still finishes in
     seconds at n=26), the gradient against central finite differences taken
     on the GPU, and E at p=1 against the published closed form.
+  * the dense N(0,1) workload's generator at n=28, p=8 (the largest size
+    whose FP64 oracle fits the host): whole state, E, gradient and top-10.
   * n=30, p=8: the oracle cannot hold 2^30 amplitudes, so the check uses a
     QUBO made of three uncoupled dense N(0,1) blocks of 10 variables: its
     state is the tensor product of the blocks' states, E and the gradient are
@@ -107,6 +109,61 @@ def test_maxcut26_full_state_and_gradient(q):
     q.qaoa_state_destroy(st)
     q.qaoa_cost_destroy(cost)
     q.qaoa_ctx_destroy(ctx)
+
+
+# ---- the dense N(0,1) workload at n=28 against the oracle ----------------------------------
+
+def _host_mem_available_gib():
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemAvailable:"):
+                return int(line.split()[1]) / 2 ** 20
+    except OSError:
+        pass
+    return 0.0
+
+
+def test_dense28_full_state_and_gradient_against_oracle(q):
+    """The n=30 workload's generator (dense N(0,1) float32 couplings, ramp
+    angles, p=8) at n=28, the largest size whose FP64 oracle state and
+    adjoint fit the host, run in the benchmark's launch configuration
+    (stored forward states, split windows, three qubit groups): every
+    amplitude (L2 <= 1e-5), E (|dE|/max|F| <= 1e-5), the 16-parameter gradient
+    (<= 1e-4) and the top-10 as tie groups against the oracle (Eq. qaoa_state,
+    Eq. qaoa_expectation_expanded)."""
+    need = 24.0
+    have = _host_mem_available_gib()
+    print(f"host memory available: {have:.1f} GiB")
+    if have < need:
+        pytest.skip(f"the n=28 oracle needs about {need:g} GiB of host memory, {have:.1f} GiB available")
+    ctx = q.qaoa_ctx_create(0)
+    Q, g, b = inst.workload_dense30(28, 8)
+    n = Q.n
+    cost = _cost(q, ctx, Q)
+    E, dg, db, ti, tp = q.qaoa_grad(ctx, cost, g, b, k_top=10)
+    st = q.qaoa_forward(ctx, cost, g, b)
+    psi = q.qaoa_state_copy_to_host(ctx, st, n)
+    q.qaoa_state_destroy(st)
+    q.qaoa_cost_destroy(cost)
+    q.qaoa_ctx_destroy(ctx)
+    F = oracle.cost_table(oracle.canonical_of(Q))
+    ref = oracle.evolve(F, g, b)
+    err2 = 0.0
+    step = 1 << 24
+    for a in range(0, 1 << n, step):
+        err2 += float(np.sum(np.abs(psi[a:a + step].astype(np.complex128) - ref[a:a + step]) ** 2))
+    assert math.sqrt(err2) <= 1e-5
+    Po = np.abs(ref) ** 2
+    del ref, psi
+    gc.collect()
+    kth = np.partition(Po, -10)[-10]
+    assert len(set(ti.tolist())) == 10
+    assert np.all(Po[ti.astype(np.int64)] >= kth - 1e-6 * Po.max())
+    del Po
+    gc.collect()
+    Eo, dgo, dbo = oracle.grad_adjoint(F, g, b)
+    assert abs(E - Eo) / np.max(np.abs(F)) <= E_TOL
+    assert _grad_err(dg, db, dgo, dbo) <= G_TOL
 
 
 # ---- block-separable pins at n=30 and n=32 -----------------------------------------------

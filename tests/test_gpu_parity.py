@@ -466,6 +466,45 @@ def test_adjoint_modes_agree(q, n, p, kind, maxq):
     assert np.max(np.abs(Eb1 - Eb2)) <= 1e-6 * np.max(np.abs(F))
 
 
+@pytest.mark.parametrize("n,p,kind,maxq,mode", [(13, 2, "normal", 10, 2), (18, 3, "int", 10, 1),
+                                               (24, 2, "normal", 10, 2), (24, 2, "normal", 10, 1),
+                                               (20, 2, "int", 6, 1), (17, 4, "normal", 4, 2),
+                                               (22, 3, "maxcut", 8, 2)])
+def test_reverse_block_layouts_agree(q, n, p, kind, maxq, mode):
+    """The final and reverse cost-layer passes on half blocks of 2^12
+    amplitudes (two CTAs per SM) for the low group (the default), on blocks of
+    2^13 (one CTA per SM) everywhere, and on half blocks everywhere give the
+    same E and gradient up to summation order, all against the oracle: low and
+    high groups, full and partial groups, adjacent and split windows, stored
+    states and the uncompute sweep, single and batched requests."""
+    Q = _instance(kind, n, 1500 + n)
+    g, b = _angles(Q, p, kind)
+    F = oracle.cost_table(oracle.canonical_of(Q))
+    Eo, dgo, dbo = oracle.grad_adjoint(F, g, b)
+    sc = max(np.max(np.abs(dgo)), np.max(np.abs(dbo)))
+    res = []
+    for layout in (0, 1, 2):
+        c = q.qaoa_ctx_create(0, adjoint_mode=mode, max_fused_qubits=maxq, reverse_blocks=layout)
+        cost = _cost(q, c, Q)
+        E, dg, db = q.qaoa_grad(c, cost, g, b)
+        assert abs(E - Eo) / np.max(np.abs(F)) <= E_TOL
+        assert max(np.max(np.abs(dg - dgo)), np.max(np.abs(db - dbo))) <= G_TOL * sc
+        Eb, dgb, dbb = q.qaoa_grad_batch(c, [cost], np.stack([g, g * 0.7, g * 1.2]), np.stack([b, b * 0.9, b]))
+        assert abs(Eb[0] - Eo) / np.max(np.abs(F)) <= E_TOL
+        assert max(np.max(np.abs(dgb[0] - dgo)), np.max(np.abs(dbb[0] - dbo))) <= G_TOL * sc
+        res.append((E, dg, db, Eb, dgb, dbb))
+        q.qaoa_cost_destroy(cost)
+        q.qaoa_ctx_destroy(c)
+    # the layouts give each thread different amplitudes, so the FP32 partial
+    # sums round differently: agreement to FP32 rounding, well inside the bounds
+    E0, dg0, db0, Eb0, dgb0, dbb0 = res[0]
+    for E1, dg1, db1, Eb1, dgb1, dbb1 in res[1:]:
+        assert abs(E0 - E1) <= 1e-7 * np.max(np.abs(F))
+        assert max(np.abs(dg0 - dg1).max(), np.abs(db0 - db1).max()) <= 1e-5 * sc
+        assert np.max(np.abs(Eb0 - Eb1)) <= 1e-7 * np.max(np.abs(F))
+        assert max(np.abs(dgb0 - dgb1).max(), np.abs(dbb0 - dbb1).max()) <= 1e-5 * sc
+
+
 def test_factorisation_noncontiguous(q, ctx):
     """A manual (non-contiguous) allocation goes through the general check."""
     n = 14
@@ -474,6 +513,50 @@ def test_factorisation_noncontiguous(q, ctx):
     manual = [(i * 7) % 3 for i in range(n)]
     qpu_of = q.qaoa_partition(n, 3, caps=[5, 5, 5], manual=manual)
     mism, perr = q.qaoa_check_factorisation(ctx, cost, qpu_of, 1.3)
+    assert mism == 0 and perr < 1e-5
+    q.qaoa_cost_destroy(cost)
+
+
+def _int32_view(ptr, count):
+    """A torch view of device memory owned by the library (for planting edits)."""
+    import torch
+
+    class _Raw:
+        __cuda_array_interface__ = {"shape": (count,), "typestr": "<i4", "data": (ptr, False),
+                                    "version": 3, "strides": None}
+    return torch.as_tensor(_Raw(), device="cuda")
+
+
+@pytest.mark.parametrize("n,caps,manual", [
+    (20, [10, 10], None),            # contiguous, QPU 0 of 10 variables: tiled kernel
+    (22, [11, 6, 5], None),          # contiguous, QPU 0 of 11: tiled kernel with a bit above the tile
+    (16, [6, 5, 5], None),           # contiguous, QPU 0 of 6: row kernel
+    (14, [5, 5, 5], [(i * 7) % 3 for i in range(14)]),  # manual: general kernel
+])
+def test_factorisation_check_detects_edited_entries(q, ctx, n, caps, manual):
+    """Sec. 3.2, Eq. local_cross_rule: the check counts exactly the entries of
+    the table that no longer split into local and cross-QPU parts.  Entries
+    are edited on the host side through the table's device address (no GPU
+    fault involved), counted, then restored."""
+    import torch
+    Q = inst.normal_qubo(n, 4200 + n)
+    cost = _cost(q, ctx, Q)
+    qpu_of = q.qaoa_partition(n, len(caps), caps=caps, manual=manual)
+    assert q.qaoa_check_factorisation(ctx, cost, qpu_of, 0.9)[0] == 0
+    ptr, count = q.qaoa_cost_device_ptr(cost)
+    assert count == 1 << n
+    T = _int32_view(ptr, count)
+    N = 1 << n
+    edits = sorted({0, 1, 2, 3, 1023, 1024, N // 2 + 5, N - 1} | set(np.random.default_rng(n).integers(0, N, 20).tolist()))
+    idx = torch.tensor(edits, dtype=torch.int64, device="cuda")
+    saved = T[idx].clone()
+    T[idx] = saved + torch.tensor([(-1) ** k * (1 + k) for k in range(len(edits))], dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    mism, _ = q.qaoa_check_factorisation(ctx, cost, qpu_of, 0.9)
+    assert mism == len(edits)
+    T[idx] = saved
+    torch.cuda.synchronize()
+    mism, perr = q.qaoa_check_factorisation(ctx, cost, qpu_of, 0.9)
     assert mism == 0 and perr < 1e-5
     q.qaoa_cost_destroy(cost)
 

@@ -41,6 +41,24 @@ def test_canonical_form_equals_input_form():
         assert np.array_equal(F, direct)
 
 
+def test_cost_at_equals_input_form():
+    """oracle.cost_at (F at sampled indices, the form used where the full table
+    does not fit the host) against the input form c0 + f.z + z^T H z evaluated
+    directly for each sampled z, exact for integers; sampled indices include
+    0, 2^n - 1 and repeats, at n = 40 (beyond any table) and n = 9."""
+    for n, seed in [(9, 5), (40, 6)]:
+        H, f, c0 = _rand_int_qubo(n, seed)
+        cq = oracle.canonicalize(H, f, c0)
+        rng = np.random.default_rng(seed)
+        xs = np.concatenate([[0, (1 << n) - 1, 5, 5], rng.integers(0, 1 << n, 60, dtype=np.uint64)]).astype(np.uint64)
+        got = oracle.cost_at(cq, xs)
+        for x, v in zip(xs.tolist(), got.tolist()):
+            z = np.array([(x >> i) & 1 for i in range(n)], dtype=float)
+            assert v == c0 + f @ z + z @ H @ z
+        if n <= 20:
+            assert np.array_equal(got, oracle.cost_table(cq)[xs.astype(np.int64)])
+
+
 def test_cost_table_gray_code():
     """Objective table vs an independent Gray-code enumeration: flipping bit k
     of z changes F by (1-2 z_k)(l_k + sum_{i != k} b_{ik} z_i).  Bit-exact on
