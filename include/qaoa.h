@@ -547,7 +547,8 @@ qaoa_status qaoa_expect_noalloc(const void *amps, const int32_t *table, int n, i
  * the kind of the one kernel that ran it: 8 = direct-load forward pass,
  * 9 = TMA-staged forward pass with a cost layer, 10 = final forward pass,
  * 11 = reverse pass of a cost-layer pass, 12 = reverse pass of a mixer-only
- * pass (kinds 0 and 1 are the sums of 8-10 and 11-12).  Returns launches, summed
+ * pass, 13 and 14 = kinds 10 and 11 on half blocks (kind 0 sums 8, 9, 10, 13;
+ * kind 1 sums 11, 12, 14).  Returns launches, summed
  * milliseconds and summed algorithmic bytes (bytes the method must move) since
  * the last reset; reset = 1 clears the counters after reading. */
 qaoa_status qaoa_profile_read(qaoa_ctx ctx, int kind, int64_t *launches, double *ms,

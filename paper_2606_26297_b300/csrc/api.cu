@@ -256,12 +256,14 @@ qaoa_status enqueue_plan(qaoa_ctx c, PlanBufs &b, const PlanRun &r, const int32_
         a.amp0 = (float)std::pow(2.0, -0.5 * n);
         const double bytes = pass_bytes_per_amp(pl) * std::ldexp((double)r.nitems, n);
         const bool fwd_tma = pl.kind == 0 && a.has_pre && a.has_cost && a.has_post && !a.init;
-        // kernel-level kinds: 8 direct-load forward, 9 TMA forward cost layer, 10 final,
-        // 11 cost-layer reverse, 12 mixer-only reverse
-        const int kernel_kind = pl.kind == 0 ? (fwd_tma ? 9 : 8) : pl.kind == 1 ? 10 : pl.kind == 2 ? 11 : 12;
         // final and cost-layer reverse passes on half blocks (two CTAs per SM)
         const bool half = (pl.kind == 1 || pl.kind == 2) &&
                           ((c->opt.reverse_blocks == 0 && pl.type == 0) || c->opt.reverse_blocks == 2);
+        // kernel-level profile kinds, one per kernel (see qaoa_profile_read)
+        const int kernel_kind = pl.kind == 0   ? (fwd_tma ? 9 : 8)
+                                : pl.kind == 1 ? (half ? 13 : 10)
+                                : pl.kind == 2 ? (half ? 14 : 11)
+                                               : 12;
         {
             ProfScope ps(c, pl.kind >= 2 ? 1 : 0, bytes, profile, kernel_kind);
             // a named range per pass for timeline tools (no cost when no tool is attached)
