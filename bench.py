@@ -525,12 +525,24 @@ def run_workload(args):
         ic = list(range(len(qs)))
         q.qaoa_grad_batch(ctx, costs, G0, B0, item_cost=ic)
         t, _ = _event_time(torch, stream, lambda: q.qaoa_grad_batch(ctx, costs, G0, B0, item_cost=ic), args.steps)
+        # the layer-pass kernels alone (CUDA events around each launch, a second context): the
+        # request time they leave is what one launch per pass across all sizes could save at most
+        pctx = q.qaoa_ctx_create(0, stream.cuda_stream, profile=True)
+        q.qaoa_grad_batch(pctx, costs, G0, B0, item_cost=ic)
+        for k in (0, 1, 3, q.PROFILE_ALL_LAUNCHES):
+            q.qaoa_profile_read(pctx, k, reset=True)
+        for _ in range(args.steps):
+            q.qaoa_grad_batch(pctx, costs, G0, B0, item_cost=ic)
+        kern = sum(q.qaoa_profile_read(pctx, k)["ms"] for k in (0, 1, 3)) / args.steps
+        launches = q.qaoa_profile_read(pctx, q.PROFILE_ALL_LAUNCHES)["launches"] / args.steps
         ns = [Qi.n for Qi in qs]
-        res.update({"qubos": len(qs), "n_min": min(ns), "n_max": max(ns), "p": G0.shape[1],
+        res.update({"qubos": len(qs), "n_min": min(ns), "n_max": max(ns), "distinct_n": len(set(ns)), "p": G0.shape[1],
                     "grad_batch_ms": 1e3 * t, "layer_evals_per_s": len(qs) * G0.shape[1] / t,
+                    "pass_kernel_ms": kern, "launches_per_request": launches,
                     "amplitudes": int(sum(2 ** n for n in ns))})
         for c in costs:
             q.qaoa_cost_destroy(c)
+        q.qaoa_ctx_destroy(pctx)
     elif args.workload == "autotune":
         Q, g, b = inst.workload_dense30(args.n, args.p)
         cost = q.qaoa_build_cost(ctx, Q.H, Q.f, Q.c0, "f32")
@@ -541,15 +553,23 @@ def run_workload(args):
         q.qaoa_cost_destroy(cost)
     elif args.workload == "uc32":
         Q, g, b = inst.workload_uc32()
-        cost = q.qaoa_build_cost(ctx, Q.H, Q.f, Q.c0, "f32")
+        actx = q.qaoa_ctx_create(0, stream.cuda_stream, adjoint_mode=args.adjoint, profile=True)
+        cost = q.qaoa_build_cost(actx, Q.H, Q.f, Q.c0, "f32")
         p = len(g)
+        # one untimed step: plan, allocation and graph capture
+        q.qaoa_optimize_adam(actx, [cost], g[None, :], b[None, :], 1, lr=0.01)
+        # the eager first step and the final evaluation each run the reverse sweep once
+        kept = q.qaoa_profile_read(actx, 12, reset=True)["launches"] // 2
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
-        g1, b1, hist, Ef = q.qaoa_optimize_adam(ctx, [cost], g[None, :], b[None, :], args.iters, lr=0.01)
+        g1, b1, hist, Ef = q.qaoa_optimize_adam(actx, [cost], g[None, :], b[None, :], args.iters, lr=0.01)
         dt = time.perf_counter() - t0
-        res.update({"n": 32, "p": p, "adam_iters": args.iters, "seconds": dt, "s_per_step": dt / args.iters,
+        res.update({"n": 32, "p": p, "adam_iters": args.iters, "adjoint_mode": args.adjoint,
+                    "stored_mixer_only_passes": kept, "seconds": dt, "s_per_step": dt / args.iters,
                     "layer_evals_per_s": args.iters * p / dt, "E_start": float(hist[0, 0]),
                     "E_end": float(Ef[0]), "E_min_history": float(hist[:, 0].min())})
         q.qaoa_cost_destroy(cost)
+        q.qaoa_ctx_destroy(actx)
     elif args.workload == "sample":
         Q, g, b = inst.workload_dense30(args.n, args.p)
         pctx = q.qaoa_ctx_create(0, stream.cuda_stream, profile=True)
@@ -647,6 +667,9 @@ def main():
     ap.add_argument("--reverse-blocks", type=int, default=0, choices=[0, 1, 2],
                     help="final and reverse cost-layer passes: half blocks of 2^12 for the low group (0, "
                          "default), blocks of 2^13 everywhere (1), half blocks everywhere (2)")
+    ap.add_argument("--adjoint", type=int, default=0, choices=[0, 1, 2],
+                    help="--workload uc32: adjoint form, 0 automatic (stored states that fit), "
+                         "1 uncompute, 2 stored")
     ap.add_argument("--n", type=int, default=N_QUBITS, help="qubits (default: the n=30 workload)")
     ap.add_argument("--p", type=int, default=DEPTH, help="depth (default 8)")
     ap.add_argument("--workload", default="",

@@ -75,7 +75,9 @@ typedef struct {
 /* Adjoint (gradient) strategy. */
 typedef enum {
     QAOA_ADJ_AUTO = 0,      /* stored states when they fit in free device memory (and the
-                               memory budget) with a 4 GiB margin, else uncompute */
+                               memory budget) with a 4 GiB margin; when only some fit, the
+                               inputs of the last mixer-only passes that fit are kept and the
+                               rest of the reverse sweep uncomputes; else uncompute */
     QAOA_ADJ_UNCOMPUTE = 1, /* the reverse sweep recomputes earlier states by U^dagger on an
                                interleaved (psi, lambda) buffer: 3 states of memory */
     QAOA_ADJ_STORE = 2      /* the forward sweep keeps the states the reverse sweep needs (about

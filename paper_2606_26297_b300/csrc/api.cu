@@ -122,40 +122,56 @@ struct PlanRun {
     std::vector<PassPlan> plan;
     int rows;
     float2 *psi_ext = nullptr;  // forward-only: evolve in this caller buffer instead of b.psi
-    bool stored = false;        // adjoint with stored forward states (else uncompute)
+    bool stored = false;        // adjoint with stored forward states (all or some; else uncompute)
     int nslots = 0;             // stored states per item
+    int kept = 0;               // mixer-only passes whose input is stored
 };
 
 // Build the pass plan of r (r.n, r.p, r.grad, r.nitems set): the adjoint
 // keeps the forward states it needs when options.adjoint_mode asks for it, or
-// (auto) when they fit in free device memory with a margin; else it
-// uncomputes psi on the interleaved buffer.
-qaoa_status make_run_plan(qaoa_ctx c, PlanRun &r, const PlanBufs &b) {
+// (auto) when they fit in free device memory (and the memory budget) with a
+// margin; when only some fit (auto), it keeps the inputs of as many of the
+// last mixer-only passes as fit and uncomputes psi on the interleaved buffer
+// for the rest; with none, the whole reverse sweep uncomputes.
+qaoa_status make_run_plan(qaoa_ctx c, PlanRun &r, const PlanBufs &b, int keep_cap = -1) {
     const int maxq = maxq_for(c, r.n);
     r.stored = false;
     r.nslots = 0;
+    r.kept = 0;
     bool tuned_unc = false;
     if (c->opt.autotune && c->opt.adjoint_mode == QAOA_ADJ_AUTO) {
         auto it = c->tuned_uncompute.find(r.n);
         tuned_unc = it != c->tuned_uncompute.end() && it->second;
     }
     if (r.grad && c->opt.adjoint_mode != QAOA_ADJ_UNCOMPUTE && !tuned_unc) {
-        int ns = 0;
-        std::vector<PassPlan> sp = make_plan(r.n, r.p, true, maxq, true, &ns);
+        int ns = 0, nm = 0;
+        std::vector<PassPlan> sp = make_plan(r.n, r.p, true, maxq, -1, &ns, &nm);
         const double N8 = std::ldexp(8.0 * r.nitems, r.n);
-        // stored: psi + interleaved + lambda + ns states; uncompute: psi + interleaved
-        const double extra = (ns + 1) * N8 - (double)(b.states.cap + b.lam.cap);
+        // bytes that can hold lambda and the stored states: free memory less a margin,
+        // plus what the context already holds for them (psi and the interleaved
+        // buffer of the uncompute sweep are needed either way)
         size_t freeb = 0, total = 0;
         cudaMemGetInfo(&freeb, &total);
         const double margin = 4.0 * (1ull << 30);
-        bool fits = extra <= (double)freeb - margin;
-        if (c->opt.memory_budget > 0 &&
-            (double)c->held + extra > (double)c->opt.memory_budget)
-            fits = false;
-        if (ns > 0 && (c->opt.adjoint_mode == QAOA_ADJ_STORE || fits)) {
+        const double held = (double)(b.states.cap + b.lam.cap);
+        double avail = (double)freeb - margin + held;
+        if (c->opt.memory_budget > 0)
+            avail = std::min(avail, (double)c->opt.memory_budget - (double)c->held + held);
+        const bool all = c->opt.adjoint_mode == QAOA_ADJ_STORE || (ns + 1) * N8 <= avail;
+        if (ns > 0 && all && (keep_cap < 0 || keep_cap >= nm)) {
             r.plan = std::move(sp);
             r.stored = true;
             r.nslots = ns;
+            r.kept = nm;
+        } else if (ns > 0) {
+            int keep = all ? nm : (int)std::floor(avail / N8) - 1;  // one state for lambda
+            if (keep_cap >= 0) keep = std::min(keep, keep_cap);
+            if (keep >= 1) {
+                r.plan = make_plan(r.n, r.p, true, maxq, keep, &ns);
+                r.stored = true;
+                r.nslots = ns;
+                r.kept = keep;
+            }
         }
     }
     if (!r.stored) r.plan = make_plan(r.n, r.p, r.grad, maxq);
@@ -163,6 +179,24 @@ qaoa_status make_run_plan(qaoa_ctx c, PlanRun &r, const PlanBufs &b) {
     if (c->opt.reverse_blocks == 2) use_half_block_counts(r.plan);
     r.rows = plan_rows(r.plan);
     return QAOA_OK;
+}
+
+qaoa_status ensure_plan_bufs(qaoa_ctx c, PlanBufs &b, const PlanRun &r);
+
+// Plan and allocate; with the automatic adjoint choice, a plan that keeps
+// stored states but meets the memory budget during allocation is retried with
+// one kept state fewer, down to the uncompute sweep.
+qaoa_status plan_and_allocate(qaoa_ctx c, PlanRun &r, PlanBufs &b) {
+    int cap = -1;
+    for (;;) {
+        QAOA_TRY(make_run_plan(c, r, b, cap));
+        const qaoa_status st = ensure_plan_bufs(c, b, r);
+        if (st == QAOA_OK) return QAOA_OK;
+        if (st != QAOA_ERR_OUT_OF_MEMORY || !r.stored || c->opt.adjoint_mode != QAOA_ADJ_AUTO) return st;
+        cap = r.kept - 1;
+        b.states.release(&c->held);
+        b.lam.release(&c->held);
+    }
 }
 
 // Allocate the working set of a plan for `nitems` items of size n.
@@ -223,7 +257,7 @@ qaoa_status enqueue_plan(qaoa_ctx c, PlanBufs &b, const PlanRun &r, const int32_
         a.psi = W;
         a.pl = b.pl.as<float4>();
         if (r.stored) {
-            a.split = pl.kind == 1 || pl.kind == 2;  // write lambda alone
+            a.split = (pl.kind == 1 || pl.kind == 2) && pl.split_out;  // write lambda alone
             a.lam = b.lam.as<float2>();
             if (pl.kind == 0) {
                 a.psi = slot_ptr(pl.in_slot);
@@ -360,8 +394,7 @@ qaoa_status run_single(qaoa_ctx c, const qaoa_cost_s *cost, int p, const double 
     r.ktop = grad ? ktop : 0;
     r.psi_ext = grad ? nullptr : psi_out;
     PlanBufs &b = c->single;
-    QAOA_TRY(make_run_plan(c, r, b));
-    QAOA_TRY(ensure_plan_bufs(c, b, r));
+    QAOA_TRY(plan_and_allocate(c, r, b));
     // scalars on the host (one item)
     std::vector<PassScal> sc(r.plan.size());
     std::vector<double> ss(r.plan.size() * NSLOT);
@@ -555,8 +588,7 @@ qaoa_status build_groups(qaoa_ctx c, int nq, const qaoa_cost *costs, const int32
         auto &slot = c->groups[g.n];
         if (!slot) slot.reset(new PlanBufs());
         g.b = slot.get();
-        QAOA_TRY(make_run_plan(c, g.r, *g.b));
-        QAOA_TRY(ensure_plan_bufs(c, *g.b, g.r));
+        QAOA_TRY(plan_and_allocate(c, g.r, *g.b));
         const size_t N = (size_t)1 << g.n;
         if (g.tabs.size() == 1) {
             g.tables = g.tabs[0]->T;
@@ -731,10 +763,8 @@ qaoa_status qaoa_build_cost(qaoa_ctx c, const qaoa_qubo *q, qaoa_cost *out) {
     h->device = c->device;
     const size_t N = (size_t)1 << n;
     {
-        cudaError_t e = cudaMalloc(&h->T, N * sizeof(int32_t));
+        cudaError_t e = ctx_malloc(c, reinterpret_cast<void **>(&h->T), N * sizeof(int32_t));
         if (e) {
-            cudaGetLastError();
-            h->T = nullptr;
             return fail(QAOA_ERR_OUT_OF_MEMORY, "objective table (%zu bytes): %s", N * 4, cudaGetErrorString(e));
         }
     }
@@ -759,7 +789,7 @@ qaoa_status qaoa_build_cost(qaoa_ctx c, const qaoa_qubo *q, qaoa_cost *out) {
     long long *min_val = nullptr;
     unsigned long long *min_idx = nullptr;
     if (digits > 0) {
-        const int grid = c->num_sms;
+        const int grid = 2 * c->num_sms;  // two tile CTAs per SM
         const size_t alo_b = ((size_t)8 << nlo), ahi_b = ((size_t)8 << nhi), w_b = (size_t)digits * 32 << nlo;
         const size_t tot = coef_bytes + (size_t)grid * 16 + 64 + alo_b + ahi_b + w_b + 1024;
         QAOA_TRY(c->misc.ensure(tot, &c->held, c->opt.memory_budget));
@@ -881,10 +911,8 @@ qaoa_status qaoa_forward(qaoa_ctx c, qaoa_cost cost, int p, const double *gamma,
         fresh->fp64 = fp64;
         fresh->device = c->device;
         const size_t bytes = ((size_t)1 << n) * (fp64 ? 16 : 8);
-        cudaError_t e = cudaMalloc(&fresh->amps, bytes);
+        cudaError_t e = ctx_malloc(c, &fresh->amps, bytes);
         if (e) {
-            cudaGetLastError();
-            fresh->amps = nullptr;
             return fail(QAOA_ERR_OUT_OF_MEMORY, "state (%zu bytes): %s", bytes, cudaGetErrorString(e));
         }
         st = fresh.get();

@@ -303,10 +303,8 @@ qaoa_status qaoa_state_from_host(qaoa_ctx c, int n, int fp64, const void *amps, 
     s->fp64 = fp64 != 0;
     s->device = c->device;
     const size_t bytes = ((size_t)1 << n) * (fp64 ? 16 : 8);
-    cudaError_t e = cudaMalloc(&s->amps, bytes);
+    cudaError_t e = ctx_malloc(c, &s->amps, bytes);
     if (e) {
-        cudaGetLastError();
-        s->amps = nullptr;
         return fail(QAOA_ERR_OUT_OF_MEMORY, "state (%zu bytes): %s", bytes, cudaGetErrorString(e));
     }
     CUDA_TRY(cudaMemcpyAsync(s->amps, amps, bytes, cudaMemcpyHostToDevice, c->stream));

@@ -115,6 +115,29 @@ struct qaoa_ctx_s {
     DevBuf sample_items, sample_scratch, sample_out, small_states;  // measurement by shots
 };
 
+// cudaMalloc for a caller-visible object (a state, an objective table).  The
+// stored forward states of the adjoint (and its lambda buffer) are scratch
+// the context re-creates on its next gradient call, so when the allocation
+// fails they are released and the allocation is tried once more.
+inline cudaError_t ctx_malloc(qaoa_ctx_s *c, void **p, size_t bytes) {
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) return e;
+    cudaGetLastError();
+    *p = nullptr;
+    c->single.states.release(&c->held);
+    c->single.lam.release(&c->held);
+    for (auto &kv : c->groups) {
+        kv.second->states.release(&c->held);
+        kv.second->lam.release(&c->held);
+    }
+    e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+    }
+    return e;
+}
+
 struct qaoa_cost_s {
     int device = 0;
     int n = 0;

@@ -26,7 +26,7 @@ namespace qaoa {
 namespace {
 
 constexpr int TM = 128;         // rows (x_lo) per tile
-constexpr int TN = 128;         // columns (x_hi) per tile
+constexpr int TN = 64;          // columns (x_hi) per tile
 constexpr int KP = 16;          // padded contraction length (n_hi <= 16)
 constexpr int OPB = TM * KP * 2;  // bytes of one 128 x 16 f16 operand tile (4 KB)
 
@@ -134,23 +134,26 @@ __global__ void table_prep_kernel(TableMmaArgs a) {
 }
 
 // ---- the tile kernel ----------------------------------------------------------------------
-// 256 threads.  Warp w reads tensor-memory lanes 32 (w mod 4) .. +31 (tile rows,
-// x_lo) and columns 64 (w / 4) .. +63 of the tile.  The epilogue works modulo
-// 2^32: T itself fits in int32, so wrapping int32 sums of A_lo, A_hi and the
-// digit products give T exactly whatever the size of the parts.
+// 256 threads, two CTAs per SM (each holds DIG x 64 tensor-memory columns,
+// at most 256, so both allocations fit the SM's 512 columns and neither waits:
+// the CTAs overlap one another's operand, MMA and epilogue latencies).  Warp w
+// reads tensor-memory lanes 32 (w mod 4) .. +31 (tile rows, x_lo) and columns
+// 32 (w / 4) .. +31 of the 64-column tile, one digit at a time.  The epilogue
+// works modulo 2^32: T itself fits in int32, so wrapping int32 sums of A_lo,
+// A_hi and the digit products give T exactly whatever the size of the parts.
 // DIG = number of base-2^11 digits of W (1..4).
 template <int DIG>
-__global__ void __launch_bounds__(256, 1) table_mma_kernel(TableMmaArgs a) {
+__global__ void __launch_bounds__(256, 2) table_mma_kernel(TableMmaArgs a) {
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char *opA = smem;                                  // DIG x 4 KB
-    unsigned char *opB = smem + DIG * OPB;                      // 4 KB
-    int32_t *ahi_t = reinterpret_cast<int32_t *>(opB + OPB);    // 128 entries, mod 2^32
+    unsigned char *opB = smem + DIG * OPB;                      // 2 KB (64 x 16 f16)
+    int32_t *ahi_t = reinterpret_cast<int32_t *>(opB + OPB);    // 64 entries, mod 2^32
     __shared__ __align__(8) unsigned long long mbar;
     __shared__ uint32_t tslot;
     __shared__ int32_t rv[8];
     __shared__ unsigned long long rx[8];
     const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
-    constexpr uint32_t ncols = DIG == 1 ? 128u : (DIG == 2 ? 256u : 512u);
+    constexpr uint32_t ncols = DIG == 1 ? 64u : (DIG == 2 ? 128u : 256u);
     if (warp == 0) tmem_alloc(&tslot, ncols);
     if (tid == 0) mbar_init(&mbar, 1);
     tc_fence_before();
@@ -158,10 +161,10 @@ __global__ void __launch_bounds__(256, 1) table_mma_kernel(TableMmaArgs a) {
     tc_fence_after();
     const uint32_t tmem = tslot;
     const int nlo = a.nlo, nhi = a.nhi;
-    const long long NT = 1ll << (nhi - 7);
-    const long long ntiles = 1ll << (a.n - 14);
+    const long long NT = 1ll << (nhi - 6);
+    const long long ntiles = 1ll << (a.n - 13);
     const uint32_t row = (warp & 3u) * 32u + lane;  // tile row of this thread
-    const int cbase = (int)(warp >> 2) * 64;        // first tile column of this thread
+    const int col0 = (int)(warp >> 2) * 32;         // first tile column of this thread
     const size_t stride = (size_t)1 << nlo;         // x step of one column
     const uint32_t kstep = 1u << (nlo - 7);         // (x >> 7) step of one column
     int32_t best = INT_MAX;
@@ -171,7 +174,7 @@ __global__ void __launch_bounds__(256, 1) table_mma_kernel(TableMmaArgs a) {
     bool ok = true;
     for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const long long mt = t / NT, nt = t % NT;
-        // operands: threads 0..127 write row `tid` of each tile
+        // operands: threads 0..127 write row `tid` of the A tiles, 0..63 row `tid` of B
         if (tid < 128) {
             if (mt != cur_mt) {
 #pragma unroll
@@ -183,20 +186,25 @@ __global__ void __launch_bounds__(256, 1) table_mma_kernel(TableMmaArgs a) {
                     *reinterpret_cast<uint4 *>(opA + d * OPB + op_off(tid, 8)) = hi;
                 }
             }
-            const unsigned long long xh = (unsigned long long)(nt * TN + tid);
-            uint32_t wds[KP / 2];
+            if (tid < TN) {
+                const unsigned long long xh = (unsigned long long)(nt * TN + tid);
+                uint32_t wds[KP / 2];
 #pragma unroll
-            for (int k = 0; k < KP; k += 2) {
-                const uint32_t b0 = (k < nhi && ((xh >> k) & 1ull)) ? 0x3C00u : 0u;        // f16 1.0
-                const uint32_t b1 = (k + 1 < nhi && ((xh >> (k + 1)) & 1ull)) ? 0x3C00u : 0u;
-                wds[k / 2] = b0 | (b1 << 16);
+                for (int k = 0; k < KP; k += 2) {
+                    const uint32_t b0 = (k < nhi && ((xh >> k) & 1ull)) ? 0x3C00u : 0u;  // f16 1.0
+                    const uint32_t b1 = (k + 1 < nhi && ((xh >> (k + 1)) & 1ull)) ? 0x3C00u : 0u;
+                    wds[k / 2] = b0 | (b1 << 16);
+                }
+                *reinterpret_cast<uint4 *>(opB + op_off(tid, 0)) = make_uint4(wds[0], wds[1], wds[2], wds[3]);
+                *reinterpret_cast<uint4 *>(opB + op_off(tid, 8)) = make_uint4(wds[4], wds[5], wds[6], wds[7]);
+                ahi_t[tid] = (int32_t)a.ahi[xh];
             }
-            *reinterpret_cast<uint4 *>(opB + op_off(tid, 0)) = make_uint4(wds[0], wds[1], wds[2], wds[3]);
-            *reinterpret_cast<uint4 *>(opB + op_off(tid, 8)) = make_uint4(wds[4], wds[5], wds[6], wds[7]);
-            ahi_t[tid] = (int32_t)a.ahi[xh];
             fence_proxy_async();
         }
         cur_mt = mt;
+        // x = x_lo + 2^nlo x_hi, x_lo = mt 128 + row; read before the barrier so the load overlaps the MMA
+        const unsigned long long xlo = (unsigned long long)(mt * TM + row);
+        const int32_t alo = (int32_t)a.alo[xlo];
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
@@ -216,34 +224,31 @@ __global__ void __launch_bounds__(256, 1) table_mma_kernel(TableMmaArgs a) {
         }
         parity ^= 1u;
         tc_fence_after();
-        // epilogue: x = x_lo + 2^nlo x_hi, x_lo = mt 128 + row, x_hi = nt 128 + column
-        const unsigned long long xlo = (unsigned long long)(mt * TM + row);
-        const int32_t alo = (int32_t)a.alo[xlo];
+        // epilogue: digits one at a time into the integer sums u
+        uint32_t u[32];
 #pragma unroll
-        for (int c0 = 0; c0 < 64; c0 += 32) {
-            const int col0 = cbase + c0;
-            float acc[DIG][32];
+        for (int j = 0; j < 32; ++j) u[j] = (uint32_t)alo + (uint32_t)ahi_t[col0 + j];
 #pragma unroll
-            for (int d = 0; d < DIG; ++d)
-                tmem_ld32(tmem + (((warp & 3u) * 32u) << 16) + (uint32_t)(d * TN + col0), acc[d]);
-            int32_t *ptr = a.T + xlo + ((size_t)(nt * TN + col0) << nlo);
-            uint32_t k = ((uint32_t)(nt * TN + col0) << (nlo - 7)) | (uint32_t)mt;
+        for (int d = 0; d < DIG; ++d) {
+            float acc[32];
+            tmem_ld32(tmem + (((warp & 3u) * 32u) << 16) + (uint32_t)(d * TN + col0), acc);
+            // exact integers |acc| <= 2^14: adding 1.5 * 2^23 puts them in the low mantissa bits
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                // exact integers |acc| <= 2^14: adding 1.5 * 2^23 puts them in the low mantissa bits
-                uint32_t u = (uint32_t)alo + (uint32_t)ahi_t[col0 + j];
+            for (int j = 0; j < 32; ++j)
+                u[j] += ((uint32_t)__float_as_int(acc[j] + 12582912.0f) - 0x4B400000u) << (11 * d);
+        }
+        int32_t *ptr = a.T + xlo + ((size_t)(nt * TN + col0) << nlo);
+        uint32_t k = ((uint32_t)(nt * TN + col0) << (nlo - 7)) | (uint32_t)mt;
 #pragma unroll
-                for (int d = 0; d < DIG; ++d)
-                    u += ((uint32_t)__float_as_int(acc[d][j] + 12582912.0f) - 0x4B400000u) << (11 * d);
-                const int32_t v = (int32_t)u;
-                __stcs(ptr, v);
-                ptr += stride;
-                if (v < best || (v == best && k < bestk)) {
-                    best = v;
-                    bestk = k;
-                }
-                k += kstep;
+        for (int j = 0; j < 32; ++j) {
+            const int32_t v = (int32_t)u[j];
+            __stcs(ptr, v);
+            ptr += stride;
+            if (v < best || (v == best && k < bestk)) {
+                best = v;
+                bestk = k;
             }
+            k += kstep;
         }
         tc_fence_before();
         __syncthreads();
@@ -298,11 +303,11 @@ cudaError_t launch_table_mma(TableMmaArgs a, int grid, cudaStream_t st) {
     table_prep_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e) return e;
-    const long long ntiles = 1ll << (a.n - 14);
+    const long long ntiles = 1ll << (a.n - 13);
     if (grid > ntiles) grid = (int)ntiles;
-    // one CTA per SM: the dynamic shared memory request keeps a second CTA off
-    // the SM, so a tensor-memory allocation never waits on another CTA
-    const int smem = 120 * 1024;
+    // two CTAs per SM: the dynamic shared memory request keeps a third CTA off
+    // the SM, so a tensor-memory allocation (at most 256 columns) never waits
+    const int smem = 80 * 1024;
     switch (a.digits) {
         case 1:
             if ((e = cudaFuncSetAttribute(table_mma_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)))

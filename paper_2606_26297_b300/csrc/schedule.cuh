@@ -42,16 +42,17 @@ struct Group {
 // State buffers: slot >= 0 is a stored forward state, SLOT_W the working
 // state, SLOT_NONE no buffer.  Without stored states every pass works in place
 // and the reverse sweep uncomputes psi on the interleaved (psi, lambda)
-// buffer.  With them (stored = 1, three or more qubit groups) the forward pass
-// f reads in_slot and writes out_slot, keeping the input of every mixer-only
-// pass; the reverse of a mixer-only pass (kind 3) reads psi from psi_slot and
-// carries lambda alone, writing it interleaved with psi (pl_out) when the next
-// reverse pass undoes a cost layer, which then runs on the interleaved buffer
-// as before and writes lambda alone.
+// buffer.  With them (three or more qubit groups) the forward pass f reads
+// in_slot and writes out_slot, keeping the input of each kept mixer-only pass
+// (all of them, or the last few when memory holds only those); the reverse of
+// a kept mixer-only pass (kind 3) reads psi from psi_slot and carries lambda
+// alone, writing it interleaved with psi (pl_out) when the next reverse pass
+// runs on the interleaved buffer.  A pass of kind 1 or 2 writes lambda alone
+// (split_out) when the next reverse pass is a kept mixer-only one.
 constexpr int SLOT_W = -1, SLOT_NONE = -2;
 struct PassPlan {
     int kind;
-    int stored;
+    int split_out;             // final / cost-layer reverse / uncomputing reverse pass: write lambda alone
     int in_slot, out_slot, psi_slot;
     int pl_out;
     int type, loA, loB;
@@ -128,11 +129,16 @@ inline std::vector<Group> make_groups(int n, int maxq) {
 }
 
 // Forward schedule, then (grad) the reverse passes in reverse order; the
-// reverse of the final pass is fused into it.  stored: keep the forward states
-// the reverse sweep needs (outputs of the first and of boundary passes, and
-// inputs of middle passes); *nslots receives their count.
-inline std::vector<PassPlan> make_plan(int n, int p, bool grad, int maxq, bool stored = false,
-                                       int *nslots = nullptr) {
+// reverse of the final pass is fused into it.  stored_mids: how many
+// mixer-only passes keep their input for the reverse sweep (-1: all; 0: none,
+// the uncompute sweep).  The kept ones are the last of the forward sweep, which
+// the reverse sweep meets first; their reverse passes carry lambda alone, the
+// others uncompute psi on the interleaved buffer, and each reverse pass writes
+// the form the next one reads.  *nslots receives the number of stored states
+// (with -1, the inputs of all mixer-only passes); *nmids the number of
+// mixer-only passes.
+inline std::vector<PassPlan> make_plan(int n, int p, bool grad, int maxq, int stored_mids = 0,
+                                       int *nslots = nullptr, int *nmids = nullptr) {
     const std::vector<Group> gs = make_groups(n, maxq);
     if (gs.empty()) return {};
     const int G = (int)gs.size();
@@ -154,26 +160,40 @@ inline std::vector<PassPlan> make_plan(int n, int p, bool grad, int maxq, bool s
         }
     }
     const int F = (int)f.size();
-    stored = stored && grad && G >= 3;
     auto is_middle = [&](int i) { return !f[i].init && !f[i].epi && f[i].la < 0 && f[i].lc < 0 && f[i].lb >= 0; };
+    int M = 0;
+    for (int i = 0; i < F; ++i) M += is_middle(i) ? 1 : 0;
+    if (nmids) *nmids = M;
+    int keep = (grad && G >= 3) ? (stored_mids < 0 ? M : (stored_mids < M ? stored_mids : M)) : 0;
+    // the last `keep` mixer-only passes keep their input
+    std::vector<char> kept(F, 0);
+    for (int i = F - 1, left = keep; i >= 0 && left > 0; --i)
+        if (is_middle(i)) {
+            kept[i] = 1;
+            --left;
+        }
     std::vector<int> in_slot(F, SLOT_NONE), out_slot(F, SLOT_W);
     int ns = 0;
     for (int i = 0; i < F; ++i) {
         in_slot[i] = i == 0 ? SLOT_NONE : out_slot[i - 1];
         if (f[i].epi) {
             out_slot[i] = SLOT_NONE;
-        } else if (stored && i + 1 < F && is_middle(i + 1)) {
+        } else if (i + 1 < F && kept[i + 1]) {
             out_slot[i] = ns++;
         }
     }
     if (nslots) *nslots = ns;
+    // form each reverse pass reads: lambda alone (a kept mixer-only pass) or the
+    // interleaved buffer (every other pass); a reverse pass writes what the next
+    // one reads, the final pass what the first reverse pass reads
+    auto reads_lambda_alone = [&](int i) { return i >= 0 && kept[i] != 0; };
     std::vector<PassPlan> plan;
     int rows = 0;
     auto base = [&](const D &d, int kind) {
         PassPlan pl{};
         const Group &g = gs[d.group];
         pl.kind = kind;
-        pl.stored = stored ? 1 : 0;
+        pl.split_out = 0;
         pl.in_slot = pl.out_slot = pl.psi_slot = SLOT_W;
         pl.type = g.type;
         pl.loA = g.loA;
@@ -198,15 +218,18 @@ inline std::vector<PassPlan> make_plan(int n, int p, bool grad, int maxq, bool s
             pl.slot_param[0] = pl.slot_param[1] = -2;
             pl.slot_param[2] = pl.slot_param[3] = d.la;
             pl.sum_index = rows++;
+            pl.split_out = reads_lambda_alone(i - 1) ? 1 : 0;
         }
         plan.push_back(pl);
     }
     if (grad)
         for (int i = (int)f.size() - 2; i >= 0; --i) {
-            const bool mid = stored && is_middle(i);
+            const bool mid = kept[i] != 0;
             PassPlan pl = base(f[i], mid ? 3 : 2);
             pl.psi_slot = mid ? in_slot[i] : SLOT_NONE;
-            pl.pl_out = mid && i >= 1 && !is_middle(i - 1);
+            const bool next_alone = reads_lambda_alone(i - 1);
+            pl.pl_out = mid && i >= 1 && !next_alone;
+            pl.split_out = !mid && next_alone ? 1 : 0;
             if (f[i].lb >= 0) pl.slot_param[0] = pl.slot_param[1] = f[i].lb;
             if (f[i].lc >= 0) pl.slot_param[2] = p + f[i].lc;
             if (f[i].la >= 0) pl.slot_param[3] = pl.slot_param[4] = f[i].la;
@@ -438,9 +461,9 @@ __host__ __device__ inline void pass_scalars(const PassPlan &pl, const double *g
 // Algorithmic bytes per amplitude of a pass (what the method must move).
 inline double pass_bytes_per_amp(const PassPlan &pl) {
     if (pl.kind == 0) return (pl.init ? 0.0 : 8.0) + 8.0 + (pl.lc >= 0 ? 4.0 : 0.0);
-    if (pl.kind == 1) return 8.0 + 4.0 + (pl.stored ? 8.0 : 16.0);
+    if (pl.kind == 1) return 8.0 + 4.0 + (pl.split_out ? 8.0 : 16.0);
     if (pl.kind == 3) return 8.0 + 8.0 + (pl.pl_out ? 16.0 : 8.0);  // psi_in, lambda in, lambda (+psi) out
-    return 16.0 + (pl.init ? 0.0 : (pl.stored ? 8.0 : 16.0)) + (pl.lc >= 0 ? 4.0 : 0.0);
+    return 16.0 + (pl.init ? 0.0 : (pl.split_out ? 8.0 : 16.0)) + (pl.lc >= 0 ? 4.0 : 0.0);
 }
 
 // Device side (batch.cu): recompute every pass's scalars from device angles,

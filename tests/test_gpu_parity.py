@@ -505,6 +505,46 @@ def test_reverse_block_layouts_agree(q, n, p, kind, maxq, mode):
         assert max(np.abs(dgb0 - dgb1).max(), np.abs(dbb0 - dbb1).max()) <= 1e-5 * sc
 
 
+def test_adjoint_keeps_what_fits(q):
+    """Between the two adjoint forms: under a memory budget the automatic
+    choice keeps the inputs of as many of the last mixer-only passes as fit and
+    uncomputes the rest.  Budgets from below the uncompute sweep's need to above
+    the fully stored form's: every evaluation that runs matches the oracle, the
+    number of mixer-only reverse passes on lambda alone (profile kind 12) never
+    falls as the budget grows, and some budget gives a mixed sweep (four qubit
+    groups, n = 20, p = 3: six mixer-only passes)."""
+    n, p = 20, 3
+    Q = inst.normal_qubo(n, 1600)
+    g, b = _angles(Q, p, "normal")
+    F = oracle.cost_table(oracle.canonical_of(Q))
+    Eo, dgo, dbo = oracle.grad_adjoint(F, g, b)
+    sc = max(np.max(np.abs(dgo)), np.max(np.abs(dbo)))
+    N8 = 8 << n
+    kept = []
+    for j in range(0, 24):
+        budget = 40 * N8 // 8 + j * N8 // 2
+        c = q.qaoa_ctx_create(0, max_fused_qubits=6, memory_budget=budget, profile=True)
+        cost = None
+        try:
+            try:
+                cost = _cost(q, c, Q)
+                E, dg, db = q.qaoa_grad(c, cost, g, b)
+            except q.QaoaError as e:
+                assert e.status == q.QAOA_ERR_OUT_OF_MEMORY
+                continue
+            assert abs(E - Eo) / np.max(np.abs(F)) <= E_TOL
+            assert max(np.max(np.abs(dg - dgo)), np.max(np.abs(db - dbo))) <= G_TOL * sc
+            kept.append(q.qaoa_profile_read(c, 12)["launches"])
+        finally:
+            if cost is not None:
+                q.qaoa_cost_destroy(cost)
+            q.qaoa_ctx_destroy(c)
+    assert kept, "no budget in the sweep ran"
+    assert kept == sorted(kept)
+    assert kept[0] == 0 and kept[-1] == 6
+    assert any(0 < k < 6 for k in kept), kept
+
+
 def test_factorisation_noncontiguous(q, ctx):
     """A manual (non-contiguous) allocation goes through the general check."""
     n = 14
