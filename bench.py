@@ -109,7 +109,8 @@ class ClockSampler:
 def _kernel_source_hash() -> str:
     h = hashlib.sha256()
     # the sources the reverse-pass kernels are compiled from
-    for name in ("kernels_adjoint.cu", "pass_body.cuh", "pass_common.cuh", "tma_util.cuh", "qaoa_internal.h"):
+    for name in ("kernels_adjoint.cu", "kernels_rev_half.cu", "pass_half.cuh", "pass_body.cuh", "pass_common.cuh",
+                 "tma_util.cuh", "qaoa_internal.h"):
         with open(os.path.join(ROOT, "paper_2606_26297_b300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -553,19 +554,27 @@ def run_workload(args):
         q.qaoa_cost_destroy(cost)
     elif args.workload == "uc32":
         Q, g, b = inst.workload_uc32()
-        actx = q.qaoa_ctx_create(0, stream.cuda_stream, adjoint_mode=args.adjoint, profile=True)
+        actx = q.qaoa_ctx_create(0, stream.cuda_stream, adjoint_mode=args.adjoint, profile=True,
+                                 reverse_blocks=args.reverse_blocks)
         cost = q.qaoa_build_cost(actx, Q.H, Q.f, Q.c0, "f32")
         p = len(g)
         # one untimed step: plan, allocation and graph capture
         q.qaoa_optimize_adam(actx, [cost], g[None, :], b[None, :], 1, lr=0.01)
         # the eager first step and the final evaluation each run the reverse sweep once
-        kept = q.qaoa_profile_read(actx, 12, reset=True)["launches"] // 2
+        kept = q.qaoa_profile_read(actx, 12)["launches"] // 2
+        # pass kernels of those two eager evaluations (the graph replays are not timed per kernel)
+        eager = {}
+        for name, k in q.PROFILE_KERNEL_KINDS.items():
+            r = q.qaoa_profile_read(actx, k, reset=True)
+            if r["launches"]:
+                eager[name] = {"launches_per_eval": r["launches"] // 2, "ms_per_eval": r["ms"] / 2}
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         g1, b1, hist, Ef = q.qaoa_optimize_adam(actx, [cost], g[None, :], b[None, :], args.iters, lr=0.01)
         dt = time.perf_counter() - t0
         res.update({"n": 32, "p": p, "adam_iters": args.iters, "adjoint_mode": args.adjoint,
-                    "stored_mixer_only_passes": kept, "seconds": dt, "s_per_step": dt / args.iters,
+                    "stored_mixer_only_passes": kept, "pass_kernels_eager": eager,
+                    "seconds": dt, "s_per_step": dt / args.iters,
                     "layer_evals_per_s": args.iters * p / dt, "E_start": float(hist[0, 0]),
                     "E_end": float(Ef[0]), "E_min_history": float(hist[:, 0].min())})
         q.qaoa_cost_destroy(cost)
@@ -665,8 +674,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-errors", action="store_true", help="skip the per-result errors against the oracle")
     ap.add_argument("--reverse-blocks", type=int, default=0, choices=[0, 1, 2],
-                    help="final and reverse cost-layer passes: half blocks of 2^12 for the low group (0, "
-                         "default), blocks of 2^13 everywhere (1), half blocks everywhere (2)")
+                    help="final and reverse cost-layer passes: half blocks of 2^12 for a ten-qubit low group "
+                         "(0, default), blocks of 2^13 everywhere (1), half blocks everywhere (2)")
     ap.add_argument("--adjoint", type=int, default=0, choices=[0, 1, 2],
                     help="--workload uc32: adjoint form, 0 automatic (stored states that fit), "
                          "1 uncompute, 2 stored")

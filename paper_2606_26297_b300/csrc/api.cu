@@ -183,16 +183,24 @@ qaoa_status make_run_plan(qaoa_ctx c, PlanRun &r, const PlanBufs &b, int keep_ca
 
 qaoa_status ensure_plan_bufs(qaoa_ctx c, PlanBufs &b, const PlanRun &r);
 
-// Plan and allocate; with the automatic adjoint choice, a plan that keeps
-// stored states but meets the memory budget during allocation is retried with
-// one kept state fewer, down to the uncompute sweep.
+// Plan and allocate.  When the allocation runs out of memory, the adjoint
+// scratch of the context's other working sets is released and the plan made
+// again (once); then, with the automatic adjoint choice, a plan that keeps
+// stored states is retried with one kept state fewer, down to the uncompute
+// sweep.
 qaoa_status plan_and_allocate(qaoa_ctx c, PlanRun &r, PlanBufs &b) {
     int cap = -1;
+    bool released = false;
     for (;;) {
         QAOA_TRY(make_run_plan(c, r, b, cap));
         const qaoa_status st = ensure_plan_bufs(c, b, r);
         if (st == QAOA_OK) return QAOA_OK;
-        if (st != QAOA_ERR_OUT_OF_MEMORY || !r.stored || c->opt.adjoint_mode != QAOA_ADJ_AUTO) return st;
+        if (st != QAOA_ERR_OUT_OF_MEMORY) return st;
+        if (!released) {
+            released = true;
+            if (release_adjoint_scratch(c, &b)) continue;
+        }
+        if (!r.stored || c->opt.adjoint_mode != QAOA_ADJ_AUTO) return st;
         cap = r.kept - 1;
         b.states.release(&c->held);
         b.lam.release(&c->held);
@@ -290,9 +298,14 @@ qaoa_status enqueue_plan(qaoa_ctx c, PlanBufs &b, const PlanRun &r, const int32_
         a.amp0 = (float)std::pow(2.0, -0.5 * n);
         const double bytes = pass_bytes_per_amp(pl) * std::ldexp((double)r.nitems, n);
         const bool fwd_tma = pl.kind == 0 && a.has_pre && a.has_cost && a.has_post && !a.init;
-        // final and cost-layer reverse passes on half blocks (two CTAs per SM)
+        // final and cost-layer reverse passes on half blocks (two CTAs per SM); by
+        // default only for a full low group (ten qubits), where it is faster
+        // (n = 30: 9.4 against 9.8 ms per reverse pass); with fewer qubits the
+        // half-block forms take their register-lean X-terms and sums and are
+        // slower (n = 32, eight-qubit groups: 47 against 39 ms)
         const bool half = (pl.kind == 1 || pl.kind == 2) &&
-                          ((c->opt.reverse_blocks == 0 && pl.type == 0) || c->opt.reverse_blocks == 2);
+                          ((c->opt.reverse_blocks == 0 && pl.type == 0 && pl.mask == 0x3FFu) ||
+                           c->opt.reverse_blocks == 2);
         // kernel-level profile kinds, one per kernel (see qaoa_profile_read)
         const int kernel_kind = pl.kind == 0   ? (fwd_tma ? 9 : 8)
                                 : pl.kind == 1 ? (half ? 13 : 10)
@@ -549,6 +562,15 @@ struct SmallSet {
     PlanBufs *b = nullptr;  // gamma/beta/item_s/item_kc/adam/history buffers
 };
 
+// Clears the in-use mark of a batch call's working sets when the call ends.
+struct GroupsInUse {
+    std::vector<BatchGroup> &gs;
+    ~GroupsInUse() {
+        for (BatchGroup &g : gs)
+            if (g.b) g.b->in_use = false;
+    }
+};
+
 qaoa_status build_groups(qaoa_ctx c, int nq, const qaoa_cost *costs, const int32_t *item_cost, int B, int p,
                          bool grad, std::vector<BatchGroup> &groups, SmallSet &small) {
     std::map<int, int> gi;
@@ -588,13 +610,17 @@ qaoa_status build_groups(qaoa_ctx c, int nq, const qaoa_cost *costs, const int32
         auto &slot = c->groups[g.n];
         if (!slot) slot.reset(new PlanBufs());
         g.b = slot.get();
+        g.b->in_use = true;
         QAOA_TRY(plan_and_allocate(c, g.r, *g.b));
         const size_t N = (size_t)1 << g.n;
         if (g.tabs.size() == 1) {
             g.tables = g.tabs[0]->T;
             g.item_table_dev = nullptr;
         } else {
-            QAOA_TRY(g.b->tables.ensure(g.tabs.size() * N * 4, &c->held, c->opt.memory_budget));
+            qaoa_status st = g.b->tables.ensure(g.tabs.size() * N * 4, &c->held, c->opt.memory_budget);
+            if (st == QAOA_ERR_OUT_OF_MEMORY && release_adjoint_scratch(c, nullptr))
+                st = g.b->tables.ensure(g.tabs.size() * N * 4, &c->held, c->opt.memory_budget);
+            QAOA_TRY(st);
             for (size_t k = 0; k < g.tabs.size(); ++k)
                 CUDA_TRY(cudaMemcpyAsync(g.b->tables.as<int32_t>() + k * N, g.tabs[k]->T, N * 4,
                                          cudaMemcpyDeviceToDevice, c->stream));
@@ -651,6 +677,58 @@ qaoa_status enqueue_group(qaoa_ctx c, BatchGroup &g, bool profile) {
         c->launches_total += 1;
     }
     return QAOA_OK;
+}
+
+constexpr int POOL_STREAMS = 4;
+
+qaoa_status ensure_pool(qaoa_ctx c) {
+    if (!c->pool_fork) CUDA_TRY(cudaEventCreateWithFlags(&c->pool_fork, cudaEventDisableTiming));
+    while ((int)c->pool.size() < POOL_STREAMS) {
+        cudaStream_t s = nullptr;
+        cudaEvent_t e = nullptr;
+        CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        c->pool.push_back(s);
+        CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        c->pool_join.push_back(e);
+    }
+    return QAOA_OK;
+}
+
+// Enqueue `home_work` on the context's stream and fn(g) for every group of a
+// batch, the groups on the streams of a small pool forked from and joined back
+// into the context's stream: the passes of a small n fill a few SMs only, so
+// groups of different n overlap on the GPU instead of running one after the
+// other.  Largest n first (the longest chain starts at once).  Legal inside a
+// stream capture (the fork and join are event waits).
+template <class H, class F>
+qaoa_status enqueue_groups(qaoa_ctx c, std::vector<BatchGroup> &groups, H &&home_work, F &&fn) {
+    if (groups.size() <= 1) {
+        QAOA_TRY(home_work());
+        for (BatchGroup &g : groups) QAOA_TRY(fn(g));
+        return QAOA_OK;
+    }
+    QAOA_TRY(ensure_pool(c));
+    std::vector<int> order(groups.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return groups[a].n > groups[b].n; });
+    const cudaStream_t home = c->stream;
+    const int used = (int)std::min(groups.size(), c->pool.size());
+    CUDA_TRY(cudaEventRecord(c->pool_fork, home));
+    for (int k = 0; k < used; ++k) CUDA_TRY(cudaStreamWaitEvent(c->pool[k], c->pool_fork, 0));
+    qaoa_status st = home_work();
+    for (size_t i = 0; i < order.size() && st == QAOA_OK; ++i) {
+        c->stream = c->pool[i % c->pool.size()];
+        st = fn(groups[order[i]]);
+        c->stream = home;
+    }
+    // join every forked stream, also after an error (a capture must end joined)
+    for (int k = 0; k < used; ++k) {
+        const cudaError_t e1 = cudaEventRecord(c->pool_join[k], c->pool[k]);
+        const cudaError_t e2 = cudaStreamWaitEvent(home, c->pool_join[k], 0);
+        if (st == QAOA_OK && (e1 || e2))
+            st = fail(QAOA_ERR_CUDA, "stream join: %s", cudaGetErrorString(e1 ? e1 : e2));
+    }
+    return st;
 }
 
 // Small items: host blocks with device output pointers; the resident kernel
@@ -748,6 +826,9 @@ void qaoa_ctx_destroy(qaoa_ctx c) {
     }
     for (auto e : c->ev_free) cudaEventDestroy(e);
     if (c->aux_stream) cudaStreamDestroy(c->aux_stream);
+    for (auto s : c->pool) cudaStreamDestroy(s);
+    for (auto e : c->pool_join) cudaEventDestroy(e);
+    if (c->pool_fork) cudaEventDestroy(c->pool_fork);
     delete c;
 }
 
@@ -1096,6 +1177,7 @@ qaoa_status qaoa::api::run_batch(qaoa_ctx c, int nq, const qaoa_cost *costs, con
     for (int k = 0; k < nq; ++k)
         if (costs[k]) QAOA_TRY(maybe_tune(c, costs[k]));
     std::vector<BatchGroup> groups;
+    GroupsInUse in_use{groups};
     SmallSet small;
     QAOA_TRY(build_groups(c, nq, costs, item_cost, B, p, grad, groups, small));
     QAOA_TRY(build_small(c, small, costs, item_cost, p, gamma, beta, grad));
@@ -1119,9 +1201,11 @@ qaoa_status qaoa::api::run_batch(qaoa_ctx c, int nq, const qaoa_cost *costs, con
                                      cudaMemcpyHostToDevice, c->stream));
     }
     CUDA_TRY(cudaMemsetAsync(c->status.p, 0, 16, c->stream));
-    QAOA_TRY(enqueue_small(c, small, p, false));
-    for (BatchGroup &g : groups) {
-        QAOA_TRY(upload_angles(c, g.items, p, gamma, beta, g.b->gamma, g.b->beta));
+    // every group's angles before any launch: a copy from pageable host memory
+    // waits for the work already on the stream
+    for (BatchGroup &g : groups) QAOA_TRY(upload_angles(c, g.items, p, gamma, beta, g.b->gamma, g.b->beta));
+    auto home = [&]() { return enqueue_small(c, small, p, false); };
+    auto one = [&](BatchGroup &g) -> qaoa_status {
         QAOA_TRY(enqueue_group(c, g, true));
         if (!grad) {
             if (states)
@@ -1140,7 +1224,9 @@ qaoa_status qaoa::api::run_batch(qaoa_ctx c, int nq, const qaoa_cost *costs, con
                                             g.b->sums.as<double>(), c->stream));
             c->launches_total += 1;
         }
-    }
+        return QAOA_OK;
+    };
+    QAOA_TRY(enqueue_groups(c, groups, home, one));
     QAOA_TRY(status_check(c));
     // results
     if (!small.items.empty()) {
@@ -1227,6 +1313,7 @@ qaoa_status optimize_adam(qaoa_ctx c, int nq, const qaoa_cost *costs, const int3
     for (int k = 0; k < nq; ++k)
         if (costs[k]) QAOA_TRY(maybe_tune(c, costs[k]));
     std::vector<BatchGroup> groups;
+    GroupsInUse in_use{groups};
     SmallSet small;
     QAOA_TRY(build_groups(c, nq, costs, item_cost, B, p, true, groups, small));
     QAOA_TRY(build_small(c, small, costs, item_cost, p, gamma, beta, true));
@@ -1308,9 +1395,9 @@ qaoa_status optimize_adam(qaoa_ctx c, int nq, const qaoa_cost *costs, const int3
         ~Restore() { c->stream = s; }
     } restore{c, user};
     auto eval = [&](bool profile) -> qaoa_status {
-        QAOA_TRY(enqueue_small(c, small, p, true));
-        for (BatchGroup &g : groups) QAOA_TRY(enqueue_group(c, g, profile));
-        return QAOA_OK;
+        return enqueue_groups(
+            c, groups, [&]() { return enqueue_small(c, small, p, true); },
+            [&](BatchGroup &g) { return enqueue_group(c, g, profile); });
     };
     auto step = [&](bool profile) -> qaoa_status {
         QAOA_TRY(eval(profile));

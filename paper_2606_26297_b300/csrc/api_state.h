@@ -84,6 +84,7 @@ struct ProfRec {
 struct PlanBufs {
     DevBuf psi, pl, states, lam, partials, partials2, sums, scal, slot_scale, plan, gamma, beta, item_s, item_kc, item_table, tables,
         out_E, out_dg, out_db, topk_a, topk_b, adam_m, adam_v, adam_step, history, small_items, small_out;
+    bool in_use = false;  // planned for the batch call that is running
 };
 
 }  // namespace api
@@ -110,26 +111,40 @@ struct qaoa_ctx_s {
     double prof_bytes[QAOA_PROF_KINDS] = {};
     int64_t launches_total = 0;  // every kernel launched by this context
     cudaStream_t aux_stream = nullptr;  // owned; runs captured optimisation loops
+    std::vector<cudaStream_t> pool;     // owned; groups of a batch of several n run side by side
+    std::vector<cudaEvent_t> pool_join; // owned; one per pool stream
+    cudaEvent_t pool_fork = nullptr;    // owned
     std::map<int, int> tuned_k;         // fusion width picked by the autotuner, by n
     std::map<int, int> tuned_uncompute; // 1: the autotuner found the uncompute sweep faster, by n
     DevBuf sample_items, sample_scratch, sample_out, small_states;  // measurement by shots
 };
 
-// cudaMalloc for a caller-visible object (a state, an objective table).  The
-// stored forward states of the adjoint (and its lambda buffer) are scratch
-// the context re-creates on its next gradient call, so when the allocation
-// fails they are released and the allocation is tried once more.
+// The stored forward states of the adjoint (and its lambda buffer) are
+// scratch that a context re-creates on its next gradient call of that size.
+// Releases them in every working set but `keep`; returns whether anything was
+// released.
+inline bool release_adjoint_scratch(qaoa_ctx_s *c, const PlanBufs *keep) {
+    bool any = false;
+    auto drop = [&](PlanBufs &b) {
+        if (&b == keep || b.in_use) return;
+        any = any || b.states.cap > 0 || b.lam.cap > 0;
+        b.states.release(&c->held);
+        b.lam.release(&c->held);
+    };
+    drop(c->single);
+    for (auto &kv : c->groups) drop(*kv.second);
+    return any;
+}
+
+// cudaMalloc for a caller-visible object (a state, an objective table): when
+// device memory is short, the adjoint scratch is released and the allocation
+// tried once more.
 inline cudaError_t ctx_malloc(qaoa_ctx_s *c, void **p, size_t bytes) {
     cudaError_t e = cudaMalloc(p, bytes);
     if (e == cudaSuccess) return e;
     cudaGetLastError();
     *p = nullptr;
-    c->single.states.release(&c->held);
-    c->single.lam.release(&c->held);
-    for (auto &kv : c->groups) {
-        kv.second->states.release(&c->held);
-        kv.second->lam.release(&c->held);
-    }
+    if (!release_adjoint_scratch(c, nullptr)) return e;
     e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();

@@ -78,18 +78,22 @@ def test_traffic_record_follows_kernel_sources(tmp_path, monkeypatch):
     import json
     b = _bench()
     d = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
-    assert 0.9 < d["rev_pass"]["dram_bytes"] / d["rev_pass"]["alg_bytes"] < 1.1
+    for k in ("rev_mid_tma_kernel", "rev_pass_kernel", "rev_pass_half_kernel", "final_pass_half_kernel"):
+        assert 0.9 < d[k]["dram_bytes"] / d[k]["alg_bytes"] < 1.1
+    # the committed record was taken from the committed sources
+    assert d["rev_mid_tma_kernel"]["source_hash"] == b._kernel_source_hash()
     root = tmp_path / "repo"
     src = root / "paper_2606_26297_b300" / "csrc"
     src.mkdir(parents=True)
-    for name in ("kernels_adjoint.cu", "pass_body.cuh", "pass_common.cuh", "tma_util.cuh", "qaoa_internal.h"):
+    for name in ("kernels_adjoint.cu", "kernels_rev_half.cu", "pass_half.cuh", "pass_body.cuh", "pass_common.cuh",
+                 "tma_util.cuh", "qaoa_internal.h"):
         (src / name).write_bytes(open(os.path.join(ROOT, "paper_2606_26297_b300", "csrc", name), "rb").read())
     monkeypatch.setattr(b, "ROOT", str(root))
-    assert b._traffic("rev_pass", 1000.0) is None  # no record
+    assert b._traffic("rev_pass_kernel", 1000.0) is None  # no record
     (root / "profiles").mkdir()
-    rec = {"rev_pass": {"dram_bytes": 980.0, "alg_bytes": 1000, "source_hash": b._kernel_source_hash()}}
+    rec = {"rev_pass_kernel": {"dram_bytes": 980.0, "alg_bytes": 1000, "source_hash": b._kernel_source_hash()}}
     (root / "profiles" / "traffic.json").write_text(json.dumps(rec))
-    assert b._traffic("rev_pass", 5000.0) == pytest.approx(4900.0)
+    assert b._traffic("rev_pass_kernel", 5000.0) == pytest.approx(4900.0)
     assert b._traffic("no_such_kernel", 5000.0) is None
-    (src / "pass_body.cuh").write_bytes((src / "pass_body.cuh").read_bytes() + b"\n")
-    assert b._traffic("rev_pass", 5000.0) is None
+    (src / "pass_half.cuh").write_bytes((src / "pass_half.cuh").read_bytes() + b"\n")
+    assert b._traffic("rev_pass_kernel", 5000.0) is None
