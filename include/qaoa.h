@@ -99,10 +99,10 @@ typedef struct {
                                ignored when max_fused_qubits is set */
     int32_t reverse_blocks; /* final forward pass and reverse passes of cost-layer passes:
                                0 = half blocks of 2^12 amplitudes (two 128-thread CTAs per SM)
-                               for the low qubit group when it has ten qubits, blocks of 2^13
-                               (one 256-thread CTA per SM) otherwise; 1 = blocks of 2^13 for every
-                               group; 2 = half blocks for every group.  The same results up to the
-                               rounding of the partial sums. */
+                               for the low qubit group, blocks of 2^13 (one 256-thread CTA per
+                               SM) for the others; 1 = blocks of 2^13 for every group; 2 = half
+                               blocks for every group.  The same results up to the rounding of
+                               the partial sums. */
     int32_t reserved[3];    /* must be zero */
 } qaoa_options;
 

@@ -299,13 +299,11 @@ qaoa_status enqueue_plan(qaoa_ctx c, PlanBufs &b, const PlanRun &r, const int32_
         const double bytes = pass_bytes_per_amp(pl) * std::ldexp((double)r.nitems, n);
         const bool fwd_tma = pl.kind == 0 && a.has_pre && a.has_cost && a.has_post && !a.init;
         // final and cost-layer reverse passes on half blocks (two CTAs per SM); by
-        // default only for a full low group (ten qubits), where it is faster
-        // (n = 30: 9.4 against 9.8 ms per reverse pass); with fewer qubits the
-        // half-block forms take their register-lean X-terms and sums and are
-        // slower (n = 32, eight-qubit groups: 47 against 39 ms)
+        // default for the low group, where they are faster (n = 30: 9.4 against
+        // 9.8 ms per reverse pass; n = 32, eight-qubit groups: 919 against 931 ms
+        // per evaluation), not for the high groups (n = 30: 13.4 against 10.4 ms)
         const bool half = (pl.kind == 1 || pl.kind == 2) &&
-                          ((c->opt.reverse_blocks == 0 && pl.type == 0 && pl.mask == 0x3FFu) ||
-                           c->opt.reverse_blocks == 2);
+                          ((c->opt.reverse_blocks == 0 && pl.type == 0) || c->opt.reverse_blocks == 2);
         // kernel-level profile kinds, one per kernel (see qaoa_profile_read)
         const int kernel_kind = pl.kind == 0   ? (fwd_tma ? 9 : 8)
                                 : pl.kind == 1 ? (half ? 13 : 10)

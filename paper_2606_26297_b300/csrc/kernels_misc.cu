@@ -703,13 +703,15 @@ __global__ void __launch_bounds__(256) fact_check_contig_kernel(FactArgs a, cons
     }
 }
 
-// Contiguous allocation with QPU 0 of at least 10 variables: a CTA checks
+// Contiguous allocation with QPU 0 of at least 10 variables: a warp checks
 // tiles of 1024 consecutive x, each inside one row hi (bits 0..9 of u0 vary,
-// its bits 10..c0-1 are fixed).  Thread t owns x = 4t .. 4t+3 of the tile, so
-// its cross term is one per-thread sum over bits 2..9 of 4t (plus the tile's
-// bits >= 10) and then 0, W0, W1, W0 + W1 for the four entries; the table is
-// read as one 16-byte load per thread, the next tile's load issued before
-// the current one is checked.  One block barrier per tile (W double-buffered).
+// its bits 10..c0-1 are fixed).  Lane l owns x = 128 k + 4 l + e (k = 0..7,
+// e = 0..3): eight 16-byte table loads per lane, each instruction reading 512
+// contiguous bytes, and the next tile's loads issued before the current one is
+// checked.  Lanes 0..c0-1 compute the row's W_q (fact_w) and the warp shares
+// them by shuffles, so no block barrier is needed: the cross term of an entry
+// is the lane's sum over bits 2..6 (from l), plus the tile's bits >= 10, plus
+// the constants of bits 7..9 (from k) and 0, W0, W1, W0 + W1 (from e).
 __device__ __forceinline__ long long fact_w(const FactArgs &a, long long hi, int q) {
     long long w = 0;
     const int c0 = a.c0;
@@ -721,46 +723,63 @@ __device__ __forceinline__ long long fact_w(const FactArgs &a, long long hi, int
     return w;
 }
 
-__global__ void __launch_bounds__(256) fact_check_tiles_kernel(FactArgs a, const long long *__restrict__ Hhi,
+__global__ void __launch_bounds__(256, 2) fact_check_tiles_kernel(FactArgs a, const long long *__restrict__ Hhi,
                                                                long long ntiles) {
-    __shared__ long long wsh[2][16];
     __shared__ unsigned long long cnt_sh;
     __shared__ unsigned int err_sh;
     const int c0 = a.c0;
-    const unsigned j = 4u * threadIdx.x;
+    const unsigned l = threadIdx.x & 31u;
     if (threadIdx.x == 0) {
         cnt_sh = 0;
         err_sh = 0;
     }
     unsigned long long bad = 0;
     float maxerr = 0.f;
-    long long tile = blockIdx.x;
-    int4 tv = make_int4(0, 0, 0, 0);
-    if (tile < ntiles) tv = __ldcs(reinterpret_cast<const int4 *>(a.T + (tile << 10) + j));
-    for (int it = 0; tile < ntiles; tile += gridDim.x, ++it) {
+    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+    long long tile = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    int4 nxt[8];
+    if (tile < ntiles) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) nxt[k] = __ldcs(reinterpret_cast<const int4 *>(a.T + (tile << 10) + 128 * k + 4 * l));
+    }
+    for (; tile < ntiles; tile += nwarps) {
+        int4 cur[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) cur[k] = nxt[k];
+        if (tile + nwarps < ntiles) {
+            const int32_t *src = a.T + ((tile + nwarps) << 10) + 4 * l;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) nxt[k] = __ldcs(reinterpret_cast<const int4 *>(src + 128 * k));
+        }
         const long long x0 = tile << 10;
         const long long hi = x0 >> c0;
         const unsigned uc = (unsigned)(x0 & ((1ll << c0) - 1));
-        long long *W = wsh[it & 1];
-        if (threadIdx.x < 16) W[threadIdx.x] = (int)threadIdx.x < c0 ? fact_w(a, hi, threadIdx.x) : 0ll;
-        __syncthreads();
-        const int4 cur = tv;
-        if (tile + gridDim.x < ntiles) tv = __ldcs(reinterpret_cast<const int4 *>(a.T + ((tile + gridDim.x) << 10) + j));
-        long long cr = 0;
+        const long long wl = (int)l < c0 ? fact_w(a, hi, (int)l) : 0ll;
+        // bits >= 10 of the tile (the same for the whole warp)
+        long long chi = ((int)l >= 10 && ((uc >> l) & 1u)) ? wl : 0ll;
 #pragma unroll
-        for (int q = 2; q < 10; ++q)
-            if ((j >> q) & 1u) cr += W[q];
-        for (int q = 10; q < c0; ++q)
-            if ((uc >> q) & 1u) cr += W[q];
-        const long long H = Hhi[hi];
-        const longlong2 l01 = *reinterpret_cast<const longlong2 *>(a.Ltab + uc + j);
-        const longlong2 l23 = *reinterpret_cast<const longlong2 *>(a.Ltab + uc + j + 2);
-        const long long w0 = W[0], w1 = W[1];
-        bad += (long long)cur.x != H + l01.x + cr;
-        bad += (long long)cur.y != H + l01.y + cr + w0;
-        bad += (long long)cur.z != H + l23.x + cr + w1;
-        bad += (long long)cur.w != H + l23.y + cr + w0 + w1;
-        if (threadIdx.x == 0) maxerr = fmaxf(maxerr, phase_split_err(cur.x, H + l01.x, cr, a));
+        for (int o = 8; o; o >>= 1) chi += __shfl_xor_sync(0xffffffffu, chi, o);
+        long long w[10];
+#pragma unroll
+        for (int q = 0; q < 10; ++q) w[q] = __shfl_sync(0xffffffffu, wl, q);
+        long long cl = __shfl_sync(0xffffffffu, chi, 0);
+#pragma unroll
+        for (int q = 2; q < 7; ++q)
+            if ((l >> (q - 2)) & 1u) cl += w[q];
+        const long long H = Hhi[hi] + cl;
+        const long long w01 = w[0] + w[1];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const long long ck = H + ((k & 1) ? w[7] : 0ll) + ((k & 2) ? w[8] : 0ll) + ((k & 4) ? w[9] : 0ll);
+            const longlong2 l01 = __ldg(reinterpret_cast<const longlong2 *>(a.Ltab + uc + 128 * k + 4 * l));
+            const longlong2 l23 = __ldg(reinterpret_cast<const longlong2 *>(a.Ltab + uc + 128 * k + 4 * l + 2));
+            bad += (long long)cur[k].x != ck + l01.x;
+            bad += (long long)cur[k].y != ck + l01.y + w[0];
+            bad += (long long)cur[k].z != ck + l23.x + w[1];
+            bad += (long long)cur[k].w != ck + l23.y + w01;
+        }
+        // phase rounding sampled on the first x of the tile
+        if (l == 0) maxerr = fmaxf(maxerr, phase_split_err(cur[0].x, Hhi[hi] + a.Ltab[uc], cl, a));
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
@@ -768,7 +787,7 @@ __global__ void __launch_bounds__(256) fact_check_tiles_kernel(FactArgs a, const
         maxerr = fmaxf(maxerr, __shfl_xor_sync(0xffffffffu, maxerr, o));
     }
     __syncthreads();  // cnt_sh / err_sh initialised before the first atomic
-    if ((threadIdx.x & 31u) == 0) {
+    if (l == 0) {
         if (bad) atomicAdd(&cnt_sh, bad);
         atomicMax(&err_sh, __float_as_uint(maxerr));
     }
@@ -786,8 +805,11 @@ cudaError_t launch_fact_check(const FactArgs &a, cudaStream_t st) {
         const unsigned long long nhi = 1ull << (a.n - a.c0);
         fact_hi_kernel<<<(unsigned)((nhi + 255) / 256), 256, 0, st>>>(a, a.hhi);
         if (fact_check_uses_tiles(a)) {
+            // one warp per tile at a time, 8 per CTA; two CTAs per SM stay resident
+            // (128 registers), each warp with two tiles of loads in flight
             const long long ntiles = 1ll << (a.n - 10);
-            const long long grid = ntiles < 148 * 8 ? ntiles : 148 * 8;
+            const long long ctas = (ntiles + 7) / 8;
+            const long long grid = ctas < 148 * 2 ? ctas : 148 * 2;
             fact_check_tiles_kernel<<<(unsigned)grid, 256, 0, st>>>(a, a.hhi, ntiles);
         } else {
             const long long grid = nhi < 2048 ? (long long)nhi : 2048;  // rows per CTA: nhi / 2048 from n - c0 = 11

@@ -224,31 +224,48 @@ __global__ void __launch_bounds__(256, 2) table_mma_kernel(TableMmaArgs a) {
         }
         parity ^= 1u;
         tc_fence_after();
-        // epilogue: digits one at a time into the integer sums u
+        // epilogue: digits one at a time into the integer sums u (modulo 2^32,
+        // so a digit of weight 2^(11 d) >= 2^32 adds nothing).  An exact integer
+        // |acc| <= 2^14 plus 1.5 * 2^23 has the bit pattern acc + 0x4B400000;
+        // the constant times 2^(11 d) of every digit is taken off once, so a
+        // digit costs one FADD and one shift-add.
+        constexpr uint32_t kOff = 0x4B400000u * (1u + (DIG > 1 ? (1u << 11) : 0u) + (DIG > 2 ? (1u << 22) : 0u));
+        const uint32_t base = (uint32_t)alo - kOff;
         uint32_t u[32];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) u[j] = (uint32_t)alo + (uint32_t)ahi_t[col0 + j];
+        for (int j = 0; j < 32; j += 4) {
+            const int4 h = *reinterpret_cast<const int4 *>(ahi_t + col0 + j);
+            u[j] = base + (uint32_t)h.x;
+            u[j + 1] = base + (uint32_t)h.y;
+            u[j + 2] = base + (uint32_t)h.z;
+            u[j + 3] = base + (uint32_t)h.w;
+        }
 #pragma unroll
-        for (int d = 0; d < DIG; ++d) {
+        for (int d = 0; d < (DIG < 3 ? DIG : 3); ++d) {
             float acc[32];
             tmem_ld32(tmem + (((warp & 3u) * 32u) << 16) + (uint32_t)(d * TN + col0), acc);
-            // exact integers |acc| <= 2^14: adding 1.5 * 2^23 puts them in the low mantissa bits
 #pragma unroll
-            for (int j = 0; j < 32; ++j)
-                u[j] += ((uint32_t)__float_as_int(acc[j] + 12582912.0f) - 0x4B400000u) << (11 * d);
+            for (int j = 0; j < 32; ++j) u[j] += (uint32_t)__float_as_int(acc[j] + 12582912.0f) << (11 * d);
         }
         int32_t *ptr = a.T + xlo + ((size_t)(nt * TN + col0) << nlo);
-        uint32_t k = ((uint32_t)(nt * TN + col0) << (nlo - 7)) | (uint32_t)mt;
+        int32_t m = INT_MAX;
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
-            const int32_t v = (int32_t)u[j];
-            __stcs(ptr, v);
-            ptr += stride;
-            if (v < best || (v == best && k < bestk)) {
-                best = v;
+            __stcs(ptr + (size_t)j * stride, (int32_t)u[j]);
+            m = min(m, (int32_t)u[j]);
+        }
+        // argmin (value, then index): the index grows with j within the tile, so
+        // only the first j holding the tile's minimum can improve (best, bestk)
+        if (m <= best) {
+            int jm = 0;
+#pragma unroll
+            for (int j = 31; j >= 0; --j)
+                if ((int32_t)u[j] == m) jm = j;
+            const uint32_t k = (((uint32_t)(nt * TN + col0) << (nlo - 7)) | (uint32_t)mt) + (uint32_t)jm * kstep;
+            if (m < best || k < bestk) {
+                best = m;
                 bestk = k;
             }
-            k += kstep;
         }
         tc_fence_before();
         __syncthreads();
