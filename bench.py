@@ -287,7 +287,8 @@ def run_gpu(args):
     f = torch.from_numpy(Q.f.astype(np.float32)).pin_memory()
     g_h = torch.from_numpy(np.asarray(gamma, dtype=np.float64)).pin_memory()
     b_h = torch.from_numpy(np.asarray(beta, dtype=np.float64)).pin_memory()
-    caps = [n // 3 + (1 if m < n % 3 else 0) for m in range(3)]
+    caps = ([int(c) for c in args.qpu_caps.split(",")] if args.qpu_caps
+            else [n // 3 + (1 if m < n % 3 else 0) for m in range(3)])
 
     def step():
         cost = q.qaoa_build_cost(ctx, H.numpy(), f.numpy(), Q.c0, "f32")
@@ -687,6 +688,8 @@ def main():
     ap.add_argument("--adjoint", type=int, default=0, choices=[0, 1, 2],
                     help="--workload uc32: adjoint form, 0 automatic (stored states that fit), "
                          "1 uncompute, 2 stored")
+    ap.add_argument("--qpu-caps", default="", help="QPU capacities of the DQAOA check, e.g. 10,8,8 (default: "
+                                                    "balanced thirds of n)")
     ap.add_argument("--n", type=int, default=N_QUBITS, help="qubits (default: the n=30 workload)")
     ap.add_argument("--p", type=int, default=DEPTH, help="depth (default 8)")
     ap.add_argument("--workload", default="",

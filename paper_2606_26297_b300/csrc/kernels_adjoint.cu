@@ -30,13 +30,15 @@ namespace qaoa {
 
 __device__ __forceinline__ float2 f2s(float s) { return make_float2(s, s); }
 
-// butterflies of every mixed register bit on the packed pair (P, Q)
+// butterflies of every mixed register bit on the packed pair (P, Q); an
+// unmixed bit runs with t = 0 (the identity) rather than a branch, as in
+// round_mix
 template <int T, int A>
 __device__ __forceinline__ void round_mix_pq(float2 (&P)[32], float2 (&Q)[32], float t, uint32_t mask) {
-    const float2 tt = f2s(t), nt = f2s(-t);
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
-        if (!((mask >> regbit<T, A>(i)) & 1u)) continue;
+        const float ti = ((mask >> regbit<T, A>(i)) & 1u) ? t : 0.f;
+        const float2 tt = f2s(ti), nt = f2s(-ti);
 #pragma unroll
         for (int m = 0; m < 32; ++m) {
             if (m & (1 << i)) continue;
@@ -602,18 +604,10 @@ __global__ void wait_probe_kernel(unsigned int *status) {
 // ---------------------------------------------------------------------------
 // host side: tensor maps and launchers
 // ---------------------------------------------------------------------------
+
 static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
-static cudaError_t get_encoder() {
-    if (g_encode) return cudaSuccess;
-    cudaDriverEntryPointQueryResult q;
-    void *fn = nullptr;
-    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
-    if (e != cudaSuccess) return e;
-    if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
-    g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-    return cudaSuccess;
-}
+static cudaError_t get_encoder() { return tensor_map_encoder(&g_encode); }
 
 // 5-D view of high-group blocks: (bits 0..2) x (bits 3..loA-1) x (window A,
 // bits loA..loA+4) x (bits loA+5..loB-1) x (bits loB..n-1, then `count`

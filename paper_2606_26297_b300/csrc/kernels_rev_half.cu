@@ -24,12 +24,14 @@ namespace half {
 
 __device__ __forceinline__ float2 f2s(float s) { return make_float2(s, s); }
 
+// butterflies on the packed pair (P, Q); an unmixed bit runs with t = 0 (the
+// identity) rather than a branch, which would pin every value to its register
 template <int T, int A>
 __device__ __forceinline__ void round_mix_pq(float2 (&P)[32], float2 (&Q)[32], float t, uint32_t mask) {
-    const float2 tt = f2s(t), nt = f2s(-t);
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
-        if (!((mask >> regbit<T, A>(i)) & 1u)) continue;
+        const float ti = ((mask >> regbit<T, A>(i)) & 1u) ? t : 0.f;
+        const float2 tt = f2s(ti), nt = f2s(-ti);
 #pragma unroll
         for (int m = 0; m < 32; ++m) {
             if (m & (1 << i)) continue;
@@ -307,15 +309,16 @@ __global__ void __launch_bounds__(THREADS, 2)
 
 // ---- final forward pass on half blocks ------------------------------------------------------
 
-// RX butterflies of the mixed register bits on one state (tangent form)
+// RX butterflies of the mixed register bits on one state (tangent form); an
+// unmixed bit runs with t = 0
 template <int T, int A>
 __device__ __forceinline__ void round_mix(float2 (&v)[32], float t, uint32_t mask) {
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
-        if (!((mask >> regbit<T, A>(i)) & 1u)) continue;
+        const float ti = ((mask >> regbit<T, A>(i)) & 1u) ? t : 0.f;
 #pragma unroll
         for (int m = 0; m < 32; ++m)
-            if (!(m & (1 << i))) bfly_tan(v[m], v[m | (1 << i)], t);
+            if (!(m & (1 << i))) bfly_tan(v[m], v[m | (1 << i)], ti);
     }
 }
 
@@ -509,20 +512,12 @@ __global__ void __launch_bounds__(THREADS, 2)
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-static PFN_cuTensorMapEncodeTiled_v12000 g_encode_half = nullptr;
 
 static int rev_half_units(int n, int nitems) { return nitems << (n - half::BITS); }
 
-static cudaError_t get_encoder_half() {
-    if (g_encode_half) return cudaSuccess;
-    cudaDriverEntryPointQueryResult q;
-    void *fn = nullptr;
-    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
-    if (e != cudaSuccess) return e;
-    if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
-    g_encode_half = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-    return cudaSuccess;
-}
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode_half = nullptr;
+
+static cudaError_t get_encoder_half() { return tensor_map_encoder(&g_encode_half); }
 
 // High-group half-block views (5-D).  The (psi, lambda) map: (bits 0,1 as
 // 8 FP64 words) x (bits 2..loA-1) x (window A) x (bits loA+5..loB-1) x

@@ -8,13 +8,16 @@
 // where A_lo holds c0, the low variables' linear terms and their couplings, and
 // A_hi the same for the high variables.  The cross term is a dense product
 // W (2^{n_lo} x 16) times Z_hi^T (16 x 2^{n_hi}, the 0/1 bits of x_hi), done by
-// tcgen05.mma kind::f16 in 128 x 128 tiles with FP32 accumulators in tensor
+// tcgen05.mma kind::f16 in 128 x 64 tiles with FP32 accumulators in tensor
 // memory.  Exactness: W is cut into balanced base-2^11 digits (|digit| <= 1024,
 // exact in f16); each digit's product sums at most 16 terms of magnitude
 // <= 1024, so every FP32 accumulator is an exact integer (< 2^24); the epilogue
-// recombines the digits in int64.  The result is bit-identical to the integer
-// definition for every fixed-point table.
+// recombines the digits in integers modulo 2^32, which gives the int32 table
+// entry exactly.  The result is bit-identical to the integer definition for
+// every fixed-point table.  Each finished tile is staged in shared memory and
+// written by one tensor store (cp.async.bulk.tensor), double-buffered.
 #include <climits>
+#include <cstring>
 
 #include <cuda_fp16.h>
 
@@ -29,6 +32,8 @@ constexpr int TM = 128;         // rows (x_lo) per tile
 constexpr int TN = 64;          // columns (x_hi) per tile
 constexpr int KP = 16;          // padded contraction length (n_hi <= 16)
 constexpr int OPB = TM * KP * 2;  // bytes of one 128 x 16 f16 operand tile (4 KB)
+constexpr int STILE_OFF = 24 * 1024;  // output tiles, after the operands (at most 4 x 4 + 4 KB + 256 B)
+constexpr int TABLE_SMEM = STILE_OFF + 2 * TM * TN * 4;  // 88 KB: two CTAs per SM, not three
 
 // ---- PTX wrappers ----------------------------------------------------------------------
 __device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols) {
@@ -143,11 +148,12 @@ __global__ void table_prep_kernel(TableMmaArgs a) {
 // A_hi and the digit products give T exactly whatever the size of the parts.
 // DIG = number of base-2^11 digits of W (1..4).
 template <int DIG>
-__global__ void __launch_bounds__(256, 2) table_mma_kernel(TableMmaArgs a) {
+__global__ void __launch_bounds__(256, 2) table_mma_kernel(TableMmaArgs a, const __grid_constant__ CUtensorMap tmap) {
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char *opA = smem;                                  // DIG x 4 KB
     unsigned char *opB = smem + DIG * OPB;                      // 2 KB (64 x 16 f16)
     int32_t *ahi_t = reinterpret_cast<int32_t *>(opB + OPB);    // 64 entries, mod 2^32
+    int32_t *stiles = reinterpret_cast<int32_t *>(smem + STILE_OFF);  // two 128 x 64 output tiles
     __shared__ __align__(8) unsigned long long mbar;
     __shared__ uint32_t tslot;
     __shared__ int32_t rv[8];
@@ -165,15 +171,18 @@ __global__ void __launch_bounds__(256, 2) table_mma_kernel(TableMmaArgs a) {
     const long long ntiles = 1ll << (a.n - 13);
     const uint32_t row = (warp & 3u) * 32u + lane;  // tile row of this thread
     const int col0 = (int)(warp >> 2) * 32;         // first tile column of this thread
-    const size_t stride = (size_t)1 << nlo;         // x step of one column
     const uint32_t kstep = 1u << (nlo - 7);         // (x >> 7) step of one column
     int32_t best = INT_MAX;
     uint32_t bestk = 0xFFFFFFFFu;  // x >> 7 of the best entry (row fixed per thread)
     long long cur_mt = -1;
     uint32_t parity = 0;
     bool ok = true;
-    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    int it = 0;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
         const long long mt = t / NT, nt = t % NT;
+        // the output tile of this iteration reuses the buffer stored two tiles ago:
+        // that store must have read it (its bulk group is the older of at most two)
+        if (tid == 0) bulk_wait_read<1>();
         // operands: threads 0..127 write row `tid` of the A tiles, 0..63 row `tid` of B
         if (tid < 128) {
             if (mt != cur_mt) {
@@ -247,13 +256,17 @@ __global__ void __launch_bounds__(256, 2) table_mma_kernel(TableMmaArgs a) {
 #pragma unroll
             for (int j = 0; j < 32; ++j) u[j] += (uint32_t)__float_as_int(acc[j] + 12582912.0f) << (11 * d);
         }
-        int32_t *ptr = a.T + xlo + ((size_t)(nt * TN + col0) << nlo);
+        // the tile goes to shared memory in the box order of the table's 2-D view
+        // (x_lo inner, x_hi outer; 32 lanes write 32 consecutive words), then one
+        // tensor store per tile
+        int32_t *st = stiles + (it & 1) * (TM * TN) + col0 * TM + row;
         int32_t m = INT_MAX;
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
-            __stcs(ptr + (size_t)j * stride, (int32_t)u[j]);
+            st[j * TM] = (int32_t)u[j];
             m = min(m, (int32_t)u[j]);
         }
+        fence_proxy_async();
         // argmin (value, then index): the index grows with j within the tile, so
         // only the first j holding the tile's minimum can improve (best, bestk)
         if (m <= best) {
@@ -269,7 +282,13 @@ __global__ void __launch_bounds__(256, 2) table_mma_kernel(TableMmaArgs a) {
         }
         tc_fence_before();
         __syncthreads();
+        if (tid == 0) {
+            tma_store_2d(&tmap, stiles + (it & 1) * (TM * TN), (int)(mt * TM), (int)(nt * TN));
+            bulk_commit();
+        }
     }
+    // shared memory stays allocated until every store of the CTA has completed
+    if (tid == 0) bulk_wait_all();
     // CTA argmin (value, then index)
     unsigned long long bestx = bestk == 0xFFFFFFFFu ? ~0ull : (((unsigned long long)bestk << 7) | row);
 #pragma unroll
@@ -322,29 +341,44 @@ cudaError_t launch_table_mma(TableMmaArgs a, int grid, cudaStream_t st) {
     if (e) return e;
     const long long ntiles = 1ll << (a.n - 13);
     if (grid > ntiles) grid = (int)ntiles;
+    // the table as a 2-D int32 tensor: x_lo (2^nlo, contiguous) x x_hi (2^nhi)
+    CUtensorMap tmap;
+    {
+        PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+        if ((e = tensor_map_encoder(&encode))) return e;
+        std::memset(&tmap, 0, sizeof(tmap));
+        cuuint64_t dims[2] = {1ull << a.nlo, 1ull << a.nhi};
+        cuuint64_t strides[1] = {4ull << a.nlo};
+        cuuint32_t box[2] = {(cuuint32_t)TM, (cuuint32_t)TN};
+        cuuint32_t estr[2] = {1u, 1u};
+        const CUresult r = encode(&tmap, CU_TENSOR_MAP_DATA_TYPE_INT32, 2, a.T, dims, strides, box, estr,
+                                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                  CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    }
     // two CTAs per SM: the dynamic shared memory request keeps a third CTA off
     // the SM, so a tensor-memory allocation (at most 256 columns) never waits
-    const int smem = 80 * 1024;
+    const int smem = TABLE_SMEM;
     switch (a.digits) {
         case 1:
             if ((e = cudaFuncSetAttribute(table_mma_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)))
                 return e;
-            table_mma_kernel<1><<<grid, 256, smem, st>>>(a);
+            table_mma_kernel<1><<<grid, 256, smem, st>>>(a, tmap);
             break;
         case 2:
             if ((e = cudaFuncSetAttribute(table_mma_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)))
                 return e;
-            table_mma_kernel<2><<<grid, 256, smem, st>>>(a);
+            table_mma_kernel<2><<<grid, 256, smem, st>>>(a, tmap);
             break;
         case 3:
             if ((e = cudaFuncSetAttribute(table_mma_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)))
                 return e;
-            table_mma_kernel<3><<<grid, 256, smem, st>>>(a);
+            table_mma_kernel<3><<<grid, 256, smem, st>>>(a, tmap);
             break;
         case 4:
             if ((e = cudaFuncSetAttribute(table_mma_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)))
                 return e;
-            table_mma_kernel<4><<<grid, 256, smem, st>>>(a);
+            table_mma_kernel<4><<<grid, 256, smem, st>>>(a, tmap);
             break;
         default:
             return cudaErrorInvalidValue;

@@ -98,15 +98,21 @@ __device__ __forceinline__ void bfly_tan(float2 &a, float2 &b, float t) {
     b = nb;
 }
 
-// One register round: the butterflies of every mixed register bit.
+// One register round: the butterflies of every mixed register bit.  A
+// register bit the group does not mix runs with t = 0, the identity, so that a
+// group smaller than its block (mask known only at run time) takes no branch:
+// a branch around a round's butterflies forces every amplitude back into the
+// register it held before the branch, one move per value, which cost the
+// partial-group forms about a third of their instructions.  With the full
+// mask (a compile-time constant) the selects fold away.
 template <int T, int A>
 __device__ __forceinline__ void round_mix(float2 (&v)[32], float t, uint32_t mask) {
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
-        if (!((mask >> regbit<T, A>(i)) & 1u)) continue;
+        const float ti = ((mask >> regbit<T, A>(i)) & 1u) ? t : 0.f;
 #pragma unroll
         for (int m = 0; m < 32; ++m)
-            if (!(m & (1 << i))) bfly_tan(v[m], v[m | (1 << i)], t);
+            if (!(m & (1 << i))) bfly_tan(v[m], v[m | (1 << i)], ti);
     }
 }
 
