@@ -442,7 +442,7 @@ def run_workload(args):
     from paper_2606_26297_b300 import qaoa as q
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
-    ctx = q.qaoa_ctx_create(0, stream.cuda_stream, reverse_blocks=args.reverse_blocks)
+    ctx = q.qaoa_ctx_create(0, stream.cuda_stream)
     res = {"workload": args.workload}
     if args.workload == "fd":
         # Equal accuracy: the adjoint gradient and central differences of
@@ -682,10 +682,9 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-errors", action="store_true", help="skip the per-result errors against the oracle")
-    ap.add_argument("--reverse-blocks", type=int, default=0, choices=[0, 1, 2, 3],
+    ap.add_argument("--reverse-blocks", type=int, default=0, choices=[0, 1, 2],
                     help="final and reverse cost-layer passes: half blocks of 2^12 for the low group (0, "
-                         "default), blocks of 2^13 everywhere (1), half blocks everywhere (2), 0 with the high "
-                         "groups' cost-layer reverse passes on 512-thread CTAs (3)")
+                         "default), blocks of 2^13 everywhere (1), half blocks everywhere (2)")
     ap.add_argument("--adjoint", type=int, default=0, choices=[0, 1, 2],
                     help="--workload uc32: adjoint form, 0 automatic (stored states that fit), "
                          "1 uncompute, 2 stored")

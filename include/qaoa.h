@@ -101,10 +101,8 @@ typedef struct {
                                0 = half blocks of 2^12 amplitudes (two 128-thread CTAs per SM)
                                for the low qubit group, blocks of 2^13 (one 256-thread CTA per
                                SM) for the others; 1 = blocks of 2^13 for every group; 2 = half
-                               blocks for every group; 3 = as 0, with the high groups' cost-layer
-                               reverse passes on the wide-CTA layout (512 threads of 16
-                               amplitudes, one CTA per SM).  The same results up to the rounding
-                               of the partial sums. */
+                               blocks for every group.  The same results up to the rounding of
+                               the partial sums. */
     int32_t reserved[3];    /* must be zero */
 } qaoa_options;
 
@@ -551,9 +549,8 @@ qaoa_status qaoa_expect_noalloc(const void *amps, const int32_t *table, int n, i
  * the kind of the one kernel that ran it: 8 = direct-load forward pass,
  * 9 = TMA-staged forward pass with a cost layer, 10 = final forward pass,
  * 11 = reverse pass of a cost-layer pass, 12 = reverse pass of a mixer-only
- * pass, 13 and 14 = kinds 10 and 11 on half blocks, 15 = kind 11 on the
- * wide-CTA layout (kind 0 sums 8, 9, 10, 13; kind 1 sums 11, 12, 14, 15).
- * Returns launches, summed
+ * pass, 13 and 14 = kinds 10 and 11 on half blocks (kind 0 sums 8, 9, 10, 13;
+ * kind 1 sums 11, 12, 14).  Returns launches, summed
  * milliseconds and summed algorithmic bytes (bytes the method must move) since
  * the last reset; reset = 1 clears the counters after reading. */
 qaoa_status qaoa_profile_read(qaoa_ctx ctx, int kind, int64_t *launches, double *ms,

@@ -177,7 +177,6 @@ qaoa_status make_run_plan(qaoa_ctx c, PlanRun &r, const PlanBufs &b, int keep_ca
     if (!r.stored) r.plan = make_plan(r.n, r.p, r.grad, maxq);
     if (r.plan.empty()) return fail(QAOA_ERR_INVALID_ARG, "no pass layout for n=%d", r.n);
     if (c->opt.reverse_blocks == 2) use_half_block_counts(r.plan);
-    if (c->opt.reverse_blocks == 3) use_wide_reverse(r.plan);
     r.rows = plan_rows(r.plan);
     return QAOA_OK;
 }
@@ -303,13 +302,12 @@ qaoa_status enqueue_plan(qaoa_ctx c, PlanBufs &b, const PlanRun &r, const int32_
         // default for the low group, where they are faster (n = 30: 9.4 against
         // 9.8 ms per reverse pass; n = 32, eight-qubit groups: 919 against 931 ms
         // per evaluation), not for the high groups (n = 30: 13.4 against 10.4 ms)
-        const bool half = (pl.kind == 1 || pl.kind == 2) && !pl.wide &&
-                          (((c->opt.reverse_blocks == 0 || c->opt.reverse_blocks == 3) && pl.type == 0) ||
-                           c->opt.reverse_blocks == 2);
+        const bool half = (pl.kind == 1 || pl.kind == 2) &&
+                          ((c->opt.reverse_blocks == 0 && pl.type == 0) || c->opt.reverse_blocks == 2);
         // kernel-level profile kinds, one per kernel (see qaoa_profile_read)
         const int kernel_kind = pl.kind == 0   ? (fwd_tma ? 9 : 8)
                                 : pl.kind == 1 ? (half ? 13 : 10)
-                                : pl.kind == 2 ? (pl.wide ? 15 : half ? 14 : 11)
+                                : pl.kind == 2 ? (half ? 14 : 11)
                                                : 12;
         {
             ProfScope ps(c, pl.kind >= 2 ? 1 : 0, bytes, profile, kernel_kind);
@@ -322,9 +320,8 @@ qaoa_status enqueue_plan(qaoa_ctx c, PlanBufs &b, const PlanRun &r, const int32_
                                                   : launch_fwd_pass(pl.type, a, c->stream))
                             : pl.kind == 1 ? (half ? launch_final_pass_half(pl.type, a, 2 * c->num_sms, stw, c->stream)
                                                    : launch_final_pass(pl.type, a, c->num_sms, stw, c->stream))
-                            : pl.kind == 2 ? (pl.wide ? launch_rev_pass_wide(a, c->num_sms, stw, c->stream)
-                                              : half    ? launch_rev_pass_half(pl.type, a, 2 * c->num_sms, stw, c->stream)
-                                                        : launch_rev_pass(pl.type, a, c->num_sms, stw, c->stream))
+                            : pl.kind == 2 ? (half ? launch_rev_pass_half(pl.type, a, 2 * c->num_sms, stw, c->stream)
+                                                   : launch_rev_pass(pl.type, a, c->num_sms, stw, c->stream))
                                            : launch_rev_mid(pl.type, a, c->num_sms, stw, c->stream);
             nvtxRangePop();
             if (e) return fail(QAOA_ERR_CUDA, "layer-pass launch failed: %s", cudaGetErrorString(e));
@@ -805,8 +802,7 @@ qaoa_status qaoa_ctx_create(int device, void *cuda_stream, const qaoa_options *o
     if (o.table_build < 0 || o.table_build > 1) return fail(QAOA_ERR_INVALID_ARG, "table_build must be 0 or 1");
     if (o.autotune < 0 || o.autotune > 1) return fail(QAOA_ERR_INVALID_ARG, "autotune must be 0 or 1");
     if (o.adjoint_mode < 0 || o.adjoint_mode > 2) return fail(QAOA_ERR_INVALID_ARG, "adjoint_mode must be 0, 1 or 2");
-    if (o.reverse_blocks < 0 || o.reverse_blocks > 3)
-        return fail(QAOA_ERR_INVALID_ARG, "reverse_blocks must be 0, 1, 2 or 3");
+    if (o.reverse_blocks < 0 || o.reverse_blocks > 2) return fail(QAOA_ERR_INVALID_ARG, "reverse_blocks must be 0, 1 or 2");
     for (int k = 0; k < 3; ++k)
         if (o.reserved[k]) return fail(QAOA_ERR_INVALID_ARG, "options.reserved[%d] must be zero", k);
     auto *c = new qaoa_ctx_s();

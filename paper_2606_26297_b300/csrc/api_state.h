@@ -29,7 +29,7 @@ const char *last_error();
         if (s__ != QAOA_OK) return s__; \
     } while (0)
 
-constexpr int QAOA_PROF_KINDS = 16;
+constexpr int QAOA_PROF_KINDS = 15;
 
 namespace qaoa {
 namespace api {

@@ -406,247 +406,6 @@ __global__ void __launch_bounds__(PASS_THREADS, 1)
 }
 
 // ---------------------------------------------------------------------------
-// Cost-layer reverse pass of a high group on the wide-CTA layout: 512
-// threads, 16 amplitudes of each state per thread (64 data registers against
-// 128 in rev_pass_kernel, whose 255 registers leave one 8-warp CTA per SM and
-// no room for instruction-level parallelism).  With four register bits per
-// arrangement a mixer takes three rounds:
-//   X: lanes {0,1,2,5,6}  regs {9,10,11,12}  warps {3,4,7,8}
-//   Z: lanes {0,1,2,5,6}  regs {3,4,7,8}     warps {9,10,11,12}   (mixes 3, 4)
-//   Y: lanes {0,1,2,3,4}  regs {5,6,7,8}     warps {9,10,11,12}
-// X <-> Z moves amplitudes between warps (block barriers; the mixer's bit flip
-// is applied there); Z and Y share their warp bits, so Z <-> Y stays inside a
-// warp.  The stage is read in X (conflict-free 16-byte reads: lanes 0..7 hold
-// eight consecutive elements), the table in Y (32 consecutive words), and the
-// result is written from X.  One swizzle serves every transpose: bit 5 of the
-// slot folded into bit 3 makes each half-warp's 8-byte accesses hit 16
-// distinct bank pairs in all three arrangements.
-// slots: 0..2 X-terms of the post mixer's rounds X, Z, Y; 3 cost term; 4..6
-// X-terms of the pre mixer's rounds Y, Z, X.
-// ---------------------------------------------------------------------------
-namespace wide {
-constexpr int THREADS = 512;
-constexpr int WARPS = THREADS / 32;
-
-template <int A>
-__device__ __forceinline__ constexpr int regbit(int i) {
-    return A == 0 ? 9 + i : (A == 1 ? (i < 2 ? 3 + i : 5 + i) : 5 + i);
-}
-// register bits a round of arrangement A mixes (Z: bits 3, 4 only)
-template <int A>
-__device__ __forceinline__ constexpr uint32_t round_regs() {
-    return A == 1 ? 0x3u : 0xFu;
-}
-template <int A>
-__device__ __forceinline__ constexpr uint32_t local_idx(uint32_t l, uint32_t m, uint32_t w) {
-    return A == 0   ? ((l & 7u) | ((l >> 3) << 5) | ((w & 3u) << 3) | ((w >> 2) << 7) | (m << 9))
-           : A == 1 ? ((l & 7u) | ((l >> 3) << 5) | ((m & 3u) << 3) | ((m >> 2) << 7) | (w << 9))
-                    : (l | (m << 5) | (w << 9));
-}
-
-// butterflies of one round on the packed pair (P, Q); an unmixed bit runs with t = 0
-template <int A>
-__device__ __forceinline__ void round_pq(float2 (&P)[16], float2 (&Q)[16], float t, uint32_t mask) {
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        if (!((round_regs<A>() >> i) & 1u)) continue;
-        const float ti = ((mask >> regbit<A>(i)) & 1u) ? t : 0.f;
-        const float2 tt = f2s(ti), nt = f2s(-ti);
-#pragma unroll
-        for (int m = 0; m < 16; ++m) {
-            if (m & (1 << i)) continue;
-            const int q = m | (1 << i);
-            const float2 pa = P[m], qa = Q[m], pb = P[q], qb = Q[q];
-            P[m] = __ffma2_rn(tt, qb, pa);
-            Q[m] = __ffma2_rn(nt, pb, qa);
-            P[q] = __ffma2_rn(tt, qa, pb);
-            Q[q] = __ffma2_rn(nt, pa, qb);
-        }
-    }
-}
-
-// Im<lambda| sum_j X_j |psi> over the bits of one round (this thread's part),
-// one f32x2 FMA per ordered pair, four packed accumulators
-template <int A>
-__device__ __forceinline__ float xterm_pq(const float2 (&P)[16], const float2 (&Q)[16], uint32_t mask) {
-    bool on[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) on[i] = ((round_regs<A>() >> i) & 1u) && ((mask >> regbit<A>(i)) & 1u);
-    float2 acc[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-#pragma unroll
-    for (int m = 0; m < 16; ++m) {
-        const float2 r = make_float2(P[m].y, -P[m].x);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            if (!on[i]) continue;
-            acc[(m + i) & 3] = __ffma2_rn(r, Q[m ^ (1 << i)], acc[(m + i) & 3]);
-        }
-    }
-    return ((acc[0].x + acc[0].y) + (acc[1].x + acc[1].y)) + ((acc[2].x + acc[2].y) + (acc[3].x + acc[3].y));
-}
-
-// Transpose one array from arrangement A to B through xbuf.  BLOCK: the two
-// arrangements' warps differ (X <-> Z), so block barriers, and the mixer's
-// flip fm is applied on the way; otherwise (Z <-> Y) warp barriers and fm = 0.
-// LEAD = false drops the barrier before the writes where one already lies
-// between them and the previous reads of the slots they write.
-template <int A, int B, bool BLOCK, bool LEAD>
-__device__ __forceinline__ void transpose(float2 (&v)[16], float2 *sm, uint32_t l, uint32_t w, uint32_t fm) {
-    if constexpr (LEAD) {
-        if constexpr (BLOCK) __syncthreads();
-        else __syncwarp();
-    }
-    const uint32_t ta = swz<1>(local_idx<A>(l, 0u, w) ^ fm);
-#pragma unroll
-    for (int m = 0; m < 16; ++m) sm[ta ^ swz<1>(local_idx<A>(0u, (uint32_t)m, 0u))] = v[m];
-    if constexpr (BLOCK) __syncthreads();
-    else __syncwarp();
-    const uint32_t tb = swz<1>(local_idx<B>(l, 0u, w));
-#pragma unroll
-    for (int m = 0; m < 16; ++m) v[m] = sm[tb ^ swz<1>(local_idx<B>(0u, (uint32_t)m, 0u))];
-}
-
-// deterministic block sum of the first K slots over the 16 warps (warp sums as
-// FP32 TwoSum pairs, then the warps' pairs in FP64 in index order)
-template <int K>
-__device__ __forceinline__ void block_sum_write(const float *val, float2 (*red)[NSLOT], double *out, uint32_t blk) {
-    const int l = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-    for (int s = 0; s < K; ++s) {
-        const float2 p = warp_sum_pair(val[s]);
-        if (l == 0) red[w][s] = p;
-    }
-    __syncthreads();
-    if (threadIdx.x < NSLOT) {
-        double t = 0.0;
-        if ((int)threadIdx.x < K) {
-#pragma unroll
-            for (int k = 0; k < WARPS; ++k) {
-                const float2 p = red[k][threadIdx.x];
-                t += (double)p.x + (double)p.y;
-            }
-        }
-        out[(size_t)blk * NSLOT + threadIdx.x] = t;
-    }
-}
-}  // namespace wide
-
-template <bool SPLIT, bool FULL>
-__global__ void __launch_bounds__(wide::THREADS, 1)
-    rev_wide_kernel(const PassArgs a, const __grid_constant__ CUtensorMap mpl,
-                    const __grid_constant__ CUtensorMap mcost, int nunits, unsigned int *status) {
-    using namespace wide;
-    extern __shared__ __align__(1024) unsigned char smraw[];
-    const uint32_t mask = FULL ? full_mask<1>() : a.mask;
-    float4 *stage = reinterpret_cast<float4 *>(smraw);                  // (psi, lambda) block, 128 KB
-    int32_t *cstage = reinterpret_cast<int32_t *>(smraw + 131072);      // table block, 32 KB
-    float2 *xbuf = reinterpret_cast<float2 *>(smraw + 131072 + 32768);  // transposes, 64 KB
-    __shared__ __align__(8) unsigned long long mbar, mbarc;
-    __shared__ float2 red[WARPS][NSLOT];
-    const uint32_t l = threadIdx.x & 31u, w = threadIdx.x >> 5;
-    const int nbits = a.n - BLOCK_BITS;
-    if (threadIdx.x == 0) {
-        mbar_init(&mbar, 1);
-        mbar_init(&mbarc, 1);
-    }
-    __syncthreads();
-    uint32_t parity = 0, parc = 0;
-    if (threadIdx.x == 0 && (int)blockIdx.x < nunits) {
-        issue_amps<1, true>(blockIdx.x, a, &mpl, stage, &mbar);
-        issue_table<1>(blockIdx.x, a, &mcost, cstage, &mbarc);
-    }
-    for (uint32_t u = blockIdx.x; (int)u < nunits; u += gridDim.x) {
-        const Unit un = unit_of(u, nbits);
-        const PassScal sc = a.scal[un.item];
-        const uint32_t fa = sc.pre_flip ? mask : 0u, fb = sc.post_flip ? mask : 0u;
-        const size_t base = block_base<1>(un.b, a.loA, a.loB);
-        float2 P[16], Q[16];
-        float acc[7];
-        if (!stage_ready(&mbar, parity, status)) return;
-        parity ^= 1u;
-        {
-            const uint32_t t = local_idx<0>(l, 0u, w);
-#pragma unroll
-            for (int m = 0; m < 16; ++m) {
-                const float4 e = stage[t + local_idx<0>(0u, (uint32_t)m, 0u)];
-                P[m] = make_float2(e.x, e.y);
-                Q[m] = make_float2(e.z, e.w);
-            }
-        }
-        __syncthreads();
-        if (threadIdx.x == 0 && (int)(u + gridDim.x) < nunits) {
-            fence_proxy_async();
-            issue_amps<1, true>(u + gridDim.x, a, &mpl, stage, &mbar);
-        }
-        // undo the post mixer: rounds X, Z, Y
-        acc[0] = xterm_pq<0>(P, Q, mask);
-        round_pq<0>(P, Q, -sc.post_t, mask);
-        transpose<0, 1, true, false>(P, xbuf, l, w, fb);  // after the stage-read barrier
-        transpose<0, 1, true, true>(Q, xbuf, l, w, fb);
-        acc[1] = xterm_pq<1>(P, Q, mask);
-        round_pq<1>(P, Q, -sc.post_t, mask);
-        transpose<1, 2, false, true>(P, xbuf, l, w, 0u);
-        transpose<1, 2, false, true>(Q, xbuf, l, w, 0u);
-        acc[2] = xterm_pq<2>(P, Q, mask);
-        round_pq<2>(P, Q, -sc.post_t, mask);
-        // cost layer in Y
-        {
-            int32_t c[16];
-            if (!stage_ready(&mbarc, parc, status)) return;
-            parc ^= 1u;
-            const uint32_t t = local_idx<2>(l, 0u, w);
-#pragma unroll
-            for (int m = 0; m < 16; ++m) c[m] = cstage[t + local_idx<2>(0u, (uint32_t)m, 0u)];
-            __syncthreads();
-            if (threadIdx.x == 0 && (int)(u + gridDim.x) < nunits) {
-                fence_proxy_async();
-                issue_table<1>(u + gridDim.x, a, &mcost, cstage, &mbarc);
-            }
-            float g0 = 0.f, g1 = 0.f;
-#pragma unroll
-            for (int m = 0; m < 16; ++m) {
-                // Im(conj(lambda) psi) = lambda.re psi.im - lambda.im psi.re
-                const float im = fmaf(P[m].y, Q[m].x, -Q[m].y * P[m].x);
-                if (m & 1) g1 = fmaf((float)c[m], im, g1);
-                else g0 = fmaf((float)c[m], im, g0);
-                cmul_pq(P[m], Q[m], cost_phase(c[m], sc.phi, sc.off, sc.kmag, a.precise_phase));
-            }
-            acc[3] = g0 + g1;
-        }
-        // undo the pre mixer: rounds Y, Z, X
-        acc[4] = xterm_pq<2>(P, Q, mask);
-        round_pq<2>(P, Q, -sc.pre_t, mask);
-        transpose<2, 1, false, true>(P, xbuf, l, w, 0u);
-        transpose<2, 1, false, true>(Q, xbuf, l, w, 0u);
-        acc[5] = xterm_pq<1>(P, Q, mask);
-        round_pq<1>(P, Q, -sc.pre_t, mask);
-        // the flipped writes may land in other warps' slots: block barrier first
-        transpose<1, 0, true, true>(P, xbuf, l, w, fa);
-        transpose<1, 0, true, true>(Q, xbuf, l, w, fa);
-        acc[6] = xterm_pq<0>(P, Q, mask);
-        round_pq<0>(P, Q, -sc.pre_t, mask);
-        {
-            const uint32_t e0 = local_idx<0>(l, 0u, w);
-            const size_t g = ((size_t)un.item << a.n) + base + goff<1>(e0, a.loA, a.loB);
-            if (SPLIT) {
-                float2 *q = a.lam + g;
-#pragma unroll
-                for (int m = 0; m < 16; ++m)
-                    __stcs(q + goff<1>(local_idx<0>(0u, (uint32_t)m, 0u), a.loA, a.loB), make_float2(P[m].y, Q[m].y));
-            } else {
-                float4 *q = a.pl + g;
-#pragma unroll
-                for (int m = 0; m < 16; ++m)
-                    __stcs(q + goff<1>(local_idx<0>(0u, (uint32_t)m, 0u), a.loA, a.loB),
-                           make_float4(P[m].x, P[m].y, Q[m].x, Q[m].y));
-            }
-        }
-        wide::block_sum_write<7>(acc, red, a.partials, u);
-        // no barrier here: the next unit passes one (after its stage read) before it writes red
-    }
-}
-
-// ---------------------------------------------------------------------------
 // reverse pass of a middle forward pass (mixer only) with stored states:
 // lambda alone is carried back through the mixer (undo the group's RX,
 // return to true scale) and written, alone or interleaved with the stored
@@ -975,34 +734,6 @@ cudaError_t launch_rev_pass(int type, const PassArgs &a, int grid, unsigned int 
     }
     if (grid > nunits) grid = nunits;
     return rev_dispatch(type, a, m, mc, grid, nunits, smem, status, st);
-}
-
-template <bool SPLIT, bool FULL>
-static cudaError_t wide_launch_f(const PassArgs &a, const CUtensorMap &m, const CUtensorMap &mc, int grid, int nunits,
-                                 int smem, unsigned int *status, cudaStream_t st) {
-    cudaError_t e = set_smem(rev_wide_kernel<SPLIT, FULL>, smem);
-    if (e) return e;
-    rev_wide_kernel<SPLIT, FULL><<<grid, wide::THREADS, smem, st>>>(a, m, mc, nunits, status);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_rev_pass_wide(const PassArgs &a, int grid, unsigned int *status, cudaStream_t st) {
-    if (!(a.has_pre && a.has_cost && a.has_post && a.store)) return cudaErrorInvalidValue;
-    const int nunits = a.nitems << (a.n - BLOCK_BITS);
-    const int smem = 131072 + 32768 + 65536;
-    CUtensorMap m, mc;
-    std::memset(&m, 0, sizeof m);
-    std::memset(&mc, 0, sizeof mc);
-    cudaError_t e;
-    if ((e = make_block_map(&m, a.pl, a.n, a.loA, a.loB, 16, a.nitems))) return e;
-    if ((e = make_block_map(&mc, a.C, a.n, a.loA, a.loB, 4, a.ntables))) return e;
-    if (grid > nunits) grid = nunits;
-    const bool full = a.mask == 0x1FF8u;  // the high group fills local bits 3..12
-    if (a.split)
-        return full ? wide_launch_f<true, true>(a, m, mc, grid, nunits, smem, status, st)
-                    : wide_launch_f<true, false>(a, m, mc, grid, nunits, smem, status, st);
-    return full ? wide_launch_f<false, true>(a, m, mc, grid, nunits, smem, status, st)
-                : wide_launch_f<false, false>(a, m, mc, grid, nunits, smem, status, st);
 }
 
 template <int T, bool PLOUT, bool FULL>

@@ -100,8 +100,6 @@ struct PassArgs {
 cudaError_t launch_fwd_pass(int type, const PassArgs &a, cudaStream_t st);
 cudaError_t launch_final_pass(int type, const PassArgs &a, int grid, unsigned int *status, cudaStream_t st);
 cudaError_t launch_rev_pass(int type, const PassArgs &a, int grid, unsigned int *status, cudaStream_t st);
-// cost-layer reverse pass of a high group on the wide-CTA layout (512 threads, 16 amplitudes each)
-cudaError_t launch_rev_pass_wide(const PassArgs &a, int grid, unsigned int *status, cudaStream_t st);
 // the same pass on half blocks of 2^12 amplitudes (two CTAs per SM; grid =
 // 2 x SMs); one partial-sum row per half block
 cudaError_t launch_rev_pass_half(int type, const PassArgs &a, int grid, unsigned int *status, cudaStream_t st);

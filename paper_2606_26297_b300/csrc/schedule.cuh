@@ -58,8 +58,6 @@ struct PassPlan {
     int type, loA, loB;
     uint32_t mask;
     int kX, kY;
-    int kZ;                    // wide-CTA reverse pass: mixed bits of its third round (0 otherwise)
-    int wide;                  // 1: cost-layer reverse pass of a high group on the wide-CTA layout
     int init;
     int la, lc, lb;            // layers (0-based) of pre mixer, cost, post mixer; -1 none
     int slot_param[NSLOT];     // -1 none, -2 expectation sums, l: dE/dbeta_l, p+l: dE/dgamma_l
@@ -256,28 +254,6 @@ inline void use_half_block_counts(std::vector<PassPlan> &plan) {
         }
 }
 
-// The cost-layer reverse passes of the high groups on the wide-CTA layout
-// (512 threads, 16 amplitudes each): every mixer runs three register rounds,
-// local bits 9..12, then 3..4, then 5..8 (undone in that order for the post
-// mixer and in the reverse order for the pre mixer), and each round's
-// X-terms get a partial-sum slot of their own, since the tangent form scales
-// the states between rounds.  Slots: 0..2 the post mixer's rounds, 3 the cost
-// term, 4..6 the pre mixer's rounds (5..8, 3..4, 9..12).
-inline void use_wide_reverse(std::vector<PassPlan> &plan) {
-    for (PassPlan &pl : plan)
-        if (pl.kind == 2 && pl.type == 1 && pl.la >= 0 && pl.lc >= 0 && pl.lb >= 0) {
-            pl.wide = 1;
-            pl.kX = __builtin_popcount(pl.mask & 0x1E00u);
-            pl.kZ = __builtin_popcount(pl.mask & 0x0018u);
-            pl.kY = __builtin_popcount(pl.mask & 0x01E0u);
-            const int lb = pl.slot_param[0], g = pl.slot_param[2], la = pl.slot_param[3];
-            pl.slot_param[0] = pl.slot_param[1] = pl.slot_param[2] = lb;
-            pl.slot_param[3] = g;
-            pl.slot_param[4] = pl.slot_param[5] = pl.slot_param[6] = la;
-            pl.slot_param[7] = -1;
-        }
-}
-
 inline int plan_rows(const std::vector<PassPlan> &plan) {
     int r = 0;
     for (const auto &pl : plan) r += pl.sum_index >= 0;
@@ -403,7 +379,7 @@ __host__ __device__ inline HdMix mix_of(double beta) {
 // partial sum back to true scale.
 __host__ __device__ inline void pass_scalars(const PassPlan &pl, const double *gamma, const double *beta, int s,
                                              long long k_c, PassScal *sc, double *slot_scale) {
-    const int k = pl.kX + pl.kY + pl.kZ;
+    const int k = pl.kX + pl.kY;
     sc->pre_t = sc->post_t = 0.f;
     sc->pre_flip = sc->post_flip = 0;
     sc->phi = sc->off = 0ull;
@@ -455,26 +431,6 @@ __host__ __device__ inline void pass_scalars(const PassPlan &pl, const double *g
         S = hc_div(S, hc_pow(hc_conj(mb.f), k));
         sc->kend = hc_f2(hc_inv(S));
         slot_scale[0] = slot_scale[1] = 1.0;
-    } else if (pl.wide) {
-        // three rounds per mixer; post: bits 9..12, 3..4, 5..8; pre: the reverse
-        slot_scale[0] = 1.0 / hc_norm(S);
-        S = hc_div(S, hc_pow(hc_conj(mb.f), pl.kX));
-        slot_scale[1] = 1.0 / hc_norm(S);
-        S = hc_div(S, hc_pow(hc_conj(mb.f), pl.kZ));
-        slot_scale[2] = 1.0 / hc_norm(S);
-        S = hc_div(S, hc_pow(hc_conj(mb.f), pl.kY));
-        slot_scale[3] = 1.0 / hc_norm(S);
-        const unsigned long long phi = phase_multiplier(gamma[pl.lc], s);
-        const HdCx Kf = hc_div(hc_pow(hc_conj(ma.f), k), S);
-        sc->phi = 0ull - phi;
-        sc->off = (0ull - (unsigned long long)k_c * phi) + turns_of_arg(Kf);
-        sc->kmag = (float)sqrt(hc_norm(Kf));
-        S = hc_mul(S, Kf);
-        slot_scale[4] = 1.0 / hc_norm(S);
-        S = hc_div(S, hc_pow(hc_conj(ma.f), pl.kY));
-        slot_scale[5] = 1.0 / hc_norm(S);
-        S = hc_div(S, hc_pow(hc_conj(ma.f), pl.kZ));
-        slot_scale[6] = 1.0 / hc_norm(S);
     } else {
         if (pl.lb >= 0) {
             slot_scale[0] = 1.0 / hc_norm(S);

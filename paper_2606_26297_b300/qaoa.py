@@ -610,7 +610,7 @@ PROFILE_KINDS = {"fwd_pass": 0, "rev_pass": 1, "cost_build": 2, "small_resident"
 # one kernel each (a layer pass is counted in its aggregate kind above and here)
 PROFILE_KERNEL_KINDS = {"fwd_pass_kernel": 8, "fwd_cost_tma_kernel": 9, "final_pass_kernel": 10,
                         "rev_pass_kernel": 11, "rev_mid_tma_kernel": 12, "final_pass_half_kernel": 13,
-                        "rev_pass_half_kernel": 14, "rev_wide_kernel": 15}
+                        "rev_pass_half_kernel": 14}
 PROFILE_ALL_LAUNCHES = 5
 
 
