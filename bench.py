@@ -442,7 +442,7 @@ def run_workload(args):
     from paper_2606_26297_b300 import qaoa as q
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
-    ctx = q.qaoa_ctx_create(0, stream.cuda_stream)
+    ctx = q.qaoa_ctx_create(0, stream.cuda_stream, reverse_blocks=args.reverse_blocks)
     res = {"workload": args.workload}
     if args.workload == "fd":
         # Equal accuracy: the adjoint gradient and central differences of
