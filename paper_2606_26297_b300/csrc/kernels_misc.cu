@@ -801,6 +801,8 @@ __global__ void __launch_bounds__(256, 2) fact_check_tiles_kernel(FactArgs a, co
 bool fact_check_uses_tiles(const FactArgs &a) { return a.contiguous && a.c0 >= 10 && a.n - a.c0 >= 1; }
 
 cudaError_t launch_fact_check(const FactArgs &a, cudaStream_t st) {
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (a.contiguous) {
         const unsigned long long nhi = 1ull << (a.n - a.c0);
         fact_hi_kernel<<<(unsigned)((nhi + 255) / 256), 256, 0, st>>>(a, a.hhi);
@@ -809,14 +811,14 @@ cudaError_t launch_fact_check(const FactArgs &a, cudaStream_t st) {
             // (128 registers), each warp with two tiles of loads in flight
             const long long ntiles = 1ll << (a.n - 10);
             const long long ctas = (ntiles + 7) / 8;
-            const long long grid = ctas < 148 * 2 ? ctas : 148 * 2;
+            const long long grid = ctas < 2ll * sms ? ctas : 2ll * sms;
             fact_check_tiles_kernel<<<(unsigned)grid, 256, 0, st>>>(a, a.hhi, ntiles);
         } else {
             const long long grid = nhi < 2048 ? (long long)nhi : 2048;  // rows per CTA: nhi / 2048 from n - c0 = 11
             fact_check_contig_kernel<<<(unsigned)grid, 256, 0, st>>>(a, a.hhi, (long long)nhi);
         }
     } else {
-        fact_check_kernel<<<148 * 8, 256, 0, st>>>(a);
+        fact_check_kernel<<<(unsigned)(8 * sms), 256, 0, st>>>(a);
     }
     return cudaGetLastError();
 }
