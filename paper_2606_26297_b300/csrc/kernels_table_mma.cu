@@ -32,7 +32,7 @@ constexpr int TM = 128;         // rows (x_lo) per tile
 constexpr int TN = 64;          // columns (x_hi) per tile
 constexpr int KP = 16;          // padded contraction length (n_hi <= 16)
 constexpr int OPB = TM * KP * 2;  // bytes of one 128 x 16 f16 operand tile (4 KB)
-constexpr int STILE_OFF = 24 * 1024;  // output tiles, after the operands (at most 4 x 4 + 4 KB + 512 B)
+constexpr int STILE_OFF = 24 * 1024;  // output tiles, after the operands (at most 4 x 4 + 4 KB + 256 B)
 constexpr int TABLE_SMEM = STILE_OFF + 2 * TM * TN * 4;  // 88 KB: two CTAs per SM, not three
 
 // ---- PTX wrappers ----------------------------------------------------------------------
@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(256, 2) table_mma_kernel(TableMmaArgs a, const
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char *opA = smem;                                  // DIG x 4 KB
     unsigned char *opB = smem + DIG * OPB;                      // 2 KB (64 x 16 f16)
-    int32_t *ahi_t = reinterpret_cast<int32_t *>(opB + OPB);    // 2 x 64 entries, mod 2^32
+    int32_t *ahi_t = reinterpret_cast<int32_t *>(opB + OPB);    // 64 entries, mod 2^32
     int32_t *stiles = reinterpret_cast<int32_t *>(smem + STILE_OFF);  // two 128 x 64 output tiles
     __shared__ __align__(8) unsigned long long mbar;
     __shared__ uint32_t tslot;
@@ -177,11 +177,13 @@ __global__ void __launch_bounds__(256, 2) table_mma_kernel(TableMmaArgs a, const
     long long cur_mt = -1;
     uint32_t parity = 0;
     bool ok = true;
-    // operands of tile t: threads 0..127 write row `tid` of the A tiles (when the
-    // row block changes), 0..63 row `tid` of B and the column sums of A_hi
-    // (double-buffered: the previous tile's epilogue may still read them)
-    auto write_operands = [&](long long t, int buf) {
+    int it = 0;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
         const long long mt = t / NT, nt = t % NT;
+        // the output tile of this iteration reuses the buffer stored two tiles ago:
+        // that store must have read it (its bulk group is the older of at most two)
+        if (tid == 0) bulk_wait_read<1>();
+        // operands: threads 0..127 write row `tid` of the A tiles, 0..63 row `tid` of B
         if (tid < 128) {
             if (mt != cur_mt) {
 #pragma unroll
@@ -204,36 +206,24 @@ __global__ void __launch_bounds__(256, 2) table_mma_kernel(TableMmaArgs a, const
                 }
                 *reinterpret_cast<uint4 *>(opB + op_off(tid, 0)) = make_uint4(wds[0], wds[1], wds[2], wds[3]);
                 *reinterpret_cast<uint4 *>(opB + op_off(tid, 8)) = make_uint4(wds[4], wds[5], wds[6], wds[7]);
-                ahi_t[buf * TN + tid] = (int32_t)a.ahi[xh];
+                ahi_t[tid] = (int32_t)a.ahi[xh];
             }
             fence_proxy_async();
         }
         cur_mt = mt;
-    };
-    auto issue_mma = [&]() {
-        const uint64_t bdesc = op_desc(smem_u32(opB));
-#pragma unroll
-        for (int d = 0; d < DIG; ++d)
-            mma_f16(tmem + (uint32_t)(d * TN), op_desc(smem_u32(opA + d * OPB)), bdesc, IDESC, 0u);
-        mma_commit(&mbar);
-    };
-    // Software pipeline: the MMAs of the next tile run while this tile's entries
-    // go to shared memory and out (the accumulators are read into registers,
-    // and the operands rewritten, before the barrier that releases them).
-    long long t = blockIdx.x;
-    if (t < ntiles) {
-        write_operands(t, 0);
+        // x = x_lo + 2^nlo x_hi, x_lo = mt 128 + row; read before the barrier so the load overlaps the MMA
+        const unsigned long long xlo = (unsigned long long)(mt * TM + row);
+        const int32_t alo = (int32_t)a.alo[xlo];
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
-        if (tid == 0) issue_mma();
-    }
-    int it = 0;
-    for (; t < ntiles; t += gridDim.x, ++it) {
-        const long long mt = t / NT, nt = t % NT;
-        // x = x_lo + 2^nlo x_hi, x_lo = mt 128 + row
-        const unsigned long long xlo = (unsigned long long)(mt * TM + row);
-        const int32_t alo = (int32_t)a.alo[xlo];
+        if (tid == 0) {
+            const uint64_t bdesc = op_desc(smem_u32(opB));
+#pragma unroll
+            for (int d = 0; d < DIG; ++d)
+                mma_f16(tmem + (uint32_t)(d * TN), op_desc(smem_u32(opA + d * OPB)), bdesc, IDESC, 0u);
+            mma_commit(&mbar);
+        }
         ok = mbar_wait_bounded(&mbar, parity);
         if (__syncthreads_or(!ok)) {
             if (tid == 0) atomicExch(a.status, 1u);
@@ -251,10 +241,9 @@ __global__ void __launch_bounds__(256, 2) table_mma_kernel(TableMmaArgs a, const
         constexpr uint32_t kOff = 0x4B400000u * (1u + (DIG > 1 ? (1u << 11) : 0u) + (DIG > 2 ? (1u << 22) : 0u));
         const uint32_t base = (uint32_t)alo - kOff;
         uint32_t u[32];
-        const int32_t *ah = ahi_t + (it & 1) * TN + col0;
 #pragma unroll
         for (int j = 0; j < 32; j += 4) {
-            const int4 h = *reinterpret_cast<const int4 *>(ah + j);
+            const int4 h = *reinterpret_cast<const int4 *>(ahi_t + col0 + j);
             u[j] = base + (uint32_t)h.x;
             u[j + 1] = base + (uint32_t)h.y;
             u[j + 2] = base + (uint32_t)h.z;
@@ -267,16 +256,6 @@ __global__ void __launch_bounds__(256, 2) table_mma_kernel(TableMmaArgs a, const
 #pragma unroll
             for (int j = 0; j < 32; ++j) u[j] += (uint32_t)__float_as_int(acc[j] + 12582912.0f) << (11 * d);
         }
-        // the next tile's operands (this tile's MMAs have completed), then its MMAs
-        const long long tn = t + gridDim.x;
-        if (tn < ntiles) write_operands(tn, (it + 1) & 1);
-        // the output tile of this iteration reuses the buffer stored two tiles ago:
-        // that store must have read it (its bulk group is the older of at most two)
-        if (tid == 0) bulk_wait_read<1>();
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-        if (tid == 0 && tn < ntiles) issue_mma();
         // the tile goes to shared memory in the box order of the table's 2-D view
         // (x_lo inner, x_hi outer; 32 lanes write 32 consecutive words), then one
         // tensor store per tile
@@ -301,6 +280,7 @@ __global__ void __launch_bounds__(256, 2) table_mma_kernel(TableMmaArgs a, const
                 bestk = k;
             }
         }
+        tc_fence_before();
         __syncthreads();
         if (tid == 0) {
             tma_store_2d(&tmap, stiles + (it & 1) * (TM * TN), (int)(mt * TM), (int)(nt * TN));
