@@ -418,6 +418,45 @@ qaoa_status qaoa_optimize_adam_resume(qaoa_ctx ctx, int nq, const qaoa_cost *cos
  * circuit once and reuses it; this is the counterpart for the pass plan. */
 qaoa_status qaoa_autotune(qaoa_ctx ctx, qaoa_cost cost, int p, int32_t *best_k, double *ms_by_k);
 
+/* ---- schedule (host only) ------------------------------------------------ */
+
+/* One pass of the schedule of an evaluation, as qaoa_plan_describe reports it. */
+typedef struct {
+    int32_t kind;        /* 0 forward; 1 final forward pass (E, top-K, lambda = H_C psi and the
+                            first reverse group); 2 reverse pass on the interleaved (psi, lambda)
+                            buffer; 3 reverse pass of a mixer-only pass on lambda alone against a
+                            stored forward state */
+    int32_t group_type;  /* 0 low qubit group (block = bits 0..12), 1 high group */
+    int32_t loA, loB;    /* high group: first global bits of its two 5-bit windows */
+    uint32_t mask;       /* mixed local bits of the group */
+    int32_t pre_layer, cost_layer, post_layer;  /* 0-based layers of the pass's mixer before
+                                                   the cost layer, its cost layer and its mixer
+                                                   after it; -1 none */
+    int32_t in_slot, out_slot, psi_slot;        /* stored forward states: slot >= 0, -1 the
+                                                   working state, -2 none */
+    int32_t lambda_alone_out;  /* kinds 1, 2: writes lambda alone (for a kind-3 pass next) */
+    int32_t interleaved_out;   /* kind 3: writes (psi, lambda) interleaved (for a kind-2 pass next) */
+    int32_t slot_param[8];     /* what each partial-sum slot adds to: -1 nothing, -2 the
+                                  expectation sums, l < p: dE/dbeta_l, p + l: dE/dgamma_l */
+    double bytes_per_amp;      /* algorithmic bytes per amplitude the pass moves */
+} qaoa_pass_info;
+
+/* The pass schedule of one evaluation of n qubits at depth p (Eq. qaoa_state;
+ * with grad = 1 the adjoint sweep): the n qubits in groups of at most
+ * max_fused_qubits (3..10), 1 + p(G-1) forward passes (consecutive layers share
+ * their boundary group), then the reverse passes in reverse order.  stored_mids:
+ * how many mixer-only passes keep their input for the reverse sweep (-1 all,
+ * 0 none: the uncompute sweep; the automatic adjoint choice picks this from the
+ * free memory), the last ones of the forward sweep.  A diagnostic of the plan
+ * the library runs; no device is touched.  out: host array of `capacity`
+ * entries (may be NULL to query the count); *count (required) receives the
+ * number of passes, *nslots the stored states, *nmids the mixer-only passes
+ * (both may be NULL).  QAOA_ERR_INVALID_ARG for n outside [13, 33], p < 0,
+ * a width outside [3, 10] or too small a capacity. */
+qaoa_status qaoa_plan_describe(int n, int p, int grad, int max_fused_qubits, int stored_mids,
+                               qaoa_pass_info *out, int capacity, int32_t *count, int32_t *nslots,
+                               int32_t *nmids);
+
 /* ---- DQAOA bookkeeping (host) and the GPU factorisation invariant ------- */
 
 /* QPU allocation of Sec. 3.1.  caps: M capacities, or NULL for balanced

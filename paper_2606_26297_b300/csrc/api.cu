@@ -1523,6 +1523,43 @@ qaoa_status qaoa_partition(int n, int M, const int32_t *caps, const int32_t *man
     return partition(n, M, caps, manual, qpu_of);
 }
 
+qaoa_status qaoa_plan_describe(int n, int p, int grad, int max_fused_qubits, int stored_mids, qaoa_pass_info *out,
+                               int capacity, int32_t *count, int32_t *nslots, int32_t *nmids) {
+    if (!count) return fail(QAOA_ERR_INVALID_ARG, "count is null");
+    if (n < 13 || n > 33) return fail(QAOA_ERR_INVALID_ARG, "n=%d outside [13, 33] (the pass path)", n);
+    if (p < 0 || p > SMALL_MAXP) return fail(QAOA_ERR_INVALID_ARG, "p=%d outside [0, %d]", p, SMALL_MAXP);
+    if (max_fused_qubits < 3 || max_fused_qubits > 10)
+        return fail(QAOA_ERR_INVALID_ARG, "max_fused_qubits=%d outside [3, 10]", max_fused_qubits);
+    int ns = 0, nm = 0;
+    const std::vector<PassPlan> plan = make_plan(n, p, grad != 0, max_fused_qubits, stored_mids, &ns, &nm);
+    if (plan.empty()) return fail(QAOA_ERR_INVALID_ARG, "no layout for n=%d at width %d", n, max_fused_qubits);
+    *count = (int32_t)plan.size();
+    if (nslots) *nslots = ns;
+    if (nmids) *nmids = nm;
+    if (!out) return QAOA_OK;
+    if (capacity < (int)plan.size()) return fail(QAOA_ERR_INVALID_ARG, "capacity %d < %zu passes", capacity, plan.size());
+    for (size_t i = 0; i < plan.size(); ++i) {
+        const PassPlan &pl = plan[i];
+        qaoa_pass_info &o = out[i];
+        o.kind = pl.kind;
+        o.group_type = pl.type;
+        o.loA = pl.loA;
+        o.loB = pl.loB;
+        o.mask = pl.mask;
+        o.pre_layer = pl.la;
+        o.cost_layer = pl.lc;
+        o.post_layer = pl.lb;
+        o.in_slot = pl.in_slot;
+        o.out_slot = pl.out_slot;
+        o.psi_slot = pl.psi_slot;
+        o.lambda_alone_out = (pl.kind == 1 || pl.kind == 2) ? pl.split_out : 0;
+        o.interleaved_out = pl.kind == 3 ? pl.pl_out : 0;
+        for (int s = 0; s < 8; ++s) o.slot_param[s] = s < NSLOT ? pl.slot_param[s] : -1;
+        o.bytes_per_amp = pass_bytes_per_amp(pl);
+    }
+    return QAOA_OK;
+}
+
 qaoa_status qaoa_classify(qaoa_cost cost, const int32_t *qpu_of, int p, int64_t *n_local, int64_t *n_cross,
                           int64_t *remote_cx_est, int64_t *n_cross_all_pairs) {
     if (!cost || !qpu_of || !n_local || !n_cross || !remote_cx_est || p < 0)

@@ -45,6 +45,15 @@ class qaoa_options(ctypes.Structure):
                 ("autotune", ctypes.c_int32), ("reverse_blocks", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
+class qaoa_pass_info(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("group_type", ctypes.c_int32), ("loA", ctypes.c_int32),
+                ("loB", ctypes.c_int32), ("mask", ctypes.c_uint32), ("pre_layer", ctypes.c_int32),
+                ("cost_layer", ctypes.c_int32), ("post_layer", ctypes.c_int32), ("in_slot", ctypes.c_int32),
+                ("out_slot", ctypes.c_int32), ("psi_slot", ctypes.c_int32), ("lambda_alone_out", ctypes.c_int32),
+                ("interleaved_out", ctypes.c_int32), ("slot_param", ctypes.c_int32 * 8),
+                ("bytes_per_amp", ctypes.c_double)]
+
+
 class qaoa_adam_options(ctypes.Structure):
     _fields_ = [("lr", ctypes.c_double), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
                 ("eps", ctypes.c_double), ("iterations", ctypes.c_int32), ("disable_graph", ctypes.c_int32),
@@ -128,6 +137,7 @@ _SIGS = {
     "qaoa_solve": ([_P, _P, ctypes.POINTER(qaoa_solve_options), _PD, _PD, _I, _PU64, _PD, _PI64,
                     ctypes.POINTER(qaoa_sample_metrics), ctypes.POINTER(qaoa_solve_result)], _I),
     "qaoa_partition": ([_I, _I, _PI32, _PI32, _PI32], _I),
+    "qaoa_plan_describe": ([_I, _I, _I, _I, _I, ctypes.POINTER(qaoa_pass_info), _I, _PI32, _PI32, _PI32], _I),
     "qaoa_telegate_simulate": ([_P, _P, _PI32, _I, _PD, _PD, _I, ctypes.c_uint64, _PD, _PF,
                                 ctypes.POINTER(qaoa_telegate_counts)], _I),
     "qaoa_partition_graph": ([ctypes.POINTER(qaoa_qubo), _I, _PI32, _PI32], _I),
@@ -500,6 +510,25 @@ def qaoa_solve(ctx, cost, p_max: int, optimizer: str = "spsa", iterations: int =
 
 
 # ---- DQAOA ----------------------------------------------------------------------------------
+
+def qaoa_plan_describe(n: int, p: int, grad: bool = True, max_fused_qubits: int = 10, stored_mids: int = 0):
+    """The pass schedule of one evaluation (host only; no device is touched):
+    a list of dicts, one per pass in execution order, and the numbers of
+    stored states and of mixer-only passes."""
+    cnt, ns, nm = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(_lib.qaoa_plan_describe(int(n), int(p), int(bool(grad)), int(max_fused_qubits), int(stored_mids), None,
+                                   0, ctypes.byref(cnt), None, None))
+    arr = (qaoa_pass_info * max(cnt.value, 1))()
+    _check(_lib.qaoa_plan_describe(int(n), int(p), int(bool(grad)), int(max_fused_qubits), int(stored_mids), arr,
+                                   cnt.value, ctypes.byref(cnt), ctypes.byref(ns), ctypes.byref(nm)))
+    passes = []
+    for i in range(cnt.value):
+        e = arr[i]
+        d = {f: getattr(e, f) for f, _ in qaoa_pass_info._fields_ if f != "slot_param"}
+        d["slot_param"] = list(e.slot_param)
+        passes.append(d)
+    return passes, ns.value, nm.value
+
 
 def qaoa_partition(n: int, M: int, caps=None, manual=None) -> np.ndarray:
     out = np.zeros(n, dtype=np.int32)
