@@ -218,6 +218,16 @@ def error_report(q, ctx):
     return rep
 
 
+def bench_config(n, p, caps, ws):
+    """The workload both arms report (the reference arm times the oracle on a
+    bounded sample of it, described in its cpu_baseline)."""
+    return {"workload": f"dense N(0,1) float32 QUBO n={n}, p={p}, forward+adjoint+top-{KTOP}, "
+                        f"3 QPUs of capacity {caps} contiguous + factorisation check",
+            "n": n, "p": p, "parallelism": f"replicas x{ws}",
+            "l2": f"inputs larger than L2 ({8 * 2 ** n / 2 ** 30:g} GiB state + "
+                  f"{4 * 2 ** n / 2 ** 30:g} GiB table per pass)"}
+
+
 def run_reference(args):
     rank, ws = _dist()
     if rank != 0:
@@ -234,8 +244,9 @@ def run_reference(args):
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * wall / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": {"workload": f"dense N(0,1) float32 QUBO n={N_QUBITS} p={DEPTH}, "
-                                                      "forward+adjoint", "sample_n": n_s},
+           "data": "synthetic",
+           "config": bench_config(N_QUBITS, DEPTH, [N_QUBITS // 3 + (1 if m < N_QUBITS % 3 else 0) for m in range(3)],
+                                  args.gpus),
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                             "sample": vals[0]["sample"]},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -362,11 +373,7 @@ def run_gpu(args):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c64 (f32 arithmetic; f64 reductions)",
             "data": "synthetic",
-            "config": {"workload": f"dense N(0,1) float32 QUBO n={n}, p={p}, forward+adjoint+top-{KTOP}, "
-                                   f"3 QPUs of capacity {caps} contiguous + factorisation check",
-                       "n": n, "p": p, "parallelism": f"replicas x{ws}",
-                       "l2": f"inputs larger than L2 ({8 * 2 ** n / 2 ** 30:g} GiB state + "
-                             f"{4 * 2 ** n / 2 ** 30:g} GiB table per pass)"},
+            "config": bench_config(n, p, caps, ws),
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                          "peak_source": f"{peak_src} hbm_gbs", "unit": "GB/s", "frac": achieved / peak,
                          "alg_bytes_per_launch": per_launch,
