@@ -197,7 +197,10 @@ qaoa_status qaoa_topk(qaoa_ctx ctx, qaoa_cost cost, qaoa_state state, int k, uin
  * double; dgamma, dbeta: host, p doubles each.  Optional top-K of the final
  * state: k_top = 0 disables it; otherwise top_idx/top_prob are host arrays of
  * k_top (<= 64), same ordering as qaoa_topk.  Device memory: one state plus
- * the context's adjoint buffer (allocated on first use and kept). */
+ * the context's adjoint buffer (allocated on first use and kept); with
+ * adjoint_mode AUTO also the stored forward states that fit (see
+ * qaoa_adjoint_mode), which the context releases when a later allocation of
+ * it (a state, a table, another n) would not fit otherwise. */
 qaoa_status qaoa_grad(qaoa_ctx ctx, qaoa_cost cost, int p, const double *gamma,
                       const double *beta, double *out_expect, double *dgamma, double *dbeta,
                       int k_top, uint64_t *top_idx, float *top_prob);
@@ -208,7 +211,10 @@ qaoa_status qaoa_grad(qaoa_ctx ctx, qaoa_cost cost, int p, const double *gamma,
  * costs[item_cost[b]] (item_cost may be NULL: all items use costs[0]), angles
  * gamma[b*p .. b*p+p-1], beta[b*p ..].  Outputs expect[b], dgamma[b*p + l],
  * dbeta[b*p + l]; dgamma/dbeta may be NULL for forward-only evaluation.
- * All pointers are host memory.  Cost handles may differ in n (ragged batch). */
+ * All pointers are host memory.  Cost handles may differ in n (ragged batch):
+ * the items of one n share each pass launch; the groups of different n run on
+ * internal streams forked from and joined back into the context's stream, so
+ * they overlap on the GPU (the call returns after all of them). */
 qaoa_status qaoa_grad_batch(qaoa_ctx ctx, int nq, const qaoa_cost *costs, const int32_t *item_cost,
                             int B, int p, const double *gamma, const double *beta,
                             double *expect, double *dgamma, double *dbeta);
