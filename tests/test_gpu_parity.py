@@ -545,6 +545,31 @@ def test_adjoint_keeps_what_fits(q):
     assert any(0 < k < 6 for k in kept), kept
 
 
+@pytest.mark.parametrize("n,p,maxq,mode", [(20, 3, 6, 2), (20, 3, 6, 1), (24, 2, 10, 2), (17, 2, 4, 2)])
+def test_launches_follow_the_described_plan(q, n, p, maxq, mode):
+    """The kernels a gradient launches are the passes qaoa_plan_describe lists
+    (the CPU tests check that plan): forward passes (kinds 8, 9), the final
+    pass (10, 13), reverse passes on (psi, lambda) (11, 14) and on lambda alone
+    (12), one launch each."""
+    Q = inst.normal_qubo(n, 1700 + n)
+    g, b = _angles(Q, p, "normal")
+    stored = -1 if mode == 2 else 0
+    plan, _, _ = q.qaoa_plan_describe(n, p, grad=True, max_fused_qubits=maxq, stored_mids=stored)
+    want = {k: sum(ps["kind"] == k for ps in plan) for k in range(4)}
+    c = q.qaoa_ctx_create(0, adjoint_mode=mode, max_fused_qubits=maxq, profile=True)
+    try:
+        cost = _cost(q, c, Q)
+        q.qaoa_grad(c, cost, g, b)
+        got = {kk: q.qaoa_profile_read(c, kk)["launches"] for kk in range(8, 15)}
+        assert got[8] + got[9] == want[0]
+        assert got[10] + got[13] == want[1] == 1
+        assert got[11] + got[14] == want[2]
+        assert got[12] == want[3]
+        q.qaoa_cost_destroy(cost)
+    finally:
+        q.qaoa_ctx_destroy(c)
+
+
 def test_factorisation_noncontiguous(q, ctx):
     """A manual (non-contiguous) allocation goes through the general check."""
     n = 14
