@@ -219,6 +219,30 @@ def test_block_separable_n32_p6(q):
     gc.collect()
 
 
+def test_block_separable_n32_forced_budget(q):
+    """The mixed adjoint at full size under a forced memory budget: the budget
+    leaves room for the uncompute sweep (state 32 GiB, interleaved buffer 64
+    GiB), lambda (32 GiB) and one stored state (32 GiB) but not two, so exactly
+    one of the twelve mixer-only reverse passes carries lambda alone against a
+    stored state (profile kind 12) and the other eleven uncompute; E and the
+    gradient still match the oracle on the blocks."""
+    gib = 1 << 30
+    ctx = q.qaoa_ctx_create(0, memory_budget=176 * gib, profile=True)
+    blocks = [inst.unit_commitment_qubo(8, 1005 + k) for k in range(4)]
+    g, b = inst.ramp_angles(6, gamma_scale=math.sqrt(32) / sum(inst.coefficient_norm(B) for B in blocks))
+    Qb = inst.block_diagonal_qubo(blocks)
+    cost = _cost(q, ctx, Qb)
+    grads = [oracle.grad_adjoint(oracle.cost_table(oracle.canonical_of(B)), g, b) for B in blocks]
+    fmax = sum(np.max(np.abs(oracle.cost_table(oracle.canonical_of(B)))) for B in blocks)
+    E, dg, db = q.qaoa_grad(ctx, cost, g, b)
+    assert q.qaoa_profile_read(ctx, 12)["launches"] == 1
+    assert abs(E - sum(r[0] for r in grads)) / fmax <= E_TOL
+    assert _grad_err(dg, db, sum(r[1] for r in grads), sum(r[2] for r in grads)) <= G_TOL
+    q.qaoa_cost_destroy(cost)
+    q.qaoa_ctx_destroy(ctx)
+    gc.collect()
+
+
 # ---- the dense workloads themselves: properties at full size --------------------------
 
 def test_dense30_properties(q):
